@@ -1,0 +1,269 @@
+"""ctypes binding of the FP64 C oracle (bdis_oracle.c).
+
+TEST INFRASTRUCTURE ONLY. Argument marshalling: every number is computed by
+the C file. `build()` compiles it with the host gcc; `load()` builds on first
+use if the library is missing or older than its source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bdis_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+
+FLAG_FLAT = 1
+FLAG_DIVERGED = 2
+FLAG_SADDLE = 4
+FLAG_GAMMA = 8
+FLAG_EMPTY = 16
+DISCARD_FLAGS = FLAG_DIVERGED | FLAG_SADDLE | FLAG_GAMMA | FLAG_EMPTY
+
+
+class OracleParams(ctypes.Structure):
+    """Mirror of orc_params. Defaults are the paper's settings (Sec. 3):
+    sigma_r = sigma_s = 4, a window of 5 samples at 0.5 and 1 px, gamma 0.75
+    at 640x480; patch 8 with overlap 0.75, 12 iterations, 5 scales."""
+
+    _fields_ = [
+        ("patch_size", ctypes.c_int),
+        ("overlap", ctypes.c_double),
+        ("iterations", ctypes.c_int),
+        ("coarsest_scale", ctypes.c_int),
+        ("finest_scale", ctypes.c_int),
+        ("sigma_r", ctypes.c_double),
+        ("sigma_s", ctypes.c_double),
+        ("window_samples", ctypes.c_int),
+        ("window_step", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("normalize", ctypes.c_int),
+    ]
+
+    @classmethod
+    def make(cls, **kw):
+        d = dict(patch_size=8, overlap=0.75, iterations=12, coarsest_scale=4, finest_scale=0,
+                 sigma_r=4.0, sigma_s=4.0, window_samples=5, window_step=0.5, gamma=0.75,
+                 normalize=1)
+        d.update(kw)
+        return cls(**d)
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile bdis_oracle.c into liborc.so next to it (plain -O2, no fast-math)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_HERE)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC,
+           "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        pp = ctypes.POINTER(OracleParams)
+        i = ctypes.c_int
+        lib.orc_level_dim.argtypes = [i, i]
+        lib.orc_grid_stride.argtypes = [i, ctypes.c_double]
+        lib.orc_grid_count.argtypes = [i, i, i]
+        lib.orc_grid_origin.argtypes = [i, i, i, i, i]
+        lib.orc_downsample.argtypes = [dp, i, i, dp]
+        lib.orc_sobel_x.argtypes = [dp, i, i, dp]
+        lib.orc_patch_init.argtypes = [dp, i, i, i, i, i]
+        lib.orc_patch_init.restype = ctypes.c_double
+        lib.orc_search_patch.argtypes = [dp, dp, dp, i, i, i, i, ctypes.c_double, pp,
+                                         ctypes.c_void_p, dp]
+        lib.orc_search_level.argtypes = [dp, dp, dp, i, i, dp, i, i, pp, dp, dp, dp, dp, ip, ip,
+                                         dp]
+        lib.orc_densify_level.argtypes = [i, i, pp, dp, dp, dp, i, i, i, dp]
+        lib.orc_upsample.argtypes = [dp, i, i, i, i, i, dp]
+        lib.orc_match.argtypes = [dp, dp, i, i, pp, dp]
+        lib.orc_match_u8.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i, i, pp, dp]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def level_dim(n, level):
+    return load().orc_level_dim(int(n), int(level))
+
+
+def grid_stride(ps, overlap):
+    return load().orc_grid_stride(int(ps), float(overlap))
+
+
+def grid_count(n, ps, stride):
+    return load().orc_grid_count(int(n), int(ps), int(stride))
+
+
+def grid_origin(i, count, n, ps, stride):
+    return load().orc_grid_origin(int(i), int(count), int(n), int(ps), int(stride))
+
+
+def grid_origins(n, ps, overlap):
+    s = grid_stride(ps, overlap)
+    c = grid_count(n, ps, s)
+    return np.array([grid_origin(i, c, n, ps, s) for i in range(c)], dtype=np.int64)
+
+
+def downsample(img):
+    img = _f64(img)
+    h, w = img.shape
+    out = np.empty(((h + 1) // 2, (w + 1) // 2))
+    load().orc_downsample(_dp(img), w, h, _dp(out))
+    return out
+
+
+def sobel_x(img):
+    img = _f64(img)
+    h, w = img.shape
+    out = np.empty_like(img)
+    load().orc_sobel_x(_dp(img), w, h, _dp(out))
+    return out
+
+
+def patch_init(coarse, x0, y0, ps):
+    if coarse is None:
+        return load().orc_patch_init(None, 0, 0, int(x0), int(y0), int(ps))
+    coarse = _f64(coarse)
+    return load().orc_patch_init(_dp(coarse), coarse.shape[1], coarse.shape[0], int(x0), int(y0),
+                                 int(ps))
+
+
+class _PatchResult(ctypes.Structure):
+    _fields_ = [("u_init", ctypes.c_double), ("d_star", ctypes.c_double),
+                ("posterior", ctypes.c_double), ("weight", ctypes.c_double),
+                ("flags", ctypes.c_int), ("n_valid", ctypes.c_int)]
+
+
+@dataclass
+class PatchResult:
+    u_init: float
+    d_star: float
+    posterior: float
+    weight: float
+    flags: int
+    n_valid: int
+    energies: np.ndarray
+
+
+def search_patch(L, R, G, x0, y0, u_init, params: OracleParams) -> PatchResult:
+    L, R, G = _f64(L), _f64(R), _f64(G)
+    h, w = L.shape
+    res = _PatchResult()
+    e = np.zeros(params.window_samples)
+    load().orc_search_patch(_dp(L), _dp(R), _dp(G), w, h, int(x0), int(y0), float(u_init),
+                            ctypes.byref(params), ctypes.byref(res), _dp(e))
+    return PatchResult(res.u_init, res.d_star, res.posterior, res.weight, res.flags, res.n_valid, e)
+
+
+def search_level(L, R, G, coarse, params: OracleParams) -> dict:
+    """All patches of one level; arrays shaped (ny, nx) (energies: (ny, nx, s))."""
+    L, R, G = _f64(L), _f64(R), _f64(G)
+    h, w = L.shape
+    s = grid_stride(params.patch_size, params.overlap)
+    nx, ny = grid_count(w, params.patch_size, s), grid_count(h, params.patch_size, s)
+    out = {k: np.empty((ny, nx)) for k in ("u_init", "d_star", "posterior", "weight")}
+    out["flags"] = np.empty((ny, nx), dtype=np.int32)
+    out["n_valid"] = np.empty((ny, nx), dtype=np.int32)
+    out["energies"] = np.empty((ny, nx, params.window_samples))
+    if coarse is None:
+        cp, cw, ch = None, 0, 0
+    else:
+        coarse = _f64(coarse)
+        cp, cw, ch = _dp(coarse), coarse.shape[1], coarse.shape[0]
+    load().orc_search_level(_dp(L), _dp(R), _dp(G), w, h, cp, cw, ch, ctypes.byref(params),
+                            _dp(out["u_init"]), _dp(out["d_star"]), _dp(out["posterior"]),
+                            _dp(out["weight"]), _ip(out["flags"]), _ip(out["n_valid"]),
+                            _dp(out["energies"]))
+    return out
+
+
+def densify_level(shape, params: OracleParams, d_star, weight, coarse, is_finest):
+    h, w = shape
+    d_star, weight = _f64(d_star), _f64(weight)
+    out = np.empty((h, w))
+    if coarse is None:
+        cp, cw, ch = None, 0, 0
+    else:
+        coarse = _f64(coarse)
+        cp, cw, ch = _dp(coarse), coarse.shape[1], coarse.shape[0]
+    load().orc_densify_level(w, h, ctypes.byref(params), _dp(d_star), _dp(weight), cp, cw, ch,
+                             int(bool(is_finest)), _dp(out))
+    return out
+
+
+def upsample(M, f, shape):
+    M = _f64(M)
+    h, w = shape
+    out = np.empty((h, w))
+    load().orc_upsample(_dp(M), M.shape[1], M.shape[0], int(f), w, h, _dp(out))
+    return out
+
+
+def match(left, right, params: OracleParams) -> np.ndarray:
+    """Full method on one pair (uint8 or float images). Returns (H, W) float64, NaN = not estimated."""
+    h, w = left.shape
+    out = np.empty((h, w))
+    if left.dtype == np.uint8 and right.dtype == np.uint8:
+        lc = np.ascontiguousarray(left)
+        rc = np.ascontiguousarray(right)
+        rc_ = load().orc_match_u8(lc.ctypes.data, rc.ctypes.data, w, h, ctypes.byref(params),
+                                  _dp(out))
+    else:
+        lf, rf = _f64(left), _f64(right)
+        rc_ = load().orc_match(_dp(lf), _dp(rf), w, h, ctypes.byref(params), _dp(out))
+    if rc_ != 0:
+        raise ValueError(f"oracle rejected the arguments (code {rc_})")
+    return out
+
+
+def match_stages(left, right, params: OracleParams) -> dict:
+    """The method step by step through the per-stage C functions, keeping
+    every intermediate: levels[l] = {L, R, G, search outputs, dense}."""
+    top, fin = params.coarsest_scale, params.finest_scale
+    Ls, Rs = [_f64(left)], [_f64(right)]
+    for _ in range(top):
+        Ls.append(downsample(Ls[-1]))
+        Rs.append(downsample(Rs[-1]))
+    levels = {}
+    coarse = None
+    for lvl in range(top, fin - 1, -1):
+        G = sobel_x(Ls[lvl])
+        srch = search_level(Ls[lvl], Rs[lvl], G, coarse, params)
+        dense = densify_level(Ls[lvl].shape, params, srch["d_star"], srch["weight"], coarse,
+                              lvl == fin)
+        levels[lvl] = dict(L=Ls[lvl], R=Rs[lvl], G=G, coarse=coarse, dense=dense, **srch)
+        coarse = dense
+    out = coarse if fin == 0 else upsample(coarse, fin, left.shape)
+    return {"levels": levels, "out": out, "pyramid_L": Ls, "pyramid_R": Rs}
