@@ -1,0 +1,420 @@
+#!/usr/bin/env python3
+"""Throughput of plain BDIS on 640x480 synthetic stereo pairs, one JSON line.
+
+A step is one pass of the whole method (pyramid + gradients, inverse search
+with the Bayesian posterior at every scale, densification) over a batch of
+640x480 uint8 pairs resident in device memory, through the library's C ABI.
+Default: 128 pairs per step, patch 8, overlap 0.75, 12 iterations, scales
+4..0, gamma 0.75 (the paper's settings, Sec. 3).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 the script runs under torchrun, one rank per GPU, each rank on its
+own pairs (replicas: pairs are independent, nothing is exchanged); `value`
+is all ranks' pairs over the slowest rank's time. `--impl reference` times
+the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "640x480 pairs/s and p99 ms, plain vs learned-init BDIS, at matched oracle error"
+W, H = 640, 480
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070
+ALU_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--batch", type=int, default=128, help="pairs per step and rank")
+    ap.add_argument("--unique", type=int, default=16, help="distinct seeded pairs per rank")
+    ap.add_argument("--patch", type=int, default=8)
+    ap.add_argument("--latency-iters", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the ps12 variant, latency and e2e measurements")
+    return ap.parse_args()
+
+
+def params_kw(ps):
+    return dict(patch_size=ps, overlap=0.75, iterations=12, coarsest_scale=4, finest_scale=0,
+                sigma_r=4.0, sigma_s=4.0, window_samples=5, window_step=0.5, gamma=0.75,
+                normalize=1)
+
+
+def make_pairs(first, count):
+    import synth
+    L, R, D = synth.make_batch(2, count, first_index=first)
+    return L, R, D
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def _oracle_job(args):
+    idx, ps = args
+    import oracle
+    import synth
+    pair = synth.make_pair(2, idx)
+    t0 = time.perf_counter()
+    out = oracle.match(pair.left, pair.right, oracle.OracleParams.make(**params_kw(ps)))
+    return idx, time.perf_counter() - t0, out
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(n_pairs, ps, pool):
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_job, [(i, ps) for i in range(n_pairs)])
+    wall = time.perf_counter() - t0
+    return wall, sorted(res, key=lambda r: r[0])
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def search_flops_per_pair(bd, ps, params):
+    """Algorithmic flops of the inverse search + window per pair: 8 flops per
+    pixel per patch evaluation, (iterations + window samples) evaluations."""
+    n = bd.patch_count(W, H, params)
+    return n * ps * ps * 8 * (params.iterations + params.window_samples), n
+
+
+def search_src_sha():
+    p = os.path.join(ROOT, "paper_2106_07136_gb300", "csrc", "search.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def recorded_traffic(ps):
+    """DRAM bytes per search launch-set per pair from the committed ncu summary,
+    only while search.cu is the source the counters were taken on."""
+    path = os.path.join(ROOT, "profiles", "search_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = rec.get(f"ps{ps}")
+    if not ent or ent.get("search_cu_sha256_16") != search_src_sha():
+        return None
+    return ent.get("dram_bytes_per_pair")
+
+
+def parity_summary(gpu, ref):
+    """Share of pixels within 0.01 px of the oracle, worst difference, NaN-mask flips."""
+    gn, rn = np.isnan(gpu), np.isnan(ref)
+    both = ~gn & ~rn
+    err = np.abs(gpu[both] - ref[both])
+    return {"frac_within_0.01px": float(((err <= 0.01).sum() + (gn & rn).sum()) / gpu.size),
+            "max_abs_px": float(err.max()) if err.size else 0.0,
+            "mask_flips": int((gn != rn).sum()), "pixels": int(gpu.size)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    cores = host_cores()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        for _ in range(args.warmup):
+            run_oracle_sample(cores, args.patch, pool)
+        walls = []
+        for _ in range(args.steps):
+            wall, _ = run_oracle_sample(cores, args.patch, pool)
+            walls.append(wall)
+    total = sum(walls)
+    value = cores * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"640x480 uint8 pairs (surgical-like synthetic), plain BDIS, "
+                               f"patch {args.patch}, overlap 0.75, 12 it, scales 4..0",
+                   "pairs_per_step": cores, "oracle": "FP64 C, one pair per process"},
+        "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} pairs per step, one per host core"},
+        "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    rank, world, local = dist_env()
+    # Start the CPU-oracle pool before any CUDA work (spawned workers).
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    cores = host_cores()
+    pool = mp.get_context("spawn").Pool(cores) if want_cpu else None
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2106_07136_gb300 as bd
+    import synth
+
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ps = args.patch
+    params = bd.default_params(**params_kw(ps))
+    B, U = args.batch, min(args.unique, args.batch)
+    first = rank * U
+    Lh, Rh, Dgt = make_pairs(first, U)
+    reps = (B + U - 1) // U
+    Lb = np.concatenate([Lh] * reps)[:B]
+    Rb = np.concatenate([Rh] * reps)[:B]
+    left = torch.from_numpy(Lb).to(device)
+    right = torch.from_numpy(Rb).to(device)
+    out = torch.empty((B, H, W), dtype=torch.float32, device=device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    stream = torch.cuda.current_stream(device)
+    m = bd.Matcher(device, stream)
+    m.reserve(W, H, B, params)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        m.match(left, right, params, out=out)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    m.read_timing()
+    m.enable_timing(True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(float(i))  # L2 flush between timed steps (not timed)
+        starts[i].record(stream)
+        m.match(left, right, params, out=out)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    m.enable_timing(False)
+    kt = m.read_timing()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * B * args.steps / (ms / 1e3)
+    launches = (kt["prepare_level0"][1] + 2 * kt["pyramid_level"][1] + kt["search"][1]
+                + kt["densify"][1] + kt["upsample"][1])
+
+    gpu_maps = out[:U].cpu().numpy()
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = measure_extras(args, bd, m, params, left, right, Lh, Rh, device, stream)
+
+    if rank != 0:
+        m.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    flops, n_patches = search_flops_per_pair(bd, ps, params)
+    s_ms, s_n = kt["search"]
+    achieved = flops * B * args.steps / (s_ms / 1e3) / 1e12
+    traffic = recorded_traffic(ps)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
+                "traffic": None if traffic is None else traffic * B / (s_n / args.steps),
+                "kernel": "search (inverse search + posterior, all scales)",
+                "kernel_ms_per_launch": s_ms / s_n,
+                "algorithmic_flops_per_launch": flops * B / (s_n / args.steps),
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+    kernel_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                    for k, v in kt.items() if v[1]}
+
+    acc = {"gpu_vs_ground_truth": synth.error_stats(gpu_maps, Dgt)}
+    cpu = None
+    if pool is not None:
+        n_cpu = min(cores, U)
+        wall, res = run_oracle_sample(n_cpu, ps, pool)
+        pool.close()
+        cpu = {"value": n_cpu / wall, "unit": "pairs/s", "cores": n_cpu, "kind": "oracle",
+               "sample": f"{n_cpu} of the bench's 640x480 pairs, one per process "
+                         f"(FP64 C oracle, single-threaded per pair)",
+               "per_pair_s_median": statistics.median(r[1] for r in res)}
+        ref = np.stack([r[2] for r in res])
+        acc["oracle_vs_ground_truth"] = synth.error_stats(ref, Dgt[:n_cpu])
+        acc["gpu_vs_oracle"] = parity_summary(gpu_maps[:n_cpu], ref)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "640x480 uint8 pairs (surgical-like synthetic: textureless "
+                               "rects, dark ellipses, right-only speculars), plain BDIS, "
+                               f"patch {ps}, overlap 0.75, 12 it, scales 4..0, gamma 0.75",
+                   "pairs_per_step_per_gpu": B, "unique_pairs_per_gpu": U,
+                   "patches_per_pair": n_patches,
+                   "l2": "flushed between timed steps (256 MB write, outside the events)",
+                   "parallelism": f"replicas x{world}"},
+        "mpix_per_s": value * W * H / 1e6,
+        "roofline": roofline,
+        "kernels": kernel_share,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "accuracy": acc,
+    }
+    line.update(extras)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    m.close()
+    if world > 1:
+        dist.destroy_process_group()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_extras(args, bd, m, params, left, right, Lh, Rh, device, stream):
+    import torch
+    res = {}
+    B = left.shape[0]
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    Lp = torch.from_numpy(np.ascontiguousarray(left.cpu().numpy())).pin_memory()
+    Rp = torch.from_numpy(np.ascontiguousarray(right.cpu().numpy())).pin_memory()
+    Op = torch.empty((B, H, W), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        m.match_host(Lp, Rp, params, out=Op)
+    k = max(3, args.steps // 3)
+    t0 = time.perf_counter()
+    for _ in range(k):
+        m.match_host(Lp, Rp, params, out=Op)
+    dt = time.perf_counter() - t0
+    res["e2e"] = {"value": B * k / dt, "unit": "pairs/s", "h2d_bytes_per_step": 2 * B * W * H,
+                  "d2h_bytes_per_step": 4 * B * W * H,
+                  "path": "bdis_match_host: pinned host uint8 in, float32 disparity out"}
+    # single-pair latency (device-resident inputs, host wall clock incl. sync)
+    l1, r1 = left[0], right[0]
+    o1 = torch.empty((H, W), dtype=torch.float32, device=device)
+    for _ in range(20):
+        m.match(l1, r1, params, out=o1)
+    torch.cuda.synchronize()
+    lat = []
+    for _ in range(args.latency_iters):
+        t0 = time.perf_counter()
+        m.match(l1, r1, params, out=o1)
+        stream.synchronize()
+        lat.append(1e3 * (time.perf_counter() - t0))
+    lat.sort()
+    res["latency"] = {"batch": 1, "p50_ms": lat[len(lat) // 2],
+                      "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                      "iters": len(lat)}
+    # patch 12 variant of the same workload
+    p12 = bd.default_params(**params_kw(12))
+    out = torch.empty((B, H, W), dtype=torch.float32, device=device)
+    for _ in range(3):
+        m.match(left, right, p12, out=out)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kk = max(3, args.steps // 3)
+    ev0.record(stream)
+    for _ in range(kk):
+        m.match(left, right, p12, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    res["variants"] = {"patch12": {"value": B * kk / (ev0.elapsed_time(ev1) / 1e3),
+                                   "unit": "pairs/s", "patches_per_pair": bd.patch_count(W, H, p12),
+                                   "l2": "not flushed (back-to-back steps)"}}
+    return res
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,232 @@
+/*
+ * bdis.h -- C ABI of the GB300 (sm_103a) implementation of Bayesian Dense
+ * Inverse Search (BDIS) stereo matching, Song et al., arXiv 2106.07136.
+ *
+ * The method (Sec. 2): build a coarse-to-fine image pyramid (Sec. 2.1,
+ * Fig. 1); at each scale run the inverse-search Lucas-Kanade of Eq. 1 on a
+ * grid of overlapping square patches; weigh every patch by the Bayesian
+ * posterior of Eqs. 3-4 over a small window of disparities, dropping patches
+ * that fail the convergence (saddle) test or the valid-pixel threshold gamma
+ * (Sec. 2.2, Sec. 3); fuse the patches into a dense map with the spatial
+ * Gaussian mask of Eq. 5 (Sec. 2.3). Pixels that no kept patch covers are
+ * not estimated (Sec. 3.2).
+ *
+ * Conventions for every entry point:
+ *   - Disparity D >= 0 with I_left(x, y) ~ I_right(x - D, y) on rectified,
+ *     row-aligned pairs (Sec. 3). Intensities are gray levels 0..255.
+ *   - Images and maps are row-major. "Dense" means pitch = width elements
+ *     and consecutive images of a batch packed back to back.
+ *   - Pointers documented as "device" must be CUDA device (or managed)
+ *     memory on the handle's device; the caller owns them.
+ *   - Work is enqueued on the given CUDA stream and returns before it
+ *     finishes; argument errors return synchronously without enqueuing
+ *     anything; a CUDA error is returned by the call that observes it.
+ *   - `void *stream` is a cudaStream_t (NULL = the legacy default stream).
+ *   - A handle is not thread-safe: use one handle per host thread/stream.
+ *
+ * Per-patch flag bits (bdis_patch_debug.flags) follow the oracle's: 1 flat
+ * (no gradient energy, no update), 2 diverged, 4 saddle, 8 below gamma,
+ * 16 no pixel valid at every window sample. Any bit but 1 drops the patch.
+ */
+#ifndef BDIS_H
+#define BDIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BDIS_OK = 0,
+    BDIS_E_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+    BDIS_E_NOMEM = 2,       /* device or pinned allocation failed; handle still usable */
+    BDIS_E_CUDA = 3,        /* a CUDA call failed; see bdis_last_error_string() */
+    BDIS_E_TIMEOUT = 4,     /* a bounded wait ran out */
+    BDIS_E_UNSUPPORTED = 5  /* valid for the method but outside this build's limits */
+} bdis_status;
+
+typedef enum { BDIS_U8 = 0, BDIS_F32 = 1 } bdis_format;
+
+/* A batch of `count` equally sized grayscale images. data points at the first
+ * pixel of the first image; rows are pitch_bytes apart and images
+ * image_stride_bytes apart (ignored when count == 1). BDIS_F32 exists for
+ * sub-pixel test fixtures whose warps are exact only in floating point. */
+typedef struct {
+    const void *data;
+    int width;
+    int height;
+    size_t pitch_bytes;
+    size_t image_stride_bytes;
+    int count;
+    bdis_format format;
+} bdis_image;
+
+/* Parameters of the method, names after the paper (Sec. 3):
+ *   patch_size      side of the square patch in pixels (Sec. 1), 4..32;
+ *   overlap         fraction shared by neighbouring patches, [0, 1); the
+ *                   stride is round(patch_size * (1 - overlap)), at least 1;
+ *   iterations      inverse-search steps per patch and scale (Eq. 1), >= 0;
+ *   coarsest_scale  pyramid level where the search starts (level l has
+ *                   ceil(W / 2^l) x ceil(H / 2^l) pixels), 0..15;
+ *   finest_scale    level where it ends, 0..coarsest_scale; above 0 the map
+ *                   is brought to full size by bilinear reads;
+ *   sigma_r         brightness std of the likelihood, Eq. 4 (paper: 4);
+ *   sigma_s         spatial std of the Gaussian mask, Eq. 5 (paper: 4);
+ *   window_samples  s, disparity candidates in the window of Eq. 3, odd,
+ *                   1..15 (paper: 5);
+ *   window_step     spacing of the candidates in px (paper: 0.5 and 1 px
+ *                   offsets, i.e. 0.5);
+ *   gamma           minimum fraction of patch pixels whose right-image
+ *                   sample lies inside the image (paper: 0.75 at 640x480,
+ *                   0.25 at 288x360);
+ *   normalize       1: subtract the patch means (DIS's normalisation). */
+typedef struct {
+    int patch_size;
+    float overlap;
+    int iterations;
+    int coarsest_scale;
+    int finest_scale;
+    float sigma_r;
+    float sigma_s;
+    int window_samples;
+    float window_step;
+    float gamma;
+    int normalize;
+} bdis_params;
+
+/* Optional per-patch outputs of bdis_search_level. Any pointer may be NULL.
+ * Arrays are count x n_patches (energies: count x n_patches x s), device. */
+typedef struct {
+    float *u_init;     /* starting disparity of each patch */
+    float *posterior;  /* Eq. 3 posterior of D* within its window */
+    float *energies;   /* window energies E_i, i = 0..s-1 */
+    uint8_t *flags;    /* flag bits listed above */
+    int32_t *n_valid;  /* pixels whose sample at D* is inside the image */
+} bdis_patch_debug;
+
+typedef struct bdis_handle bdis_handle;
+
+/* Paper defaults (Sec. 3): patch 8, overlap 0.75, 12 iterations, scales 4..0,
+ * sigma_r = sigma_s = 4, 5 samples 0.5 px apart, gamma 0.75, normalize 1. */
+void bdis_default_params(bdis_params *p);
+
+const char *bdis_status_string(bdis_status s);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *bdis_last_error_string(void);
+
+/* ABI version: (major << 16) | minor. */
+int bdis_version(void);
+
+/* ---------------------------------------------------------------- geometry
+ * Pure host functions, no GPU needed. */
+
+/* Size of pyramid level `level` for a W x H image (Sec. 2.1): ceil halving. */
+bdis_status bdis_level_dims(int width, int height, int level, int *level_width,
+                            int *level_height);
+
+/* Patch grid along an axis of n pixels: stride and number of origins
+ * (origins i * stride, the last moved to n - patch_size). */
+bdis_status bdis_grid(int n, int patch_size, float overlap, int *stride, int *count);
+
+/* Total number of patches searched for one W x H pair over all levels. */
+bdis_status bdis_patch_count(int width, int height, const bdis_params *p, int64_t *total);
+
+/* ------------------------------------------------------------------ handle */
+
+/* Create a matcher bound to CUDA device `device` and stream `stream`.
+ * The handle owns a device workspace that grows on demand. */
+bdis_status bdis_create(bdis_handle **out, int device, void *stream);
+
+/* Reserve the workspace for a batch of `count` W x H pairs under `p`, so that
+ * later bdis_match calls of that size or smaller allocate nothing. */
+bdis_status bdis_reserve(bdis_handle *h, int width, int height, int count, const bdis_params *p);
+
+/* Bytes of device workspace the handle currently holds. */
+size_t bdis_workspace_bytes(const bdis_handle *h);
+
+void bdis_destroy(bdis_handle *h);
+
+/* Kernel timing. When enabled, the handle brackets each of its launches with
+ * CUDA events on its stream (one pair of event records per launch, no
+ * synchronisation). bdis_read_timing waits for the recorded events, adds
+ * their durations per kernel class and clears them. Classes:
+ * 0 level-0 preparation, 1 pyramid step, 2 inverse search + posterior,
+ * 3 densification, 4 upsampling. */
+#define BDIS_TIMING_CLASSES 8
+typedef struct {
+    double ms[BDIS_TIMING_CLASSES];
+    int64_t launches[BDIS_TIMING_CLASSES];
+} bdis_timing;
+
+bdis_status bdis_enable_timing(bdis_handle *h, int on);
+bdis_status bdis_read_timing(bdis_handle *h, bdis_timing *out);
+
+/* --------------------------------------------------------------- the method */
+
+/* Dense disparity of `left->count` pairs (Sec. 2, the whole method).
+ * left/right: device images, identical geometry and format.
+ * disparity_out: device, count x height x width float, dense; NaN where no
+ * kept patch covers the pixel (Sec. 3.2). Enqueued on the handle's stream. */
+bdis_status bdis_match(bdis_handle *h, const bdis_image *left, const bdis_image *right,
+                       const bdis_params *p, float *disparity_out);
+
+/* Same, with HOST buffers: left/right are `count` dense width x height uint8
+ * images in host memory, disparity_out a dense host float array. The call
+ * copies in, matches, copies out and waits for the stream. Pinned host memory
+ * makes the copies asynchronous DMA; pageable memory works but is slower. */
+bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right,
+                            int width, int height, int count, const bdis_params *p,
+                            float *disparity_out);
+
+/* ------------------------------------------------------------------ steps
+ * The method's steps, one launch sequence each, on dense device batches of
+ * `count` planes. bdis_match runs exactly these kernels. */
+
+/* Level 0 (Sec. 2.1): gray levels as float and the template gradient.
+ * L0, R0, G0: device, count x H x W float. G0 = Sobel-x / 8 of the left image
+ * with a mirrored (reflect-101) border. */
+bdis_status bdis_prepare_level0(const bdis_image *left, const bdis_image *right, float *L0,
+                                float *R0, float *G0, void *stream);
+
+/* One pyramid step (Sec. 2.1): 5x5 binomial [1 4 6 4 1]/16 smoothing with a
+ * reflect-101 border, keeping even samples, for both views; plus Sobel-x / 8
+ * of the new left level. Inputs count x h x w; outputs count x ceil(h/2) x
+ * ceil(w/2). */
+bdis_status bdis_pyramid_level(const float *L, const float *R, int width, int height, int count,
+                               float *L1, float *R1, float *G1, void *stream);
+
+/* Inverse search of every patch of one level (Eq. 1) with the posterior and
+ * patch tests (Eqs. 3-4, Sec. 2.2, Sec. 3). L, R, G: count x h x w device.
+ * coarse: the next coarser dense map, count x ch x cw, or NULL at the
+ * coarsest level (patches then start at 0); a patch starts from twice the
+ * coarse map read bilinearly at half its centre. Outputs, count x n_patches
+ * with patches row-major over the grid: d_star (D*), weight (posterior times
+ * the valid-pixel fraction; 0 for a dropped patch). dbg may be NULL. */
+bdis_status bdis_search_level(const float *L, const float *R, const float *G, int width,
+                              int height, int count, const float *coarse, int coarse_width,
+                              int coarse_height, const bdis_params *p, float *d_star,
+                              float *weight, const bdis_patch_debug *dbg, void *stream);
+
+/* Densification of one level (Sec. 2.3): each pixel is the mean of its kept
+ * covering patches' D* weighted by weight_k * exp(-|x - c_k|^2 / (2 sigma_s^2)).
+ * Pixels without a kept patch get NaN when is_finest, otherwise twice the
+ * coarse map at half their position (0 when coarse is NULL). out: count x h
+ * x w device. */
+bdis_status bdis_densify_level(int width, int height, int count, const bdis_params *p,
+                               const float *d_star, const float *weight, const float *coarse,
+                               int coarse_width, int coarse_height, int is_finest, float *out,
+                               void *stream);
+
+/* Bring a map of level f to full size: bilinear over finite neighbours,
+ * values times 2^f; NaN where no finite neighbour has weight. */
+bdis_status bdis_upsample(const float *map, int map_width, int map_height, int level, int width,
+                          int height, int count, float *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDIS_H */

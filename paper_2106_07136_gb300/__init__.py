@@ -1,0 +1,21 @@
+"""BDIS (Bayesian Dense Inverse Search, arXiv 2106.07136) on GB300 / sm_103a.
+
+The method runs in hand-written CUDA kernels behind the C ABI of
+include/bdis.h (libbdis.so, built in-tree by `build.build()`); this package
+only marshals arguments. There is no CPU fallback: without the CUDA library
+every call raises.
+"""
+from .api import (  # noqa: F401
+    Matcher,
+    default_params,
+    densify_level,
+    grid,
+    image_desc,
+    level_dims,
+    patch_count,
+    prepare_level0,
+    pyramid_level,
+    search_level,
+    upsample,
+)
+from ._lib import BdisError, BdisParams, library_path, load  # noqa: F401

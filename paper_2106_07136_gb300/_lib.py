@@ -1,0 +1,120 @@
+"""ctypes declarations of libbdis.so (include/bdis.h). Marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int, c_float, c_size_t, c_void_p = ctypes.c_int, ctypes.c_float, ctypes.c_size_t, ctypes.c_void_p
+
+BDIS_OK, BDIS_E_INVALID_ARG, BDIS_E_NOMEM, BDIS_E_CUDA, BDIS_E_TIMEOUT, BDIS_E_UNSUPPORTED = range(6)
+BDIS_U8, BDIS_F32 = 0, 1
+
+# Every symbol include/bdis.h declares.
+EXPORTED = [
+    "bdis_default_params", "bdis_status_string", "bdis_last_error_string", "bdis_version",
+    "bdis_level_dims", "bdis_grid", "bdis_patch_count", "bdis_create", "bdis_reserve",
+    "bdis_workspace_bytes", "bdis_destroy", "bdis_match", "bdis_match_host",
+    "bdis_prepare_level0", "bdis_pyramid_level", "bdis_search_level", "bdis_densify_level",
+    "bdis_upsample", "bdis_enable_timing", "bdis_read_timing",
+]
+
+TIMING_CLASSES = ["prepare_level0", "pyramid_level", "search", "densify", "upsample"]
+
+
+class BdisParams(ctypes.Structure):
+    _fields_ = [
+        ("patch_size", c_int), ("overlap", c_float), ("iterations", c_int),
+        ("coarsest_scale", c_int), ("finest_scale", c_int), ("sigma_r", c_float),
+        ("sigma_s", c_float), ("window_samples", c_int), ("window_step", c_float),
+        ("gamma", c_float), ("normalize", c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class BdisImage(ctypes.Structure):
+    _fields_ = [
+        ("data", c_void_p), ("width", c_int), ("height", c_int), ("pitch_bytes", c_size_t),
+        ("image_stride_bytes", c_size_t), ("count", c_int), ("format", c_int),
+    ]
+
+
+class BdisPatchDebug(ctypes.Structure):
+    _fields_ = [("u_init", c_void_p), ("posterior", c_void_p), ("energies", c_void_p),
+                ("flags", c_void_p), ("n_valid", c_void_p)]
+
+
+class BdisTiming(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8)]
+
+
+class BdisError(RuntimeError):
+    def __init__(self, status, what):
+        lib = load()
+        msg = lib.bdis_status_string(status).decode()
+        detail = lib.bdis_last_error_string().decode()
+        super().__init__(f"{what}: {msg}" + (f" ({detail})" if detail else ""))
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the in-tree libbdis.so, building it first if it is missing or stale.
+
+    There is no fallback: without the CUDA library nothing here runs."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libbdis.so is missing at {path}")
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER
+    pp, ip = P(BdisParams), P(BdisImage)
+    lib.bdis_default_params.argtypes = [pp]
+    lib.bdis_default_params.restype = None
+    lib.bdis_status_string.argtypes = [c_int]
+    lib.bdis_status_string.restype = ctypes.c_char_p
+    lib.bdis_last_error_string.argtypes = []
+    lib.bdis_last_error_string.restype = ctypes.c_char_p
+    lib.bdis_version.restype = c_int
+    lib.bdis_level_dims.argtypes = [c_int, c_int, c_int, P(c_int), P(c_int)]
+    lib.bdis_grid.argtypes = [c_int, c_int, c_float, P(c_int), P(c_int)]
+    lib.bdis_patch_count.argtypes = [c_int, c_int, pp, P(ctypes.c_int64)]
+    lib.bdis_create.argtypes = [P(c_void_p), c_int, c_void_p]
+    lib.bdis_reserve.argtypes = [c_void_p, c_int, c_int, c_int, pp]
+    lib.bdis_workspace_bytes.argtypes = [c_void_p]
+    lib.bdis_workspace_bytes.restype = c_size_t
+    lib.bdis_destroy.argtypes = [c_void_p]
+    lib.bdis_destroy.restype = None
+    lib.bdis_match.argtypes = [c_void_p, ip, ip, pp, c_void_p]
+    lib.bdis_match_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, pp,
+                                    c_void_p]
+    lib.bdis_prepare_level0.argtypes = [ip, ip, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.bdis_pyramid_level.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
+                                       c_void_p, c_void_p, c_void_p]
+    lib.bdis_search_level.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
+                                      c_int, c_int, pp, c_void_p, c_void_p,
+                                      P(BdisPatchDebug), c_void_p]
+    lib.bdis_densify_level.argtypes = [c_int, c_int, c_int, pp, c_void_p, c_void_p, c_void_p,
+                                       c_int, c_int, c_int, c_void_p, c_void_p]
+    lib.bdis_upsample.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p,
+                                  c_void_p]
+    lib.bdis_enable_timing.argtypes = [c_void_p, c_int]
+    lib.bdis_read_timing.argtypes = [c_void_p, P(BdisTiming)]
+    _lib = lib
+    return lib
+
+
+def check(status: int, what: str):
+    if status != BDIS_OK:
+        raise BdisError(status, what)

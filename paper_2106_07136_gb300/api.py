@@ -1,0 +1,246 @@
+"""Python face of the BDIS CUDA library: argument marshalling over the C ABI.
+
+Every step of the method runs in libbdis.so's kernels. PyTorch provides the
+device memory (tensors) and the CUDA stream; nothing here computes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import BdisImage, BdisParams, BdisPatchDebug, check
+
+
+def default_params(**overrides) -> BdisParams:
+    """The paper's settings (Sec. 3) with optional overrides."""
+    p = BdisParams()
+    _lib.load().bdis_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def level_dims(width: int, height: int, level: int):
+    w, h = ctypes.c_int(), ctypes.c_int()
+    check(_lib.load().bdis_level_dims(width, height, level, ctypes.byref(w), ctypes.byref(h)),
+          "bdis_level_dims")
+    return w.value, h.value
+
+
+def grid(n: int, patch_size: int, overlap: float):
+    s, c = ctypes.c_int(), ctypes.c_int()
+    check(_lib.load().bdis_grid(n, patch_size, overlap, ctypes.byref(s), ctypes.byref(c)),
+          "bdis_grid")
+    return s.value, c.value
+
+
+def patch_count(width: int, height: int, params: BdisParams) -> int:
+    t = ctypes.c_int64()
+    check(_lib.load().bdis_patch_count(width, height, ctypes.byref(params), ctypes.byref(t)),
+          "bdis_patch_count")
+    return t.value
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _as_batch(t: torch.Tensor) -> torch.Tensor:
+    if t.dim() == 2:
+        return t.unsqueeze(0)
+    if t.dim() != 3:
+        raise ValueError("images must be (H, W) or (B, H, W)")
+    return t
+
+
+def image_desc(t: torch.Tensor) -> BdisImage:
+    """Describe a (B, H, W) or (H, W) CUDA tensor (uint8 or float32, unit column stride)."""
+    t = _as_batch(t)
+    if t.dtype == torch.uint8:
+        fmt, es = _lib.BDIS_U8, 1
+    elif t.dtype == torch.float32:
+        fmt, es = _lib.BDIS_F32, 4
+    else:
+        raise TypeError("images must be uint8 or float32")
+    if t.stride(2) != 1:
+        raise ValueError("image rows must be contiguous")
+    b, h, w = t.shape
+    return BdisImage(t.data_ptr(), w, h, t.stride(1) * es, t.stride(0) * es, b, fmt)
+
+
+class Matcher:
+    """A BDIS matcher bound to one CUDA device and stream (bdis_create)."""
+
+    def __init__(self, device=None, stream=None):
+        self._lib = _lib.load()
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else \
+            torch.device(device)
+        self.device = dev
+        with torch.cuda.device(dev):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        h = ctypes.c_void_p()
+        check(self._lib.bdis_create(ctypes.byref(h), dev.index or 0,
+                                    ctypes.c_void_p(int(self.stream.cuda_stream))), "bdis_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bdis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, width, height, count, params: BdisParams):
+        check(self._lib.bdis_reserve(self._h, width, height, count, ctypes.byref(params)),
+              "bdis_reserve")
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.bdis_workspace_bytes(self._h))
+
+    def enable_timing(self, on: bool = True):
+        """Bracket every kernel launch of this handle with CUDA events."""
+        check(self._lib.bdis_enable_timing(self._h, int(bool(on))), "bdis_enable_timing")
+
+    def read_timing(self) -> dict:
+        """Per kernel class: (total ms, launches) since the last read; waits for them."""
+        t = _lib.BdisTiming()
+        check(self._lib.bdis_read_timing(self._h, ctypes.byref(t)), "bdis_read_timing")
+        return {name: (t.ms[i], int(t.launches[i]))
+                for i, name in enumerate(_lib.TIMING_CLASSES)}
+
+    def match(self, left: torch.Tensor, right: torch.Tensor, params: BdisParams = None,
+              out: torch.Tensor = None) -> torch.Tensor:
+        """Disparity of device images (H, W) or (B, H, W); NaN = not estimated."""
+        params = params if params is not None else default_params()
+        squeeze = left.dim() == 2
+        lb, rb = _as_batch(left), _as_batch(right)
+        b, h, w = lb.shape
+        if out is None:
+            out = torch.empty((b, h, w), dtype=torch.float32, device=left.device)
+        if not (out.is_contiguous() and out.dtype == torch.float32 and out.numel() == b * h * w):
+            raise ValueError("out must be a dense float32 tensor of B*H*W elements")
+        li, ri = image_desc(lb), image_desc(rb)
+        check(self._lib.bdis_match(self._h, ctypes.byref(li), ctypes.byref(ri),
+                                   ctypes.byref(params), out.data_ptr()), "bdis_match")
+        return out[0] if squeeze else out
+
+    def match_host(self, left, right, params: BdisParams = None, out=None):
+        """Host buffers in and out (numpy arrays or CPU tensors, pinned for DMA).
+
+        left/right: uint8 (H, W) or (B, H, W) dense; returns float32 of the
+        same shape. The call blocks until the result is in `out`."""
+        params = params if params is not None else default_params()
+        lt = torch.as_tensor(left)
+        rt = torch.as_tensor(right)
+        if lt.dtype != torch.uint8 or rt.dtype != torch.uint8 or lt.device.type != "cpu":
+            raise TypeError("match_host takes uint8 host images")
+        lt, rt = lt.contiguous(), rt.contiguous()
+        shape = lt.shape
+        b = 1 if lt.dim() == 2 else lt.shape[0]
+        h, w = lt.shape[-2], lt.shape[-1]
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32)
+        ot = torch.as_tensor(out)
+        if not (ot.is_contiguous() and ot.dtype == torch.float32 and ot.numel() == b * h * w):
+            raise ValueError("out must be a dense float32 host buffer of B*H*W elements")
+        check(self._lib.bdis_match_host(self._h, lt.data_ptr(), rt.data_ptr(), w, h, b,
+                                        ctypes.byref(params), ot.data_ptr()), "bdis_match_host")
+        return out
+
+
+# ------------------------------------------------------------------ steps
+
+def prepare_level0(left: torch.Tensor, right: torch.Tensor, stream=None):
+    lb, rb = _as_batch(left), _as_batch(right)
+    b, h, w = lb.shape
+    L0, R0, G0 = (torch.empty((b, h, w), dtype=torch.float32, device=left.device)
+                  for _ in range(3))
+    li, ri = image_desc(lb), image_desc(rb)
+    check(_lib.load().bdis_prepare_level0(ctypes.byref(li), ctypes.byref(ri), L0.data_ptr(),
+                                          R0.data_ptr(), G0.data_ptr(), _stream_ptr(stream)),
+          "bdis_prepare_level0")
+    return L0, R0, G0
+
+
+def pyramid_level(L: torch.Tensor, R: torch.Tensor, stream=None):
+    L, R = _as_batch(L).contiguous(), _as_batch(R).contiguous()
+    b, h, w = L.shape
+    dh, dw = (h + 1) // 2, (w + 1) // 2
+    L1, R1, G1 = (torch.empty((b, dh, dw), dtype=torch.float32, device=L.device)
+                  for _ in range(3))
+    check(_lib.load().bdis_pyramid_level(L.data_ptr(), R.data_ptr(), w, h, b, L1.data_ptr(),
+                                         R1.data_ptr(), G1.data_ptr(), _stream_ptr(stream)),
+          "bdis_pyramid_level")
+    return L1, R1, G1
+
+
+def search_level(L, R, G, coarse, params: BdisParams, debug: bool = True, stream=None) -> dict:
+    """Inverse search + posterior of every patch of one level.
+
+    Returns tensors shaped (B, ny, nx): d_star, weight and, with debug, u_init,
+    posterior, flags, n_valid and energies (B, ny, nx, s)."""
+    L, R, G = (_as_batch(t).contiguous() for t in (L, R, G))
+    b, h, w = L.shape
+    s, nx = grid(w, params.patch_size, params.overlap)
+    _, ny = grid(h, params.patch_size, params.overlap)
+    dev = L.device
+    f32 = dict(dtype=torch.float32, device=dev)
+    out = {"d_star": torch.empty((b, ny, nx), **f32), "weight": torch.empty((b, ny, nx), **f32)}
+    dbg = None
+    if debug:
+        out.update(u_init=torch.empty((b, ny, nx), **f32),
+                   posterior=torch.empty((b, ny, nx), **f32),
+                   energies=torch.empty((b, ny, nx, params.window_samples), **f32),
+                   flags=torch.empty((b, ny, nx), dtype=torch.uint8, device=dev),
+                   n_valid=torch.empty((b, ny, nx), dtype=torch.int32, device=dev))
+        dbg = BdisPatchDebug(out["u_init"].data_ptr(), out["posterior"].data_ptr(),
+                             out["energies"].data_ptr(), out["flags"].data_ptr(),
+                             out["n_valid"].data_ptr())
+    if coarse is not None:
+        coarse = _as_batch(coarse).contiguous()
+        cp, cw, ch = coarse.data_ptr(), coarse.shape[2], coarse.shape[1]
+    else:
+        cp, cw, ch = None, 0, 0
+    check(_lib.load().bdis_search_level(L.data_ptr(), R.data_ptr(), G.data_ptr(), w, h, b, cp, cw,
+                                        ch, ctypes.byref(params), out["d_star"].data_ptr(),
+                                        out["weight"].data_ptr(),
+                                        ctypes.byref(dbg) if dbg is not None else None,
+                                        _stream_ptr(stream)), "bdis_search_level")
+    return out
+
+
+def densify_level(shape, params: BdisParams, d_star, weight, coarse, is_finest, stream=None):
+    d_star, weight = _as_batch(d_star).contiguous(), _as_batch(weight).contiguous()
+    b = d_star.shape[0]
+    h, w = shape
+    out = torch.empty((b, h, w), dtype=torch.float32, device=d_star.device)
+    if coarse is not None:
+        coarse = _as_batch(coarse).contiguous()
+        cp, cw, ch = coarse.data_ptr(), coarse.shape[2], coarse.shape[1]
+    else:
+        cp, cw, ch = None, 0, 0
+    check(_lib.load().bdis_densify_level(w, h, b, ctypes.byref(params), d_star.data_ptr(),
+                                         weight.data_ptr(), cp, cw, ch, int(bool(is_finest)),
+                                         out.data_ptr(), _stream_ptr(stream)),
+          "bdis_densify_level")
+    return out
+
+
+def upsample(M, level, shape, stream=None):
+    M = _as_batch(M).contiguous()
+    b, mh, mw = M.shape
+    h, w = shape
+    out = torch.empty((b, h, w), dtype=torch.float32, device=M.device)
+    check(_lib.load().bdis_upsample(M.data_ptr(), mw, mh, level, w, h, b, out.data_ptr(),
+                                    _stream_ptr(stream)), "bdis_upsample")
+    return out

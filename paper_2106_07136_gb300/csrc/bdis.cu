@@ -1,0 +1,565 @@
+// bdis.cu -- C ABI, parameter checks, workspace and the coarse-to-fine driver
+// of the BDIS CUDA library (arXiv 2106.07136, Sec. 2).
+//
+// bdis_match enqueues, on the handle's stream:
+//   prepare_level0, (pyramid_level) x coarsest,
+//   then for l = coarsest .. finest: search(l), densify(l),
+//   and an upsample when finest > 0.
+// That is 1 + 2 * coarsest + 2 * (coarsest - finest + 1) (+1) launches per
+// batch, independent of the number of pairs in it.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "bdis_internal.cuh"
+
+struct bdis_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  // kernel timing (bdis_enable_timing)
+  bool timing = false;
+  struct Mark {
+    cudaEvent_t start, stop;
+    int cls;
+  };
+  std::vector<cudaEvent_t> event_pool;
+  std::vector<Mark> marks;
+};
+
+namespace bdis {
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+// Device workspace of one bdis_match call. Offsets from the workspace base.
+struct Layout {
+  int levels = 0;  // coarsest + 1
+  int lw[16] = {0}, lh[16] = {0};
+  size_t L[16] = {0}, R[16] = {0}, G[16] = {0}, D[16] = {0};
+  size_t d_star = 0, weight = 0;
+  size_t in_left = 0, in_right = 0, out = 0;  // host-path staging
+  size_t bytes = 0;
+};
+
+Layout plan(int w, int h, int count, const bdis_params &p, bool host_staging) {
+  Layout lay;
+  size_t off = 0;
+  auto take = [&](size_t n) {
+    size_t o = off;
+    off += align_up(n);
+    return o;
+  };
+  lay.levels = p.coarsest_scale + 1;
+  const int stride = grid_stride(p.patch_size, p.overlap);
+  size_t max_np = 0;
+  for (int l = 0; l < lay.levels; ++l) {
+    lay.lw[l] = level_dim(w, l);
+    lay.lh[l] = level_dim(h, l);
+    const size_t plane = (size_t)lay.lw[l] * lay.lh[l] * count * sizeof(float);
+    lay.L[l] = take(plane);
+    lay.R[l] = take(plane);
+    lay.G[l] = take(plane);
+    if (l >= p.finest_scale && l > 0) lay.D[l] = take(plane);
+    if (l >= p.finest_scale) {
+      size_t np = (size_t)grid_count(lay.lw[l], p.patch_size, stride) *
+                  grid_count(lay.lh[l], p.patch_size, stride);
+      if (np > max_np) max_np = np;
+    }
+  }
+  lay.d_star = take(max_np * count * sizeof(float));
+  lay.weight = take(max_np * count * sizeof(float));
+  if (host_staging) {
+    lay.in_left = take((size_t)w * h * count);
+    lay.in_right = take((size_t)w * h * count);
+    lay.out = take((size_t)w * h * count * sizeof(float));
+  }
+  lay.bytes = off;
+  return lay;
+}
+
+bdis_status ensure_workspace(bdis_handle *h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return BDIS_OK;
+  // The old block may still be read by work already on the stream.
+  if (h->ws) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return record_cuda(e);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    snprintf(g_last_error, sizeof g_last_error, "workspace of %zu bytes: %s", bytes,
+             cudaGetErrorString(e));
+    return BDIS_E_NOMEM;
+  }
+  h->ws = p;
+  h->ws_bytes = bytes;
+  return BDIS_OK;
+}
+
+bdis_status check_image(const bdis_image *im) {
+  if (!im || !im->data) return BDIS_E_INVALID_ARG;
+  if (im->width < 1 || im->height < 1 || im->count < 1) return BDIS_E_INVALID_ARG;
+  if (im->format != BDIS_U8 && im->format != BDIS_F32) return BDIS_E_INVALID_ARG;
+  const size_t es = im->format == BDIS_U8 ? 1 : 4;
+  if (im->pitch_bytes < (size_t)im->width * es || im->pitch_bytes % es) return BDIS_E_INVALID_ARG;
+  if (im->count > 1 && im->image_stride_bytes < im->pitch_bytes * (size_t)im->height)
+    return BDIS_E_INVALID_ARG;
+  if (im->count > 1 && im->image_stride_bytes % es) return BDIS_E_INVALID_ARG;
+  return BDIS_OK;
+}
+
+bdis_status check_pair(const bdis_image *l, const bdis_image *r) {
+  bdis_status s = check_image(l);
+  if (s != BDIS_OK) return s;
+  s = check_image(r);
+  if (s != BDIS_OK) return s;
+  if (l->width != r->width || l->height != r->height || l->count != r->count ||
+      l->format != r->format || l->pitch_bytes != r->pitch_bytes ||
+      (l->count > 1 && l->image_stride_bytes != r->image_stride_bytes))
+    return BDIS_E_INVALID_ARG;
+  return BDIS_OK;
+}
+
+bdis_status check_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BDIS_E_INVALID_ARG;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return BDIS_E_INVALID_ARG;
+  return BDIS_OK;
+}
+
+bdis_status check_geometry(int w, int h, const bdis_params &p) {
+  if (level_dim(w, p.coarsest_scale) < p.patch_size ||
+      level_dim(h, p.coarsest_scale) < p.patch_size)
+    return BDIS_E_INVALID_ARG;
+  return BDIS_OK;
+}
+
+cudaEvent_t take_event(bdis_handle *h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+// Bracket one launch with events when timing is on.
+struct Timed {
+  bdis_handle *h;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int cls;
+  Timed(bdis_handle *h_, int cls_) : h(h_), cls(cls_) {
+    if (h->timing) {
+      a = take_event(h);
+      b = take_event(h);
+      if (a && b) cudaEventRecord(a, h->stream);
+    }
+  }
+  ~Timed() {
+    if (a && b) {
+      cudaEventRecord(b, h->stream);
+      h->marks.push_back({a, b, cls});
+    } else {
+      if (a) h->event_pool.push_back(a);
+      if (b) h->event_pool.push_back(b);
+    }
+  }
+};
+
+// The whole method on device images already checked; `out` dense device.
+bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &right,
+                      const bdis_params &p, float *out, const Layout &lay) {
+  char *base = static_cast<char *>(h->ws);
+  auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
+  const int count = left.count;
+  cudaStream_t st = h->stream;
+  cudaError_t e;
+  {
+    Timed tm(h, 0);
+    e = launch_prepare_level0(left, right, F(lay.L[0]), F(lay.R[0]), F(lay.G[0]), st);
+  }
+  if (e != cudaSuccess) return record_cuda(e);
+  for (int l = 0; l < p.coarsest_scale; ++l) {
+    {
+      Timed tm(h, 1);
+      e = launch_pyramid_level(F(lay.L[l]), F(lay.R[l]), lay.lw[l], lay.lh[l], count,
+                               F(lay.L[l + 1]), F(lay.R[l + 1]), F(lay.G[l + 1]), st);
+    }
+    if (e != cudaSuccess) return record_cuda(e);
+  }
+  const float *coarse = nullptr;
+  int cw = 0, ch = 0;
+  for (int l = p.coarsest_scale; l >= p.finest_scale; --l) {
+    const int w = lay.lw[l], hh = lay.lh[l];
+    SearchArgs sa{};
+    fill_search_args(sa, w, hh, count, p);
+    sa.L = F(lay.L[l]);
+    sa.R = F(lay.R[l]);
+    sa.G = F(lay.G[l]);
+    sa.coarse = coarse;
+    sa.cw = cw;
+    sa.ch = ch;
+    sa.cplane = (long long)cw * ch;
+    sa.d_star = F(lay.d_star);
+    sa.weight = F(lay.weight);
+    {
+      Timed tm(h, 2);
+      e = launch_search(sa, st);
+    }
+    if (e != cudaSuccess) return record_cuda(e);
+    DensifyArgs da{};
+    fill_densify_args(da, w, hh, count, p);
+    da.d_star = F(lay.d_star);
+    da.weight = F(lay.weight);
+    da.coarse = coarse;
+    da.cw = cw;
+    da.ch = ch;
+    da.cplane = (long long)cw * ch;
+    da.is_finest = (l == p.finest_scale);
+    da.out = (l == 0) ? out : F(lay.D[l]);
+    {
+      Timed tm(h, 3);
+      e = launch_densify(da, st);
+    }
+    if (e != cudaSuccess) return record_cuda(e);
+    coarse = da.out;
+    cw = w;
+    ch = hh;
+  }
+  if (p.finest_scale > 0) {
+    Timed tm(h, 4);
+    e = launch_upsample(coarse, cw, ch, p.finest_scale, left.width, left.height, count, out, st);
+    if (e != cudaSuccess) return record_cuda(e);
+  }
+  return BDIS_OK;
+}
+
+bdis_status bind_device(const bdis_handle *h) {
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return record_cuda(e);
+  if (cur != h->device) {
+    e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return record_cuda(e);
+  }
+  return BDIS_OK;
+}
+
+}  // namespace
+
+bdis_status record_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return BDIS_OK;
+  snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e),
+           cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? BDIS_E_NOMEM : BDIS_E_CUDA;
+}
+
+bdis_status check_params(const bdis_params *p) {
+  if (!p) return BDIS_E_INVALID_ARG;
+  if (p->patch_size < 1 || !(p->overlap >= 0.f && p->overlap < 1.f) || p->iterations < 0 ||
+      p->finest_scale < 0 || p->finest_scale > p->coarsest_scale || p->window_samples < 1 ||
+      p->window_samples % 2 == 0 || !(p->sigma_r > 0.f) || !(p->sigma_s > 0.f) ||
+      !(p->window_step >= 0.f) || !(p->gamma >= 0.f && p->gamma <= 1.f))
+    return BDIS_E_INVALID_ARG;
+  if (p->patch_size < 4 || p->patch_size > kMaxPatch || p->window_samples > kMaxWindow ||
+      p->coarsest_scale > 15)
+    return BDIS_E_UNSUPPORTED;
+  return BDIS_OK;
+}
+
+}  // namespace bdis
+
+using namespace bdis;
+
+extern "C" {
+
+void bdis_default_params(bdis_params *p) {
+  if (!p) return;
+  p->patch_size = 8;
+  p->overlap = 0.75f;
+  p->iterations = 12;
+  p->coarsest_scale = 4;
+  p->finest_scale = 0;
+  p->sigma_r = 4.f;
+  p->sigma_s = 4.f;
+  p->window_samples = 5;
+  p->window_step = 0.5f;
+  p->gamma = 0.75f;
+  p->normalize = 1;
+}
+
+const char *bdis_status_string(bdis_status s) {
+  switch (s) {
+    case BDIS_OK: return "ok";
+    case BDIS_E_INVALID_ARG: return "invalid argument";
+    case BDIS_E_NOMEM: return "out of memory";
+    case BDIS_E_CUDA: return "CUDA error";
+    case BDIS_E_TIMEOUT: return "timeout";
+    case BDIS_E_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *bdis_last_error_string(void) { return g_last_error; }
+
+int bdis_version(void) { return (1 << 16) | 0; }
+
+bdis_status bdis_level_dims(int width, int height, int level, int *lw, int *lh) {
+  if (width < 1 || height < 1 || level < 0 || level > 30 || !lw || !lh) return BDIS_E_INVALID_ARG;
+  *lw = level_dim(width, level);
+  *lh = level_dim(height, level);
+  return BDIS_OK;
+}
+
+bdis_status bdis_grid(int n, int patch_size, float overlap, int *stride, int *count) {
+  if (n < 1 || patch_size < 1 || !(overlap >= 0.f && overlap < 1.f) || !stride || !count)
+    return BDIS_E_INVALID_ARG;
+  *stride = grid_stride(patch_size, overlap);
+  *count = grid_count(n, patch_size, *stride);
+  return BDIS_OK;
+}
+
+bdis_status bdis_patch_count(int width, int height, const bdis_params *p, int64_t *total) {
+  bdis_status s = check_params(p);
+  if (s != BDIS_OK) return s;
+  if (!total || width < 1 || height < 1) return BDIS_E_INVALID_ARG;
+  s = check_geometry(width, height, *p);
+  if (s != BDIS_OK) return s;
+  const int stride = grid_stride(p->patch_size, p->overlap);
+  int64_t t = 0;
+  for (int l = p->finest_scale; l <= p->coarsest_scale; ++l)
+    t += (int64_t)grid_count(level_dim(width, l), p->patch_size, stride) *
+         grid_count(level_dim(height, l), p->patch_size, stride);
+  *total = t;
+  return BDIS_OK;
+}
+
+bdis_status bdis_create(bdis_handle **out, int device, void *stream) {
+  if (!out) return BDIS_E_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return record_cuda(e);
+  if (device < 0 || device >= n) return BDIS_E_INVALID_ARG;
+  bdis_handle *h = new (std::nothrow) bdis_handle();
+  if (!h) return BDIS_E_NOMEM;
+  h->device = device;
+  h->stream = static_cast<cudaStream_t>(stream);
+  *out = h;
+  return BDIS_OK;
+}
+
+bdis_status bdis_reserve(bdis_handle *h, int width, int height, int count, const bdis_params *p) {
+  if (!h || width < 1 || height < 1 || count < 1) return BDIS_E_INVALID_ARG;
+  bdis_status s = check_params(p);
+  if (s != BDIS_OK) return s;
+  s = check_geometry(width, height, *p);
+  if (s != BDIS_OK) return s;
+  s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  return ensure_workspace(h, plan(width, height, count, *p, false).bytes);
+}
+
+size_t bdis_workspace_bytes(const bdis_handle *h) { return h ? h->ws_bytes : 0; }
+
+void bdis_destroy(bdis_handle *h) {
+  if (!h) return;
+  if (bind_device(h) == BDIS_OK) {
+    cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    for (auto &m : h->marks) {
+      cudaEventDestroy(m.start);
+      cudaEventDestroy(m.stop);
+    }
+    for (auto e : h->event_pool) cudaEventDestroy(e);
+  }
+  delete h;
+}
+
+bdis_status bdis_enable_timing(bdis_handle *h, int on) {
+  if (!h) return BDIS_E_INVALID_ARG;
+  h->timing = on != 0;
+  return BDIS_OK;
+}
+
+bdis_status bdis_read_timing(bdis_handle *h, bdis_timing *out) {
+  if (!h || !out) return BDIS_E_INVALID_ARG;
+  bdis_status s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  for (int c = 0; c < BDIS_TIMING_CLASSES; ++c) {
+    out->ms[c] = 0.0;
+    out->launches[c] = 0;
+  }
+  cudaError_t err = cudaSuccess;
+  for (auto &m : h->marks) {
+    cudaError_t e = cudaEventSynchronize(m.stop);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, m.start, m.stop);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    if (m.cls >= 0 && m.cls < BDIS_TIMING_CLASSES) {
+      out->ms[m.cls] += ms;
+      out->launches[m.cls] += 1;
+    }
+    h->event_pool.push_back(m.start);
+    h->event_pool.push_back(m.stop);
+  }
+  h->marks.clear();
+  return record_cuda(err);
+}
+
+bdis_status bdis_match(bdis_handle *h, const bdis_image *left, const bdis_image *right,
+                       const bdis_params *p, float *disparity_out) {
+  if (!h || !disparity_out) return BDIS_E_INVALID_ARG;
+  bdis_status s = check_pair(left, right);
+  if (s != BDIS_OK) return s;
+  s = check_params(p);
+  if (s != BDIS_OK) return s;
+  s = check_geometry(left->width, left->height, *p);
+  if (s != BDIS_OK) return s;
+  s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  if (check_device_ptr(left->data) != BDIS_OK || check_device_ptr(right->data) != BDIS_OK ||
+      check_device_ptr(disparity_out) != BDIS_OK)
+    return BDIS_E_INVALID_ARG;
+  const Layout lay = plan(left->width, left->height, left->count, *p, false);
+  s = ensure_workspace(h, lay.bytes);
+  if (s != BDIS_OK) return s;
+  return run_match(h, *left, *right, *p, disparity_out, lay);
+}
+
+bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right, int width,
+                            int height, int count, const bdis_params *p, float *disparity_out) {
+  if (!h || !left || !right || !disparity_out || width < 1 || height < 1 || count < 1)
+    return BDIS_E_INVALID_ARG;
+  bdis_status s = check_params(p);
+  if (s != BDIS_OK) return s;
+  s = check_geometry(width, height, *p);
+  if (s != BDIS_OK) return s;
+  s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  const Layout lay = plan(width, height, count, *p, true);
+  s = ensure_workspace(h, lay.bytes);
+  if (s != BDIS_OK) return s;
+  char *base = static_cast<char *>(h->ws);
+  const size_t in_bytes = (size_t)width * height * count;
+  cudaError_t e = cudaMemcpyAsync(base + lay.in_left, left, in_bytes, cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + lay.in_right, right, in_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return record_cuda(e);
+  bdis_image L{base + lay.in_left, width, height, (size_t)width, (size_t)width * height, count,
+               BDIS_U8};
+  bdis_image R = L;
+  R.data = base + lay.in_right;
+  float *dout = reinterpret_cast<float *>(base + lay.out);
+  s = run_match(h, L, R, *p, dout, lay);
+  if (s != BDIS_OK) return s;
+  e = cudaMemcpyAsync(disparity_out, dout, in_bytes * sizeof(float), cudaMemcpyDeviceToHost,
+                      h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return record_cuda(e);
+}
+
+bdis_status bdis_prepare_level0(const bdis_image *left, const bdis_image *right, float *L0,
+                                float *R0, float *G0, void *stream) {
+  bdis_status s = check_pair(left, right);
+  if (s != BDIS_OK) return s;
+  if (!L0 || !R0 || !G0 || left->width < 2 || left->height < 2) return BDIS_E_INVALID_ARG;
+  return record_cuda(
+      launch_prepare_level0(*left, *right, L0, R0, G0, static_cast<cudaStream_t>(stream)));
+}
+
+bdis_status bdis_pyramid_level(const float *L, const float *R, int width, int height, int count,
+                               float *L1, float *R1, float *G1, void *stream) {
+  if (!L || !R || !L1 || !R1 || !G1 || width < 3 || height < 3 || count < 1)
+    return BDIS_E_INVALID_ARG;
+  return record_cuda(launch_pyramid_level(L, R, width, height, count, L1, R1, G1,
+                                          static_cast<cudaStream_t>(stream)));
+}
+
+bdis_status bdis_search_level(const float *L, const float *R, const float *G, int width,
+                              int height, int count, const float *coarse, int coarse_width,
+                              int coarse_height, const bdis_params *p, float *d_star,
+                              float *weight, const bdis_patch_debug *dbg, void *stream) {
+  bdis_status s = check_params(p);
+  if (s != BDIS_OK) return s;
+  if (!L || !R || !G || !d_star || !weight || count < 1 || width < p->patch_size ||
+      height < p->patch_size)
+    return BDIS_E_INVALID_ARG;
+  if (coarse && (coarse_width < 1 || coarse_height < 1)) return BDIS_E_INVALID_ARG;
+  SearchArgs a{};
+  fill_search_args(a, width, height, count, *p);
+  a.L = L;
+  a.R = R;
+  a.G = G;
+  a.coarse = coarse;
+  a.cw = coarse ? coarse_width : 0;
+  a.ch = coarse ? coarse_height : 0;
+  a.cplane = (long long)a.cw * a.ch;
+  a.d_star = d_star;
+  a.weight = weight;
+  if (dbg) {
+    a.u_init = dbg->u_init;
+    a.posterior = dbg->posterior;
+    a.energies = dbg->energies;
+    a.flags = dbg->flags;
+    a.n_valid = dbg->n_valid;
+  }
+  return record_cuda(launch_search(a, static_cast<cudaStream_t>(stream)));
+}
+
+bdis_status bdis_densify_level(int width, int height, int count, const bdis_params *p,
+                               const float *d_star, const float *weight, const float *coarse,
+                               int coarse_width, int coarse_height, int is_finest, float *out,
+                               void *stream) {
+  bdis_status s = check_params(p);
+  if (s != BDIS_OK) return s;
+  if (!d_star || !weight || !out || count < 1 || width < p->patch_size ||
+      height < p->patch_size)
+    return BDIS_E_INVALID_ARG;
+  if (coarse && (coarse_width < 1 || coarse_height < 1)) return BDIS_E_INVALID_ARG;
+  DensifyArgs a{};
+  fill_densify_args(a, width, height, count, *p);
+  a.d_star = d_star;
+  a.weight = weight;
+  a.coarse = coarse;
+  a.cw = coarse ? coarse_width : 0;
+  a.ch = coarse ? coarse_height : 0;
+  a.cplane = (long long)a.cw * a.ch;
+  a.is_finest = is_finest ? 1 : 0;
+  a.out = out;
+  return record_cuda(launch_densify(a, static_cast<cudaStream_t>(stream)));
+}
+
+bdis_status bdis_upsample(const float *map, int map_width, int map_height, int level, int width,
+                          int height, int count, float *out, void *stream) {
+  if (!map || !out || map_width < 1 || map_height < 1 || level < 0 || level > 15 || width < 1 ||
+      height < 1 || count < 1)
+    return BDIS_E_INVALID_ARG;
+  return record_cuda(launch_upsample(map, map_width, map_height, level, width, height, count, out,
+                                     static_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

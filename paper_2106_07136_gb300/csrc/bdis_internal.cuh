@@ -1,0 +1,113 @@
+// bdis_internal.cuh -- shared declarations of the BDIS CUDA library.
+//
+// The library is the GB300 (sm_103a) implementation of Bayesian Dense Inverse
+// Search (arXiv 2106.07136). Kernels live in pyramid.cu (Sec. 2.1 pyramid and
+// template gradient), search.cu (Eq. 1 inverse search with the Eqs. 3-4
+// posterior) and densify.cu (Sec. 2.3 Gaussian-mask fusion); bdis.cu holds the
+// C ABI, parameter checks, the workspace and the coarse-to-fine driver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "bdis.h"
+
+namespace bdis {
+
+// Saddle tolerance: a patch is dropped when another window sample beats the
+// centre by more than this fraction of max(E_centre, 1) (Sec. 2.2 filter).
+constexpr float kSaddleTau = 1e-6f;
+// A patch is flat (no update) when its Hessian is at most this much per pixel.
+constexpr float kFlatEps = 1e-4f;
+// Largest window the search kernel keeps track of.
+constexpr int kMaxWindow = 15;
+// Largest patch side (one patch per group of at most 32 lanes).
+constexpr int kMaxPatch = 32;
+
+constexpr uint8_t kFlagFlat = 1, kFlagDiverged = 2, kFlagSaddle = 4, kFlagGamma = 8,
+                  kFlagEmpty = 16;
+constexpr uint8_t kDropFlags = kFlagDiverged | kFlagSaddle | kFlagGamma | kFlagEmpty;
+
+__host__ __device__ inline int level_dim(int n, int level) {
+  for (int l = 0; l < level; ++l) n = (n + 1) / 2;
+  return n;
+}
+
+// Stride from size and overlap, rounded in double so that the host and any
+// caller that computes in double agree on every representable overlap.
+inline int grid_stride(int ps, float overlap) {
+  double s = ps * (1.0 - (double)overlap) + 0.5;
+  int si = (int)s;
+  if ((double)si > s) --si;  // floor for positive values
+  return si < 1 ? 1 : si;
+}
+
+inline int grid_count(int n, int ps, int stride) {
+  if (n < ps) return 0;
+  return (n - ps + stride - 1) / stride + 1;
+}
+
+__host__ __device__ __forceinline__ int grid_origin(int i, int count, int n, int ps, int stride) {
+  return (i == count - 1) ? n - ps : i * stride;
+}
+
+// Smallest valid-pixel count that passes the gamma test, decided in double.
+inline int gamma_min_count(float gamma, int ps) {
+  const double need = (double)gamma * (double)(ps * ps);
+  int n = 0;
+  while (n <= ps * ps && (double)n < need) ++n;
+  return n;
+}
+
+struct SearchArgs {
+  const float *L, *R, *G;
+  int w, h;
+  long long plane;  // w * h
+  const float *coarse;
+  int cw, ch;
+  long long cplane;
+  int ps, stride, nx, ny, np;
+  long long total;  // count * np
+  int iters, s;
+  float step, kappa;
+  int nmin_valid, normalize;
+  float *d_star, *weight;
+  float *u_init, *posterior, *energies;
+  uint8_t *flags;
+  int32_t *n_valid;
+};
+
+struct DensifyArgs {
+  int w, h;
+  long long plane;
+  long long total;  // count * plane
+  int ps, stride, nx, ny, np;
+  float two_s2;
+  const float *d_star, *weight;
+  const float *coarse;
+  int cw, ch;
+  long long cplane;
+  int is_finest;
+  float *out;
+};
+
+// Launchers (return the launch error, if any).
+cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &right, float *L0,
+                                  float *R0, float *G0, cudaStream_t st);
+cudaError_t launch_pyramid_level(const float *L, const float *R, int w, int h, int count,
+                                 float *L1, float *R1, float *G1, cudaStream_t st);
+cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
+cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st);
+cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, int h, int count,
+                            float *out, cudaStream_t st);
+
+// Fill SearchArgs / DensifyArgs geometry from parameters (host).
+void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p);
+void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_params &p);
+
+// Record a CUDA error for bdis_last_error_string() and map it to a status.
+bdis_status record_cuda(cudaError_t e);
+bdis_status check_params(const bdis_params *p);
+
+}  // namespace bdis

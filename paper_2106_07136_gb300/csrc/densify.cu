@@ -1,0 +1,150 @@
+// densify.cu -- fusion of the patch disparities into a dense map (Sec. 2.3).
+//
+// Each pixel gathers its covering patches straight from the regular grid (no
+// scatter, no atomics): w = weight_k * m(x - x0_k) * m(y - y0_k), where the
+// Gaussian mask m (Eq. 5, sigma_s) is separable and depends only on the
+// position inside the patch, so it is tabulated once per block. The pixel's
+// disparity is sum w D*_k / sum w (the normalised form of Eq. 2 with the
+// combined posterior as weight). Pixels without a kept patch are NaN at the
+// finest level (Sec. 3.2: not estimated); coarser levels carry the value
+// their patches started from.
+//
+// Roofline: one thread per pixel; reads (ps/stride)^2 patch records per
+// pixel, mostly from L1/L2 (neighbouring pixels share patches); DRAM bytes per
+// pixel: 4 written plus the patch arrays (8 B per patch) read once.
+#include "bdis_internal.cuh"
+
+namespace bdis {
+namespace {
+
+__device__ __forceinline__ float bilinear_clamped(const float *M, int w, int h, float x,
+                                                  float y) {
+  x = fminf(fmaxf(x, 0.f), (float)(w - 1));
+  y = fminf(fmaxf(y, 0.f), (float)(h - 1));
+  const int x0 = (int)floorf(x), y0 = (int)floorf(y);
+  const int x1 = min(x0 + 1, w - 1), y1 = min(y0 + 1, h - 1);
+  const float tx = x - x0, ty = y - y0;
+  const float top = (1.f - tx) * __ldg(M + (size_t)y0 * w + x0) + tx * __ldg(M + (size_t)y0 * w + x1);
+  const float bot = (1.f - tx) * __ldg(M + (size_t)y1 * w + x0) + tx * __ldg(M + (size_t)y1 * w + x1);
+  return (1.f - ty) * top + ty * bot;
+}
+
+// Patches covering coordinate x along one axis: the regular ones
+// [lo, hi] (indices <= n - 2) plus the last one (origin n_px - ps) if it covers.
+__device__ __forceinline__ void cover_range(int x, int n_px, int ps, int stride, int n, int &lo,
+                                            int &hi, int &last) {
+  const int a = x - ps + 1;
+  lo = a <= 0 ? 0 : (a + stride - 1) / stride;
+  hi = min(x / stride, n - 2);
+  last = (x >= n_px - ps) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
+  __shared__ float mask[kMaxPatch];
+  if (threadIdx.x < a.ps) {
+    const float m = (float)threadIdx.x - (a.ps - 1) * 0.5f;
+    mask[threadIdx.x] = expf(-(m * m) / a.two_s2);
+  }
+  __syncthreads();
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.total) return;
+  const int b = (int)(idx / a.plane);
+  const int rem = (int)(idx - (long long)b * a.plane);
+  const int y = rem / a.w, x = rem - (rem / a.w) * a.w;
+  int ilo, ihi, ilast, jlo, jhi, jlast;
+  cover_range(x, a.w, a.ps, a.stride, a.nx, ilo, ihi, ilast);
+  cover_range(y, a.h, a.ps, a.stride, a.ny, jlo, jhi, jlast);
+  const float *wp = a.weight + (long long)b * a.np;
+  const float *dp = a.d_star + (long long)b * a.np;
+  float num = 0.f, den = 0.f;
+  for (int jj = jlo; jj <= jhi + jlast; ++jj) {
+    const int j = jj > jhi ? a.ny - 1 : jj;
+    const int y0 = grid_origin(j, a.ny, a.h, a.ps, a.stride);
+    const float my = mask[y - y0];
+    for (int ii = ilo; ii <= ihi + ilast; ++ii) {
+      const int i = ii > ihi ? a.nx - 1 : ii;
+      const int x0 = grid_origin(i, a.nx, a.w, a.ps, a.stride);
+      const int kk = j * a.nx + i;
+      const float wk = __ldg(wp + kk);
+      if (wk > 0.f) {
+        const float q = wk * my * mask[x - x0];
+        num = fmaf(q, __ldg(dp + kk), num);
+        den += q;
+      }
+    }
+  }
+  float out;
+  if (den > 0.f)
+    out = num / den;
+  else if (a.is_finest)
+    out = __int_as_float(0x7fc00000);  // NaN: not estimated
+  else if (a.coarse)
+    out = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, x * 0.5f,
+                                 y * 0.5f);
+  else
+    out = 0.f;
+  a.out[idx] = out;
+}
+
+// Full-size map from level f: bilinear over finite neighbours with positive
+// weight, values times 2^f.
+__global__ void upsample_kernel(const float *__restrict__ M, int mw, int mh, float scale, int w,
+                                int h, long long total, float *__restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const long long plane = (long long)w * h;
+  const int b = (int)(idx / plane);
+  const int rem = (int)(idx - (long long)b * plane);
+  const int y = rem / w, x = rem - (rem / w) * w;
+  const float *Mb = M + (long long)b * mw * mh;
+  float fx = fminf((float)x / scale, (float)(mw - 1));
+  float fy = fminf((float)y / scale, (float)(mh - 1));
+  const int x0 = (int)floorf(fx), y0 = (int)floorf(fy);
+  const int x1 = min(x0 + 1, mw - 1), y1 = min(y0 + 1, mh - 1);
+  const float tx = fx - x0, ty = fy - y0;
+  const float wt[4] = {(1.f - tx) * (1.f - ty), tx * (1.f - ty), (1.f - tx) * ty, tx * ty};
+  const float v[4] = {Mb[(size_t)y0 * mw + x0], Mb[(size_t)y0 * mw + x1],
+                      Mb[(size_t)y1 * mw + x0], Mb[(size_t)y1 * mw + x1]};
+  float s = 0.f, sw = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (wt[q] > 0.f && isfinite(v[q])) {
+      s += wt[q] * v[q];
+      sw += wt[q];
+    }
+  out[idx] = sw > 0.f ? scale * s / sw : __int_as_float(0x7fc00000);
+}
+
+}  // namespace
+
+void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_params &p) {
+  a.w = w;
+  a.h = h;
+  a.plane = (long long)w * h;
+  a.total = a.plane * count;
+  a.ps = p.patch_size;
+  a.stride = grid_stride(p.patch_size, p.overlap);
+  a.nx = grid_count(w, p.patch_size, a.stride);
+  a.ny = grid_count(h, p.patch_size, a.stride);
+  a.np = a.nx * a.ny;
+  a.two_s2 = 2.f * p.sigma_s * p.sigma_s;
+}
+
+cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
+  if (a.total == 0) return cudaSuccess;
+  const int threads = 256;
+  densify_kernel<<<(unsigned)((a.total + threads - 1) / threads), threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, int h, int count,
+                            float *out, cudaStream_t st) {
+  const long long total = (long long)w * h * count;
+  if (total == 0) return cudaSuccess;
+  const int threads = 256;
+  upsample_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
+      map, mw, mh, (float)(1 << level), w, h, total, out);
+  return cudaGetLastError();
+}
+
+}  // namespace bdis

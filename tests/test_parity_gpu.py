@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA kernels (through the C ABI) against the FP64 oracle.
+
+Stage tests feed both sides the same inputs (the oracle's own intermediates,
+cast to float32) and compare element by element; end-to-end tests run both
+on the same seeded pairs. Sizes span several patch tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2106_07136_gb300 as bd
+import synth
+from gpu_helpers import (DENSE_ATOL, DSTAR_ATOL, POST_ATOL, PYR_ATOL, assert_e2e, dev,
+                         explained_flag_mismatch, host)
+
+pytestmark = pytest.mark.gpu
+
+CFG1 = dict(patch_size=8, overlap=0.5, iterations=8, coarsest_scale=2, finest_scale=0,
+            gamma=0.25)
+CFG2 = dict(patch_size=8, overlap=0.75, iterations=12, coarsest_scale=4, finest_scale=0,
+            gamma=0.75)
+
+
+def params(orc, **kw):
+    return bd.default_params(**kw), orc.OracleParams.make(**kw)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return synth.make_cfg1()
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    return synth.make_cfg2()
+
+
+@pytest.fixture(scope="module")
+def matcher():
+    m = bd.Matcher()
+    yield m
+    m.close()
+
+
+# ---------------------------------------------------------------- pyramid
+
+@pytest.mark.parametrize("shape", [(120, 160), (61, 97), (480, 640)])
+def test_pyramid_and_gradient(orc, shape):
+    h, w = shape
+    rng = np.random.default_rng(h * w)
+    left = rng.integers(0, 256, (2, h, w), dtype=np.uint8)
+    right = rng.integers(0, 256, (2, h, w), dtype=np.uint8)
+    L, R, G = bd.prepare_level0(dev(left, torch.uint8), dev(right, torch.uint8))
+    for b in range(2):
+        np.testing.assert_array_equal(host(L)[b], left[b].astype(np.float32))
+        np.testing.assert_allclose(host(G)[b], orc.sobel_x(left[b]), atol=PYR_ATOL)
+    oL = [left[b].astype(np.float64) for b in range(2)]
+    oR = [right[b].astype(np.float64) for b in range(2)]
+    for lvl in range(1, 4):
+        L, R, G = bd.pyramid_level(L, R)
+        for b in range(2):
+            oL[b], oR[b] = orc.downsample(oL[b]), orc.downsample(oR[b])
+            assert host(L)[b].shape == oL[b].shape == (orc.level_dim(h, lvl),
+                                                        orc.level_dim(w, lvl))
+            np.testing.assert_allclose(host(L)[b], oL[b], atol=PYR_ATOL)
+            np.testing.assert_allclose(host(R)[b], oR[b], atol=PYR_ATOL)
+            np.testing.assert_allclose(host(G)[b], orc.sobel_x(oL[b]), atol=PYR_ATOL)
+
+
+def test_pitched_and_float_inputs(orc):
+    pair = synth.make_cfg1()
+    h, w = pair.shape
+    big = torch.zeros((h, w + 24), dtype=torch.uint8, device="cuda")
+    big[:, 3:3 + w] = dev(pair.left, torch.uint8)
+    bigr = torch.zeros_like(big)
+    bigr[:, 3:3 + w] = dev(pair.right, torch.uint8)
+    a = bd.prepare_level0(big[:, 3:3 + w], bigr[:, 3:3 + w])
+    b = bd.prepare_level0(dev(pair.left, torch.float32), dev(pair.right, torch.float32))
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+# ------------------------------------------------------- search + posterior
+
+def _search_stage(orc, pair, kw, levels):
+    gp, op = params(orc, **kw)
+    st = orc.match_stages(pair.left, pair.right, op)
+    for lvl in levels:
+        o = st["levels"][lvl]
+        coarse = None if o["coarse"] is None else dev(o["coarse"])
+        g = bd.search_level(dev(o["L"]), dev(o["R"]), dev(o["G"]), coarse, gp)
+        g = {k: host(v)[0] for k, v in g.items()}
+        np.testing.assert_allclose(g["u_init"], o["u_init"], atol=1e-4)
+        diff, explained = explained_flag_mismatch(o, g["flags"], gp.patch_size)
+        assert explained.all(), (lvl, np.argwhere(~explained)[:5])
+        assert diff.mean() < 2e-3, (lvl, int(diff.sum()))
+        same = ~diff & (o["flags"] & 2 == 0)
+        np.testing.assert_allclose(g["d_star"][same], o["d_star"][same], atol=DSTAR_ATOL)
+        np.testing.assert_array_equal(g["n_valid"][same], o["n_valid"][same])
+        np.testing.assert_allclose(g["posterior"][same], o["posterior"][same], atol=POST_ATOL)
+        np.testing.assert_allclose(g["weight"][same], o["weight"][same], atol=POST_ATOL)
+        e_scale = np.maximum(np.abs(o["energies"][same]), 1.0)
+        assert np.all(np.abs(g["energies"][same] - o["energies"][same]) <= 1e-4 * e_scale)
+
+
+def test_search_stage_cfg1(orc, cfg1):
+    _search_stage(orc, cfg1, CFG1, levels=[2, 1, 0])
+
+
+@pytest.mark.parametrize("ps", [8, 12])
+def test_search_stage_cfg2(orc, cfg2, ps):
+    _search_stage(orc, cfg2, dict(CFG2, patch_size=ps), levels=[4, 2, 0])
+
+
+@pytest.mark.parametrize("kw", [dict(normalize=0), dict(window_samples=3, window_step=1.0),
+                                dict(window_samples=1), dict(iterations=0),
+                                dict(patch_size=5, overlap=0.4), dict(patch_size=16),
+                                dict(patch_size=4, overlap=0.0), dict(patch_size=32,
+                                                                      coarsest_scale=1)])
+def test_search_stage_variants(orc, cfg1, kw):
+    _search_stage(orc, cfg1, dict(CFG1, **kw), levels=[min(kw.get("coarsest_scale", 2), 1), 0])
+
+
+# ----------------------------------------------------------------- densify
+
+@pytest.mark.parametrize("lvl,finest", [(2, False), (1, False), (0, True)])
+def test_densify_stage(orc, cfg1, lvl, finest):
+    gp, op = params(orc, **CFG1)
+    st = orc.match_stages(cfg1.left, cfg1.right, op)
+    o = st["levels"][lvl]
+    rng = np.random.default_rng(lvl)
+    weight = o["weight"].copy()
+    weight[rng.uniform(size=weight.shape) < 0.3] = 0.0  # force uncovered pixels
+    ref = orc.densify_level(o["L"].shape, op, o["d_star"], weight, o["coarse"], finest)
+    coarse = None if o["coarse"] is None else dev(o["coarse"])
+    out = host(bd.densify_level(o["L"].shape, gp, dev(o["d_star"]), dev(weight), coarse,
+                                finest))[0]
+    assert np.array_equal(np.isnan(out), np.isnan(ref))
+    np.testing.assert_allclose(out[~np.isnan(ref)], ref[~np.isnan(ref)], atol=DENSE_ATOL)
+
+
+def test_upsample_stage(orc):
+    rng = np.random.default_rng(9)
+    M = rng.uniform(0, 10, (31, 41))
+    M[rng.uniform(size=M.shape) < 0.1] = np.nan
+    for f in (1, 2):
+        shape = (31 * 2 ** f - 3, 41 * 2 ** f - 1)
+        ref = orc.upsample(M, f, shape)
+        out = host(bd.upsample(dev(M), f, shape))[0]
+        assert np.array_equal(np.isnan(out), np.isnan(ref))
+        np.testing.assert_allclose(out[~np.isnan(ref)], ref[~np.isnan(ref)], atol=1e-4)
+
+
+# -------------------------------------------------------------- end to end
+
+def test_e2e_cfg1(orc, cfg1, matcher):
+    gp, op = params(orc, **CFG1)
+    ref = orc.match(cfg1.left, cfg1.right, op)
+    out = host(matcher.match(dev(cfg1.left, torch.uint8), dev(cfg1.right, torch.uint8), gp))
+    assert_e2e(out, ref, "cfg1")
+
+
+@pytest.mark.parametrize("ps", [8, 12])
+def test_e2e_cfg2(orc, cfg2, matcher, ps):
+    gp, op = params(orc, **dict(CFG2, patch_size=ps))
+    ref = orc.match(cfg2.left, cfg2.right, op)
+    out = host(matcher.match(dev(cfg2.left, torch.uint8), dev(cfg2.right, torch.uint8), gp))
+    assert_e2e(out, ref, f"cfg2 ps{ps}")
+
+
+@pytest.mark.parametrize("shape,kw", [
+    ((61, 97), dict(CFG1)),
+    ((45, 77), dict(CFG1, patch_size=12, overlap=0.75, coarsest_scale=1)),
+    ((120, 160), dict(CFG1, finest_scale=1)),
+    ((33, 40), dict(CFG1, coarsest_scale=0)),
+])
+def test_e2e_ragged_and_variants(orc, shape, kw, matcher):
+    h, w = shape
+    pair = synth.make_cfg1(seed=synth.stereo.pair_seed(1, 7), h=h, w=w)
+    gp, op = params(orc, **kw)
+    ref = orc.match(pair.left, pair.right, op)
+    out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
+    assert_e2e(out, ref, str((shape, kw)))
+
+
+def test_batch_equals_single_pairs(orc, matcher):
+    L, R, _ = synth.make_batch(1, 3)
+    gp, op = params(orc, **CFG1)
+    outb = host(matcher.match(dev(L, torch.uint8), dev(R, torch.uint8), gp))
+    for b in range(3):
+        single = host(matcher.match(dev(L[b], torch.uint8), dev(R[b], torch.uint8), gp))
+        assert np.array_equal(np.isnan(single), np.isnan(outb[b]))
+        assert np.array_equal(single[~np.isnan(single)], outb[b][~np.isnan(single)])
+        assert_e2e(outb[b], orc.match(L[b], R[b], op), f"pair {b}")
+
+
+def test_match_host_equals_device(matcher):
+    L, R, _ = synth.make_batch(1, 2)
+    gp = bd.default_params(**CFG1)
+    dv = host(matcher.match(dev(L, torch.uint8), dev(R, torch.uint8), gp))
+    out = matcher.match_host(torch.from_numpy(L).pin_memory(), torch.from_numpy(R).pin_memory(),
+                             gp).numpy()
+    assert np.array_equal(np.isnan(dv), np.isnan(out))
+    assert np.array_equal(dv[~np.isnan(dv)], out[~np.isnan(out)])
+
+
+# ----------------------------------------------------- pins on the GPU path
+
+@pytest.mark.parametrize("k", [1, 3, 5])
+def test_gpu_integer_shift(matcher, k):
+    pair = synth.make_integer_shift_pair(48, 64, k)
+    gp = bd.default_params(**dict(CFG2, coarsest_scale=2, gamma=0.25))
+    out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
+    est = np.isfinite(out) & np.isfinite(pair.disp)
+    assert est.sum() > 0.95 * np.isfinite(pair.disp).sum()
+    assert np.max(np.abs(out[est] - k)) < 1e-3
+
+
+@pytest.mark.parametrize("d", [0.25, 0.5, 2.37])
+def test_gpu_linear_texture(matcher, d):
+    pair = synth.make_linear_texture_pair(48, 64, d, a0=0.5, a1=2.0)
+    gp = bd.default_params(**dict(CFG2, coarsest_scale=2, gamma=0.25, iterations=20))
+    out = host(matcher.match(dev(pair.left), dev(pair.right), gp))
+    inner = out[8:-8, 8:-8]
+    assert np.all(np.isfinite(inner))
+    assert np.max(np.abs(inner - d)) < 1e-3
+
+
+def test_gpu_flat_pair(matcher):
+    pair = synth.make_flat_pair(48, 64)
+    gp = bd.default_params(**dict(CFG2, coarsest_scale=2, gamma=0.25))
+    out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
+    assert np.all(out == 0.0)
+    o = synth.make_flat_pair(24, 32)
+    g = bd.search_level(dev(o.left), dev(o.right), torch.zeros((24, 32), device="cuda"), None,
+                        gp)
+    assert torch.all(g["flags"] == 1) and torch.all(g["posterior"] == 0.2)
+
+
+# ------------------------------------------------------------------ errors
+
+def test_argument_errors(matcher):
+    l = torch.zeros((40, 50), dtype=torch.uint8, device="cuda")
+    r = torch.zeros((40, 51), dtype=torch.uint8, device="cuda")
+    with pytest.raises(bd.BdisError, match="invalid argument"):
+        matcher.match(l, r)
+    with pytest.raises(bd.BdisError, match="invalid argument"):
+        matcher.match(l, l, bd.default_params(coarsest_scale=4))  # 40/16 < 8
+    with pytest.raises(bd.BdisError, match="invalid argument"):
+        matcher.match(l.cpu(), l.cpu(), bd.default_params(coarsest_scale=1))  # host pointers
+    out = matcher.match(l, l, bd.default_params(coarsest_scale=1, gamma=0.25))
+    assert torch.all(out == 0.0)
