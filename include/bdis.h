@@ -24,9 +24,11 @@
  *   - `void *stream` is a cudaStream_t (NULL = the legacy default stream).
  *   - A handle is not thread-safe: use one handle per host thread/stream.
  *
- * Per-patch flag bits (bdis_patch_debug.flags) follow the oracle's: 1 flat
- * (no gradient energy, no update), 2 diverged, 4 saddle, 8 below gamma,
- * 16 no pixel valid at every window sample. Any bit but 1 drops the patch.
+ * Per-patch flag bits (bdis_patch_debug.flags): 1 flat (no gradient energy,
+ * no update), 2 diverged (moved more than the patch size from its start, or
+ * non-finite), 4 saddle (another window sample has lower energy), 8 below
+ * gamma, 16 no pixel valid at every window sample, 32 not converged (last
+ * update above 0.02 px). Any bit but 1 drops the patch.
  */
 #ifndef BDIS_H
 #define BDIS_H

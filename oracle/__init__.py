@@ -28,5 +28,6 @@ from .oracle import (  # noqa: F401
     FLAG_SADDLE,
     FLAG_GAMMA,
     FLAG_EMPTY,
+    FLAG_UNCONVERGED,
     DISCARD_FLAGS,
 )

@@ -63,12 +63,15 @@ enum {
     ORC_FLAG_DIVERGED = 2,  /* |D* - u_init| > patch size, or non-finite */
     ORC_FLAG_SADDLE = 4,    /* D* is not the minimum of its window (Sec. 2.2) */
     ORC_FLAG_GAMMA = 8,     /* valid-pixel fraction below gamma (Sec. 3) */
-    ORC_FLAG_EMPTY = 16     /* no pixel valid at every window sample */
+    ORC_FLAG_EMPTY = 16,    /* no pixel valid at every window sample */
+    ORC_FLAG_UNCONVERGED = 32 /* last update above ORC_CONVERGE_TOL (Sec. 3.2) */
 };
 
-/* Saddle tolerance (R7) and flat-patch threshold (R5). */
+/* Saddle tolerance (R7), flat-patch threshold (R5) and the largest final
+ * update, in pixels, of a patch that counts as converged (R8). */
 #define ORC_SADDLE_TAU 1e-6
 #define ORC_FLAT_EPS 1e-4
+#define ORC_CONVERGE_TOL 0.02
 
 /* ---------------------------------------------------------------- geometry */
 
@@ -206,7 +209,12 @@ typedef struct {
  *     valid at the current D; the step is the Gauss-Newton step of the
  *     normalised objective. A patch whose Hessian is below ORC_FLAT_EPS per
  *     pixel (or with no valid pixel) is flat and gets no further update.
- * R12: exactly `iterations` steps, no early exit other than flatness.
+ * R8: a patch that moves more than ps from its start has left its search
+ *     range and is abandoned there (no further steps, dropped); a patch
+ *     whose last step is still above ORC_CONVERGE_TOL has not converged and
+ *     is dropped (Sec. 3.2 discards the patches that do not converge).
+ * R12: exactly `iterations` steps, no early exit other than flatness and
+ *     leaving the search range.
  * energies[] receives s values (may be NULL). */
 void orc_search_patch(const double *L, const double *R, const double *G, int w, int h,
                       int x0, int y0, double u_init, const orc_params *p,
@@ -216,6 +224,7 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
     const int ps = p->patch_size;
     const int s = p->window_samples;
     double D = u_init;
+    double last_step = 0.0;
     int flags = 0;
 
     for (int it = 0; it < p->iterations; ++it) {
@@ -256,12 +265,15 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
             flags |= ORC_FLAG_FLAT;
             break;
         }
-        D += num / H;
+        last_step = num / H;
+        D += last_step;
         if (!isfinite(D)) break;
+        if (fabs(D - u_init) > (double)ps) break; /* R8: left the search range */
     }
 
-    /* R8: divergence */
+    /* R8: divergence and convergence */
     if (!isfinite(D) || fabs(D - u_init) > (double)ps) flags |= ORC_FLAG_DIVERGED;
+    if (fabs(last_step) > ORC_CONVERGE_TOL) flags |= ORC_FLAG_UNCONVERGED;
 
     /* R9: pixels valid at D* (their right sample is inside the image) */
     int n_valid = 0;
@@ -343,7 +355,8 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
     /* R9: gamma test on the pixels valid at D* (Sec. 3) */
     if ((double)n_valid < p->gamma * (double)(ps * ps)) flags |= ORC_FLAG_GAMMA;
 
-    int discard = flags & (ORC_FLAG_DIVERGED | ORC_FLAG_SADDLE | ORC_FLAG_GAMMA | ORC_FLAG_EMPTY);
+    int discard = flags & (ORC_FLAG_DIVERGED | ORC_FLAG_SADDLE | ORC_FLAG_GAMMA | ORC_FLAG_EMPTY |
+                           ORC_FLAG_UNCONVERGED);
     res->u_init = u_init;
     res->d_star = D;
     res->posterior = post;

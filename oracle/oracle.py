@@ -23,7 +23,8 @@ FLAG_DIVERGED = 2
 FLAG_SADDLE = 4
 FLAG_GAMMA = 8
 FLAG_EMPTY = 16
-DISCARD_FLAGS = FLAG_DIVERGED | FLAG_SADDLE | FLAG_GAMMA | FLAG_EMPTY
+FLAG_UNCONVERGED = 32
+DISCARD_FLAGS = FLAG_DIVERGED | FLAG_SADDLE | FLAG_GAMMA | FLAG_EMPTY | FLAG_UNCONVERGED
 
 
 class OracleParams(ctypes.Structure):

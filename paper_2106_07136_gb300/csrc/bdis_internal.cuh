@@ -20,14 +20,18 @@ namespace bdis {
 constexpr float kSaddleTau = 1e-6f;
 // A patch is flat (no update) when its Hessian is at most this much per pixel.
 constexpr float kFlatEps = 1e-4f;
+// Largest final update (px) of a patch that counts as converged; patches whose
+// last step is larger are dropped (Sec. 3.2 discards non-converged patches).
+constexpr float kConvergeTol = 0.02f;
 // Largest window the search kernel keeps track of.
 constexpr int kMaxWindow = 15;
 // Largest patch side (one patch per group of at most 32 lanes).
 constexpr int kMaxPatch = 32;
 
 constexpr uint8_t kFlagFlat = 1, kFlagDiverged = 2, kFlagSaddle = 4, kFlagGamma = 8,
-                  kFlagEmpty = 16;
-constexpr uint8_t kDropFlags = kFlagDiverged | kFlagSaddle | kFlagGamma | kFlagEmpty;
+                  kFlagEmpty = 16, kFlagUnconverged = 32;
+constexpr uint8_t kDropFlags =
+    kFlagDiverged | kFlagSaddle | kFlagGamma | kFlagEmpty | kFlagUnconverged;
 
 __host__ __device__ inline int level_dim(int n, int level) {
   for (int l = 0; l < level; ++l) n = (n + 1) / 2;

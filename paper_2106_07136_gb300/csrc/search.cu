@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
 
   // ---- inverse-search iterations (Eq. 1)
   float D = u0;
+  float last_step = 0.f;
   bool frozen = false, flat = false, have = false;
   unsigned prev = 0u;
   float gc[G];
@@ -161,8 +162,10 @@ __global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
     }
     const float S = group_sum<G>(acc);
     if (!frozen) {
-      D += (S - gcT) / H;
-      if (!isfinite(D)) frozen = true;
+      last_step = (S - gcT) / H;
+      D += last_step;
+      // non-finite, or left the search range: no further steps (dropped below)
+      if (!isfinite(D) || fabsf(D - u0) > (float)ps) frozen = true;
     }
   }
 
@@ -229,6 +232,7 @@ __global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
 
   uint8_t flags = flat ? kFlagFlat : 0;
   if (!fin || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
+  if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
   float post = 0.f;
   if (nc == 0) {
     flags |= kFlagEmpty;

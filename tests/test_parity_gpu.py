@@ -10,8 +10,8 @@ import torch
 
 import paper_2106_07136_gb300 as bd
 import synth
-from gpu_helpers import (DENSE_ATOL, DSTAR_ATOL, POST_ATOL, PYR_ATOL, assert_e2e, dev,
-                         explained_flag_mismatch, host)
+from gpu_helpers import (DENSE_ATOL, DROP, DSTAR_ATOL, POST_ATOL, PYR_ATOL, assert_e2e, dev,
+                         explained_flag_mismatch, host, oracle_unstable)
 
 pytestmark = pytest.mark.gpu
 
@@ -91,16 +91,23 @@ def _search_stage(orc, pair, kw, levels):
         g = bd.search_level(dev(o["L"]), dev(o["R"]), dev(o["G"]), coarse, gp)
         g = {k: host(v)[0] for k, v in g.items()}
         np.testing.assert_allclose(g["u_init"], o["u_init"], atol=1e-4)
-        diff, explained = explained_flag_mismatch(o, g["flags"], gp.patch_size)
+        unstable = oracle_unstable(orc, o, op)
+        assert unstable.mean() < 2e-3, (lvl, int(unstable.sum()))
+        diff, explained = explained_flag_mismatch(o, g["flags"], gp.patch_size, unstable)
         assert explained.all(), (lvl, np.argwhere(~explained)[:5])
         assert diff.mean() < 2e-3, (lvl, int(diff.sum()))
-        same = ~diff & (o["flags"] & 2 == 0)
-        np.testing.assert_allclose(g["d_star"][same], o["d_star"][same], atol=DSTAR_ATOL)
-        np.testing.assert_array_equal(g["n_valid"][same], o["n_valid"][same])
-        np.testing.assert_allclose(g["posterior"][same], o["posterior"][same], atol=POST_ATOL)
-        np.testing.assert_allclose(g["weight"][same], o["weight"][same], atol=POST_ATOL)
-        e_scale = np.maximum(np.abs(o["energies"][same]), 1.0)
-        assert np.all(np.abs(g["energies"][same] - o["energies"][same]) <= 1e-4 * e_scale)
+        kept = ~diff & ((o["flags"] & DROP) == 0) & ~unstable
+        assert np.array_equal(g["flags"][kept], o["flags"][kept])
+        np.testing.assert_allclose(g["d_star"][kept], o["d_star"][kept], atol=DSTAR_ATOL)
+        np.testing.assert_array_equal(g["n_valid"][kept], o["n_valid"][kept])
+        np.testing.assert_allclose(g["posterior"][kept], o["posterior"][kept], atol=POST_ATOL)
+        np.testing.assert_allclose(g["weight"][kept], o["weight"][kept], atol=POST_ATOL)
+        # E moves with D* (dE/dD ~ 2 sqrt(C E)); 1e-3 relative covers 1e-4 px of D*
+        e_scale = np.maximum(np.abs(o["energies"][kept]), 10.0)
+        rel = np.abs(g["energies"][kept] - o["energies"][kept]) / e_scale
+        assert rel.max() <= 1e-3, (lvl, float(rel.max()))
+        dropped = ~diff & ((o["flags"] & DROP) != 0)
+        assert np.all(g["weight"][dropped] == 0.0)
 
 
 def test_search_stage_cfg1(orc, cfg1):
@@ -250,3 +257,31 @@ def test_argument_errors(matcher):
         matcher.match(l.cpu(), l.cpu(), bd.default_params(coarsest_scale=1))  # host pointers
     out = matcher.match(l, l, bd.default_params(coarsest_scale=1, gamma=0.25))
     assert torch.all(out == 0.0)
+
+
+# ------------------------------------------- full sizes, bench launch shape
+
+def test_bench_launch_configuration(orc, matcher):
+    """The benchmark's launch: 128 pairs of 640x480 in one call (16 distinct
+    pairs tiled). Sampled pairs match the oracle; repeated pairs are
+    bit-identical wherever they sit in the batch."""
+    L, R, _ = synth.make_batch(2, 16)
+    Lb, Rb = np.concatenate([L] * 8), np.concatenate([R] * 8)
+    gp, op = params(orc, **CFG2)
+    out = host(matcher.match(dev(Lb, torch.uint8), dev(Rb, torch.uint8), gp))
+    for i in (0, 5):
+        assert_e2e(out[i], orc.match(L[i], R[i], op), f"batch pair {i}")
+    for i in (0, 5, 11):
+        for rep in (1, 7):
+            a, b = out[i], out[i + 16 * rep]
+            assert np.array_equal(np.isnan(a), np.isnan(b))
+            assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
+
+
+def test_full_hd_frame(orc, matcher):
+    pair = synth.make_cfg2(seed=synth.stereo.pair_seed(3, 0), h=1080, w=1920)
+    kw = dict(CFG2, coarsest_scale=5)
+    gp, op = params(orc, **kw)
+    ref = orc.match(pair.left, pair.right, op)
+    out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
+    assert_e2e(out, ref, "1920x1080")
