@@ -187,21 +187,32 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
  * The method's steps, one launch sequence each, on dense device batches of
  * `count` planes. bdis_match runs exactly these kernels. */
 
+/* The right view of every level is kept PACKED: two floats per pixel,
+ * (R[x], R[x+1] - R[x]), the difference 0 in the last column, so that the
+ * search interpolates with one 8-byte load. Packed planes are count x H x W
+ * x 2 floats and must be 8-byte aligned. */
+
 /* Level 0 (Sec. 2.1): gray levels as float and the template gradient.
- * L0, R0, G0: device, count x H x W float. G0 = Sobel-x / 8 of the left image
- * with a mirrored (reflect-101) border. */
+ * L0, G0: device, count x H x W float; R0: device, packed. G0 = Sobel-x / 8
+ * of the left image with a mirrored (reflect-101) border. */
 bdis_status bdis_prepare_level0(const bdis_image *left, const bdis_image *right, float *L0,
                                 float *R0, float *G0, void *stream);
 
 /* One pyramid step (Sec. 2.1): 5x5 binomial [1 4 6 4 1]/16 smoothing with a
  * reflect-101 border, keeping even samples, for both views; plus Sobel-x / 8
- * of the new left level. Inputs count x h x w; outputs count x ceil(h/2) x
- * ceil(w/2). */
+ * of the new left level. Inputs count x h x w (R, R1 packed); outputs count x
+ * ceil(h/2) x ceil(w/2). */
 bdis_status bdis_pyramid_level(const float *L, const float *R, int width, int height, int count,
                                float *L1, float *R1, float *G1, void *stream);
 
+/* Pack a plain right-view plane (count x h x w float) into the packed layout
+ * the search reads (for callers that bring their own pyramid). */
+bdis_status bdis_pack_right(const float *R, int width, int height, int count, float *R2,
+                            void *stream);
+
 /* Inverse search of every patch of one level (Eq. 1) with the posterior and
- * patch tests (Eqs. 3-4, Sec. 2.2, Sec. 3). L, R, G: count x h x w device.
+ * patch tests (Eqs. 3-4, Sec. 2.2, Sec. 3). L, G: count x h x w device; R:
+ * the packed right view of the level.
  * coarse: the next coarser dense map, count x ch x cw, or NULL at the
  * coarsest level (patches then start at 0); a patch starts from twice the
  * coarse map read bilinearly at half its centre. Outputs, count x n_patches

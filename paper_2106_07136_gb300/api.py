@@ -161,10 +161,11 @@ class Matcher:
 # ------------------------------------------------------------------ steps
 
 def prepare_level0(left: torch.Tensor, right: torch.Tensor, stream=None):
+    """Level 0: (L0, R0 packed (B, H, W, 2), G0)."""
     lb, rb = _as_batch(left), _as_batch(right)
     b, h, w = lb.shape
-    L0, R0, G0 = (torch.empty((b, h, w), dtype=torch.float32, device=left.device)
-                  for _ in range(3))
+    L0, G0 = (torch.empty((b, h, w), dtype=torch.float32, device=left.device) for _ in range(2))
+    R0 = torch.empty((b, h, w, 2), dtype=torch.float32, device=left.device)
     li, ri = image_desc(lb), image_desc(rb)
     check(_lib.load().bdis_prepare_level0(ctypes.byref(li), ctypes.byref(ri), L0.data_ptr(),
                                           R0.data_ptr(), G0.data_ptr(), _stream_ptr(stream)),
@@ -172,12 +173,31 @@ def prepare_level0(left: torch.Tensor, right: torch.Tensor, stream=None):
     return L0, R0, G0
 
 
+def _packed(R):
+    if R.dim() == 3:
+        R = R.unsqueeze(0)
+    if R.dim() != 4 or R.shape[-1] != 2:
+        raise ValueError("packed right planes are (B, H, W, 2)")
+    return R.contiguous()
+
+
+def pack_right(R: torch.Tensor, stream=None) -> torch.Tensor:
+    """(B, H, W) float32 right plane -> packed (B, H, W, 2)."""
+    R = _as_batch(R).contiguous()
+    b, h, w = R.shape
+    out = torch.empty((b, h, w, 2), dtype=torch.float32, device=R.device)
+    check(_lib.load().bdis_pack_right(R.data_ptr(), w, h, b, out.data_ptr(), _stream_ptr(stream)),
+          "bdis_pack_right")
+    return out
+
+
 def pyramid_level(L: torch.Tensor, R: torch.Tensor, stream=None):
-    L, R = _as_batch(L).contiguous(), _as_batch(R).contiguous()
+    """One pyramid step: (L, packed R) -> (L1, packed R1, G1)."""
+    L, R = _as_batch(L).contiguous(), _packed(R)
     b, h, w = L.shape
     dh, dw = (h + 1) // 2, (w + 1) // 2
-    L1, R1, G1 = (torch.empty((b, dh, dw), dtype=torch.float32, device=L.device)
-                  for _ in range(3))
+    L1, G1 = (torch.empty((b, dh, dw), dtype=torch.float32, device=L.device) for _ in range(2))
+    R1 = torch.empty((b, dh, dw, 2), dtype=torch.float32, device=L.device)
     check(_lib.load().bdis_pyramid_level(L.data_ptr(), R.data_ptr(), w, h, b, L1.data_ptr(),
                                          R1.data_ptr(), G1.data_ptr(), _stream_ptr(stream)),
           "bdis_pyramid_level")
@@ -185,11 +205,12 @@ def pyramid_level(L: torch.Tensor, R: torch.Tensor, stream=None):
 
 
 def search_level(L, R, G, coarse, params: BdisParams, debug: bool = True, stream=None) -> dict:
-    """Inverse search + posterior of every patch of one level.
+    """Inverse search + posterior of every patch of one level (R packed).
 
     Returns tensors shaped (B, ny, nx): d_star, weight and, with debug, u_init,
     posterior, flags, n_valid and energies (B, ny, nx, s)."""
-    L, R, G = (_as_batch(t).contiguous() for t in (L, R, G))
+    L, G = (_as_batch(t).contiguous() for t in (L, G))
+    R = _packed(R)
     b, h, w = L.shape
     s, nx = grid(w, params.patch_size, params.overlap)
     _, ny = grid(h, params.patch_size, params.overlap)

@@ -7,6 +7,7 @@
 //   and an upsample when finest > 0.
 // That is 1 + 2 * coarsest + 2 * (coarsest - finest + 1) (+1) launches per
 // batch, independent of the number of pairs in it.
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -65,7 +66,7 @@ Layout plan(int w, int h, int count, const bdis_params &p, bool host_staging) {
     lay.lh[l] = level_dim(h, l);
     const size_t plane = (size_t)lay.lw[l] * lay.lh[l] * count * sizeof(float);
     lay.L[l] = take(plane);
-    lay.R[l] = take(plane);
+    lay.R[l] = take(2 * plane);  // packed (R, R[x+1] - R[x])
     lay.G[l] = take(plane);
     if (l >= p.finest_scale && l > 0) lay.D[l] = take(plane);
     if (l >= p.finest_scale) {
@@ -193,19 +194,20 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
                       const bdis_params &p, float *out, const Layout &lay) {
   char *base = static_cast<char *>(h->ws);
   auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
+  auto F2 = [&](size_t off) { return reinterpret_cast<float2 *>(base + off); };
   const int count = left.count;
   cudaStream_t st = h->stream;
   cudaError_t e;
   {
     Timed tm(h, 0);
-    e = launch_prepare_level0(left, right, F(lay.L[0]), F(lay.R[0]), F(lay.G[0]), st);
+    e = launch_prepare_level0(left, right, F(lay.L[0]), F2(lay.R[0]), F(lay.G[0]), st);
   }
   if (e != cudaSuccess) return record_cuda(e);
   for (int l = 0; l < p.coarsest_scale; ++l) {
     {
       Timed tm(h, 1);
-      e = launch_pyramid_level(F(lay.L[l]), F(lay.R[l]), lay.lw[l], lay.lh[l], count,
-                               F(lay.L[l + 1]), F(lay.R[l + 1]), F(lay.G[l + 1]), st);
+      e = launch_pyramid_level(F(lay.L[l]), F2(lay.R[l]), lay.lw[l], lay.lh[l], count,
+                               F(lay.L[l + 1]), F2(lay.R[l + 1]), F(lay.G[l + 1]), st);
     }
     if (e != cudaSuccess) return record_cuda(e);
   }
@@ -216,7 +218,7 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
     SearchArgs sa{};
     fill_search_args(sa, w, hh, count, p);
     sa.L = F(lay.L[l]);
-    sa.R = F(lay.R[l]);
+    sa.R2 = F2(lay.R[l]);
     sa.G = F(lay.G[l]);
     sa.coarse = coarse;
     sa.cw = cw;
@@ -482,21 +484,34 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
   return record_cuda(e);
 }
 
+static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
+
 bdis_status bdis_prepare_level0(const bdis_image *left, const bdis_image *right, float *L0,
                                 float *R0, float *G0, void *stream) {
   bdis_status s = check_pair(left, right);
   if (s != BDIS_OK) return s;
-  if (!L0 || !R0 || !G0 || left->width < 2 || left->height < 2) return BDIS_E_INVALID_ARG;
-  return record_cuda(
-      launch_prepare_level0(*left, *right, L0, R0, G0, static_cast<cudaStream_t>(stream)));
+  if (!L0 || !R0 || !G0 || !aligned8(R0) || left->width < 2 || left->height < 2)
+    return BDIS_E_INVALID_ARG;
+  return record_cuda(launch_prepare_level0(*left, *right, L0, reinterpret_cast<float2 *>(R0), G0,
+                                           static_cast<cudaStream_t>(stream)));
 }
 
 bdis_status bdis_pyramid_level(const float *L, const float *R, int width, int height, int count,
                                float *L1, float *R1, float *G1, void *stream) {
-  if (!L || !R || !L1 || !R1 || !G1 || width < 3 || height < 3 || count < 1)
+  if (!L || !R || !L1 || !R1 || !G1 || !aligned8(R) || !aligned8(R1) || width < 3 ||
+      height < 3 || count < 1)
     return BDIS_E_INVALID_ARG;
-  return record_cuda(launch_pyramid_level(L, R, width, height, count, L1, R1, G1,
+  return record_cuda(launch_pyramid_level(L, reinterpret_cast<const float2 *>(R), width, height,
+                                          count, L1, reinterpret_cast<float2 *>(R1), G1,
                                           static_cast<cudaStream_t>(stream)));
+}
+
+bdis_status bdis_pack_right(const float *R, int width, int height, int count, float *R2,
+                            void *stream) {
+  if (!R || !R2 || !aligned8(R2) || width < 1 || height < 1 || count < 1)
+    return BDIS_E_INVALID_ARG;
+  return record_cuda(launch_pack_right(R, width, height, count, reinterpret_cast<float2 *>(R2),
+                                       static_cast<cudaStream_t>(stream)));
 }
 
 bdis_status bdis_search_level(const float *L, const float *R, const float *G, int width,
@@ -505,14 +520,14 @@ bdis_status bdis_search_level(const float *L, const float *R, const float *G, in
                               float *weight, const bdis_patch_debug *dbg, void *stream) {
   bdis_status s = check_params(p);
   if (s != BDIS_OK) return s;
-  if (!L || !R || !G || !d_star || !weight || count < 1 || width < p->patch_size ||
-      height < p->patch_size)
+  if (!L || !R || !G || !d_star || !weight || !aligned8(R) || count < 1 ||
+      width < p->patch_size || height < p->patch_size)
     return BDIS_E_INVALID_ARG;
   if (coarse && (coarse_width < 1 || coarse_height < 1)) return BDIS_E_INVALID_ARG;
   SearchArgs a{};
   fill_search_args(a, width, height, count, *p);
   a.L = L;
-  a.R = R;
+  a.R2 = reinterpret_cast<const float2 *>(R);
   a.G = G;
   a.coarse = coarse;
   a.cw = coarse ? coarse_width : 0;

@@ -65,7 +65,8 @@ inline int gamma_min_count(float gamma, int ps) {
 }
 
 struct SearchArgs {
-  const float *L, *R, *G;
+  const float *L, *G;
+  const float2 *R2;  // packed right plane: (R[x], R[x+1] - R[x]) per pixel
   int w, h;
   long long plane;  // w * h
   const float *coarse;
@@ -98,9 +99,11 @@ struct DensifyArgs {
 
 // Launchers (return the launch error, if any).
 cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &right, float *L0,
-                                  float *R0, float *G0, cudaStream_t st);
-cudaError_t launch_pyramid_level(const float *L, const float *R, int w, int h, int count,
-                                 float *L1, float *R1, float *G1, cudaStream_t st);
+                                  float2 *R0, float *G0, cudaStream_t st);
+cudaError_t launch_pyramid_level(const float *L, const float2 *R, int w, int h, int count,
+                                 float *L1, float2 *R1, float *G1, cudaStream_t st);
+cudaError_t launch_pack_right(const float *R, int w, int h, int count, float2 *R2,
+                              cudaStream_t st);
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st);
 cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, int h, int count,

@@ -6,10 +6,15 @@
 // search needs the x-gradient of the left (template) image only: Sobel-x / 8,
 // exact on linear ramps.
 //
-// Roofline: all three kernels stream planes once (HBM/L2 bandwidth bound).
-// prepare_level0: reads 2 B/px (uint8 pair), writes 12 B/px (L, R, G float).
-// pyramid_level (per output px): reads 4 input px of each view (~32 B with
-// halo reuse from L1), writes 8 B; the gradient pass reads 4 B, writes 4 B.
+// The right view is stored packed, (R[x], R[x+1] - R[x]) per pixel (the
+// difference is 0 in the last column), so that the inverse search gets a
+// linearly interpolated sample from one 8-byte load and one FMA.
+//
+// Roofline: all kernels stream planes once (HBM/L2 bandwidth bound).
+// prepare_level0: reads 2 B/px (uint8 pair), writes 16 B/px (L, packed R, G).
+// pyramid_level (per output px): reads 4 input px of each view (~24 B with
+// halo reuse from L1), writes 8 B; the gradient/packing pass reads 8 B and
+// writes 8 B.
 #include "bdis_internal.cuh"
 
 namespace bdis {
@@ -30,7 +35,7 @@ __device__ __forceinline__ float load_px(const void *base, size_t pitch, int x, 
 template <typename T>
 __global__ void prepare_level0_kernel(const void *left, const void *right, size_t pitch,
                                       size_t stride, int w, int h, long long total, float *L0,
-                                      float *R0, float *G0) {
+                                      float2 *R0, float *G0) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const long long plane = (long long)w * h;
@@ -40,7 +45,8 @@ __global__ void prepare_level0_kernel(const void *left, const void *right, size_
   const char *lb = reinterpret_cast<const char *>(left) + (size_t)b * stride;
   const char *rb = reinterpret_cast<const char *>(right) + (size_t)b * stride;
   L0[idx] = load_px<T>(lb, pitch, x, y);
-  R0[idx] = load_px<T>(rb, pitch, x, y);
+  const float r = load_px<T>(rb, pitch, x, y);
+  R0[idx] = make_float2(r, x + 1 < w ? load_px<T>(rb, pitch, x + 1, y) - r : 0.f);
   const int xm = reflect101(x - 1, w), xp = reflect101(x + 1, w);
   const int ym = reflect101(y - 1, h), yp = reflect101(y + 1, h);
   const float dm = load_px<T>(lb, pitch, xp, ym) - load_px<T>(lb, pitch, xm, ym);
@@ -50,9 +56,9 @@ __global__ void prepare_level0_kernel(const void *left, const void *right, size_
 }
 
 // One pyramid step for both views: out(X, Y) = sum_ij b_i b_j in(2X+i, 2Y+j).
-__global__ void down_kernel(const float *__restrict__ L, const float *__restrict__ R, int w,
+__global__ void down_kernel(const float *__restrict__ L, const float2 *__restrict__ R, int w,
                             int h, int dw, int dh, long long total, float *__restrict__ L1,
-                            float *__restrict__ R1) {
+                            float2 *__restrict__ R1) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const long long dplane = (long long)dw * dh;
@@ -60,7 +66,7 @@ __global__ void down_kernel(const float *__restrict__ L, const float *__restrict
   const int rem = (int)(idx - (long long)b * dplane);
   const int Y = rem / dw, X = rem - (rem / dw) * dw;
   const float *Lb = L + (long long)b * w * h;
-  const float *Rb = R + (long long)b * w * h;
+  const float2 *Rb = R + (long long)b * w * h;
   const float k[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
   int xs[5];
 #pragma unroll
@@ -70,22 +76,23 @@ __global__ void down_kernel(const float *__restrict__ L, const float *__restrict
   for (int j = 0; j < 5; ++j) {
     const int yy = reflect101(2 * Y + j - 2, h);
     const float *lr = Lb + (size_t)yy * w;
-    const float *rr = Rb + (size_t)yy * w;
+    const float2 *rr = Rb + (size_t)yy * w;
     float hl = 0.f, hr = 0.f;
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
       hl = fmaf(k[i], __ldg(lr + xs[i]), hl);
-      hr = fmaf(k[i], __ldg(rr + xs[i]), hr);
+      hr = fmaf(k[i], __ldg(rr + xs[i]).x, hr);
     }
     accL = fmaf(k[j], hl, accL);
     accR = fmaf(k[j], hr, accR);
   }
   L1[idx] = accL;
-  R1[idx] = accR;
+  R1[idx].x = accR;  // the difference term is filled by the gradient pass
 }
 
-__global__ void sobel_kernel(const float *__restrict__ L, int w, int h, long long total,
-                             float *__restrict__ G) {
+// Sobel-x / 8 of the left level and the difference term of the packed right level.
+__global__ void sobel_pack_kernel(const float *__restrict__ L, float2 *__restrict__ R, int w,
+                                  int h, long long total, float *__restrict__ G) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const long long plane = (long long)w * h;
@@ -99,6 +106,17 @@ __global__ void sobel_kernel(const float *__restrict__ L, int w, int h, long lon
   const float d0 = __ldg(Lb + (size_t)y * w + xp) - __ldg(Lb + (size_t)y * w + xm);
   const float dp = __ldg(Lb + (size_t)yp * w + xp) - __ldg(Lb + (size_t)yp * w + xm);
   G[idx] = (dm + 2.f * d0 + dp) * 0.125f;
+  float2 *Rb = R + (long long)b * plane + (size_t)y * w;
+  Rb[x].y = x + 1 < w ? Rb[x + 1].x - Rb[x].x : 0.f;
+}
+
+__global__ void pack_right_kernel(const float *__restrict__ R, int w, long long total,
+                                  float2 *__restrict__ R2) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int x = (int)(idx % w);
+  const float r = R[idx];
+  R2[idx] = make_float2(r, x + 1 < w ? R[idx + 1] - r : 0.f);
 }
 
 inline unsigned blocks_for(long long n, int threads) {
@@ -108,7 +126,7 @@ inline unsigned blocks_for(long long n, int threads) {
 }  // namespace
 
 cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &right, float *L0,
-                                  float *R0, float *G0, cudaStream_t st) {
+                                  float2 *R0, float *G0, cudaStream_t st) {
   const long long total = (long long)left.width * left.height * left.count;
   if (total == 0) return cudaSuccess;
   const int threads = 256;
@@ -124,8 +142,8 @@ cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &righ
   return cudaGetLastError();
 }
 
-cudaError_t launch_pyramid_level(const float *L, const float *R, int w, int h, int count,
-                                 float *L1, float *R1, float *G1, cudaStream_t st) {
+cudaError_t launch_pyramid_level(const float *L, const float2 *R, int w, int h, int count,
+                                 float *L1, float2 *R1, float *G1, cudaStream_t st) {
   const int dw = (w + 1) / 2, dh = (h + 1) / 2;
   const long long total = (long long)dw * dh * count;
   if (total == 0) return cudaSuccess;
@@ -133,7 +151,16 @@ cudaError_t launch_pyramid_level(const float *L, const float *R, int w, int h, i
   down_kernel<<<blocks_for(total, threads), threads, 0, st>>>(L, R, w, h, dw, dh, total, L1, R1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  sobel_kernel<<<blocks_for(total, threads), threads, 0, st>>>(L1, dw, dh, total, G1);
+  sobel_pack_kernel<<<blocks_for(total, threads), threads, 0, st>>>(L1, R1, dw, dh, total, G1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_right(const float *R, int w, int h, int count, float2 *R2,
+                              cudaStream_t st) {
+  const long long total = (long long)w * h * count;
+  if (total == 0) return cudaSuccess;
+  const int threads = 256;
+  pack_right_kernel<<<blocks_for(total, threads), threads, 0, st>>>(R, w, total, R2);
   return cudaGetLastError();
 }
 

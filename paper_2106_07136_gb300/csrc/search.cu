@@ -3,24 +3,32 @@
 //
 // Layout: one patch per group of G lanes (G = 4, 8, 16 or 32, the smallest
 // power of two >= patch size), lane c owning column c of its patch and
-// walking the rows. Per lane the template T and gradient g of its column stay
-// in registers for the whole search; the right image is read with
-// coalesced row loads (the G lanes of a group read consecutive pixels of one
-// row) served mostly from L1/L2, since neighbouring patches overlap.
-// Reductions over the patch are xor-butterflies inside the group.
+// walking the rows. Per lane the template T of its column (and the centred
+// gradient) stays in registers for the whole search; the right image is read
+// as packed (R[x], R[x+1] - R[x]) pairs, so one 8-byte load and one FMA give
+// a linearly interpolated sample. The G lanes of a group read consecutive
+// pairs of one row (coalesced); neighbouring patches overlap, so these loads
+// are served from L1/L2. Reductions over the patch are xor-butterflies inside
+// the group.
 //
 // Arithmetic per patch (the method's own, Eq. 1 and Eq. 3):
-//   - the valid set is a run of columns (rows are aligned), so its sums are
-//     recomputed only when that run changes;
+//   - rows are aligned, so the set of pixels whose sample is inside the right
+//     image is a run of columns; its sums (centred gradient, Hessian,
+//     template term) are recomputed only when that run changes;
 //   - with mean normalisation, sum g_n (R~_n - T_n) = sum g_c R~ - sum g_c T
 //     where g_c is the gradient centred on the valid set, so an iteration is
-//     two FMAs per pixel (interpolate, accumulate) and one group reduction;
+//     two FMAs and one load per pixel and one group reduction;
 //   - the window energies use two passes (mean, then squares) to keep the
 //     saddle decisions well conditioned.
 //
-// Roofline: FP32/L1 bound. Algorithmic work per patch: ps^2 * (2*iters + 4*s)
-// flops; unique DRAM bytes are only the level planes (12 B/px) plus 8 B per
-// patch written.
+// Two instantiations: a fast path with the patch size and window length fixed
+// at compile time (fully unrolled, no per-row guards) for the common settings,
+// and a generic path for any patch size up to 32 and window up to 15.
+//
+// Roofline: instruction-issue / FP32 bound. Algorithmic work per patch
+// (patch evaluations x 8 flops per pixel): ps^2 * 8 * (iterations + s).
+// DRAM bytes per patch level: the L, G and packed R planes read once
+// (16 B per pixel) plus 8 B written per patch.
 #include "bdis_internal.cuh"
 
 namespace bdis {
@@ -38,8 +46,8 @@ __device__ __forceinline__ float group_sum(float v) {
 // Split a sample position x - D into integer base and fraction computed from
 // D alone (exact in float): x - D = (x + k) + t with t in [0, 1).
 __device__ __forceinline__ void split_disp(float D, int &k, float &t) {
-  float nd = fminf(fmaxf(-D, -1.0e7f), 1.0e7f);  // NaN -> bound, never in range
-  float f = floorf(nd);
+  const float nd = fminf(fmaxf(-D, -1.0e7f), 1.0e7f);  // NaN -> bound, never in range
+  const float f = floorf(nd);
   k = (int)f;
   t = nd - f;
 }
@@ -48,6 +56,8 @@ __device__ __forceinline__ void split_disp(float D, int &k, float &t) {
 __device__ __forceinline__ bool sample_ok(int i0, float t, int w) {
   return i0 >= 0 && (i0 < w - 1 || (i0 == w - 1 && t == 0.f));
 }
+
+__device__ __forceinline__ float lerp_packed(float2 q, float t) { return fmaf(t, q.y, q.x); }
 
 __device__ __forceinline__ float bilinear_clamped(const float *M, int w, int h, float x,
                                                   float y) {
@@ -61,47 +71,228 @@ __device__ __forceinline__ float bilinear_clamped(const float *M, int w, int h, 
   return (1.f - ty) * top + ty * bot;
 }
 
-template <int G>
-__global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
+// Patch index -> (pair, origin) and the coarse-to-fine start (Sec. 2.1: twice
+// the coarser map read bilinearly at half the patch centre; 0 at the top).
+struct PatchPos {
+  int b, x0, y0;
+  float u0;
+};
+
+__device__ __forceinline__ PatchPos patch_pos(const SearchArgs &a, long long k) {
+  PatchPos p;
+  p.b = (int)(k / a.np);
+  const int kk = (int)(k - (long long)p.b * a.np);
+  const int pj = kk / a.nx, pi = kk - (kk / a.nx) * a.nx;
+  p.x0 = grid_origin(pi, a.nx, a.w, a.ps, a.stride);
+  p.y0 = grid_origin(pj, a.ny, a.h, a.ps, a.stride);
+  p.u0 = 0.f;
+  if (a.coarse) {
+    const float cx = (float)p.x0 + (a.ps - 1) * 0.5f, cy = (float)p.y0 + (a.ps - 1) * 0.5f;
+    p.u0 = 2.f * bilinear_clamped(a.coarse + (long long)p.b * a.cplane, a.cw, a.ch, cx * 0.5f,
+                                  cy * 0.5f);
+  }
+  return p;
+}
+
+// Posterior of the window centre (Eq. 3 with Eq. 4 as likelihood, evaluated
+// relative to the smallest energy) and the patch flags; writes the outputs.
+__device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, bool write,
+                                             float D, float u0, float last_step, bool flat,
+                                             int nvalid, int nc, float Ec, float Eo, float Emin,
+                                             float z, int ps) {
+  uint8_t flags = flat ? kFlagFlat : 0;
+  if (!isfinite(D) || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
+  if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
+  float post = 0.f;
+  if (nc == 0) {
+    flags |= kFlagEmpty;
+  } else {
+    post = expf(-(Ec - Emin) / a.kappa) / z;
+    if (a.s > 1 && Eo < Ec - kSaddleTau * fmaxf(Ec, 1.f)) flags |= kFlagSaddle;
+  }
+  if (nvalid < a.nmin_valid) flags |= kFlagGamma;
+  const bool drop = (flags & kDropFlags) != 0;
+  if (write) {
+    a.d_star[k] = D;
+    a.weight[k] = drop ? 0.f : post * (float)nvalid / (float)(ps * ps);
+    if (a.u_init) a.u_init[k] = u0;
+    if (a.posterior) a.posterior[k] = post;
+    if (a.flags) a.flags[k] = flags;
+    if (a.n_valid) a.n_valid[k] = nvalid;
+  }
+}
+
+// ------------------------------------------------------------- fast path
+
+template <int PS, int G, int S>
+__global__ void __launch_bounds__(128, PS <= 8 ? 8 : 4) search_fixed_kernel(const SearchArgs a) {
+  static_assert(PS <= G && G <= 32 && (G & (G - 1)) == 0, "group size");
+  static_assert(S >= 1 && S % 2 == 1, "window");
+  constexpr int HALF = (S - 1) / 2;
   const int lane = threadIdx.x & 31;
   const int c = lane & (G - 1);
   const unsigned gbits = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
   const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const bool live = gid < a.total;
-  // Groups past the end redo the last patch (so every lane joins the
-  // shuffles) and store nothing.
-  const long long k = live ? gid : a.total - 1;
-  const int b = (int)(k / a.np);
-  const int kk = (int)(k - (long long)b * a.np);
-  const int pj = kk / a.nx, pi = kk - (kk / a.nx) * a.nx;
-  const int ps = a.ps, w = a.w;
-  const int x0 = grid_origin(pi, a.nx, w, ps, a.stride);
-  const int y0 = grid_origin(pj, a.ny, a.h, ps, a.stride);
-  const bool act = c < ps;
-  const int x = x0 + c;
-  const float *Lp = a.L + (long long)b * a.plane;
-  const float *Rp = a.R + (long long)b * a.plane;
-  const float *Gp = a.G + (long long)b * a.plane;
+  const long long k = live ? gid : a.total - 1;  // past the end: redo the last, store nothing
+  const PatchPos pp = patch_pos(a, k);
+  const int w = a.w;
+  const bool act = (PS == G) || c < PS;
+  const int x = pp.x0 + (act ? c : 0);
+  const long long poff = (long long)pp.b * a.plane + (long long)pp.y0 * w;
+  const float *Lc = a.L + poff + x;
+  const float *Gc = a.G + poff + x;
+  const float2 *R2 = a.R2 + poff;  // row y0 of the packed right plane
 
-  float T[G], g[G];
+  float T[PS];
 #pragma unroll
-  for (int r = 0; r < G; ++r) {
-    const bool in = act && r < ps;
-    T[r] = in ? __ldg(Lp + (size_t)(y0 + r) * w + x) : 0.f;
-    g[r] = in ? __ldg(Gp + (size_t)(y0 + r) * w + x) : 0.f;
-  }
-
-  // Coarse-to-fine start (Sec. 2.1): twice the coarser map at half the centre.
-  float u0 = 0.f;
-  if (a.coarse) {
-    const float cx = (float)x0 + (ps - 1) * 0.5f, cy = (float)y0 + (ps - 1) * 0.5f;
-    u0 = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, cx * 0.5f,
-                                cy * 0.5f);
-  }
+  for (int r = 0; r < PS; ++r) T[r] = act ? __ldg(Lc + (size_t)r * w) : 0.f;
 
   // ---- inverse-search iterations (Eq. 1)
-  float D = u0;
-  float last_step = 0.f;
+  const float u0 = pp.u0;
+  float D = u0, last_step = 0.f;
+  bool frozen = false, flat = false, have = false;
+  unsigned prev = 0u;
+  float gc[PS];
+#pragma unroll
+  for (int r = 0; r < PS; ++r) gc[r] = 0.f;
+  float H = 0.f, invH = 0.f, gcT = 0.f;
+  int n = 0;
+  for (int it = 0; it < a.iters; ++it) {
+    int kd;
+    float t;
+    split_disp(D, kd, t);
+    const int i0 = x + kd;
+    const bool v = act && sample_ok(i0, t, w);
+    const unsigned m = __ballot_sync(kFull, v) & gbits;
+    const bool need = !frozen && (!have || m != prev);
+    if (__any_sync(kFull, need)) {
+      // sums of the new valid set: centred gradient, Hessian, template term
+      float g[PS];
+      float sg = 0.f;
+#pragma unroll
+      for (int r = 0; r < PS; ++r) {
+        g[r] = v ? __ldg(Gc + (size_t)r * w) : 0.f;
+        sg += g[r];
+      }
+      sg = group_sum<G>(sg);
+      const int nn = PS * __popc(m);
+      const float mg = (a.normalize && nn > 0) ? sg / (float)nn : 0.f;
+      float hh = 0.f, ct = 0.f;
+#pragma unroll
+      for (int r = 0; r < PS; ++r) {
+        const float q = v ? g[r] - mg : 0.f;
+        if (need) gc[r] = q;
+        hh = fmaf(q, q, hh);
+        ct = fmaf(q, T[r], ct);
+      }
+      hh = group_sum<G>(hh);
+      ct = group_sum<G>(ct);
+      if (need) {
+        H = hh;
+        invH = hh > 0.f ? 1.f / hh : 0.f;
+        gcT = ct;
+        n = nn;
+        prev = m;
+        have = true;
+      }
+    }
+    if (!frozen && (n == 0 || H <= kFlatEps * (float)n)) {
+      frozen = true;
+      flat = true;
+    }
+    float acc = 0.f;
+    if (v && !frozen) {
+      const float2 *p = R2 + i0;
+#pragma unroll
+      for (int r = 0; r < PS; ++r) acc = fmaf(gc[r], lerp_packed(__ldg(p + (size_t)r * w), t), acc);
+    }
+    const float Ssum = group_sum<G>(acc);
+    if (!frozen) {
+      last_step = (Ssum - gcT) * invH;
+      D += last_step;
+      // non-finite, or left the search range: no further steps (dropped below)
+      if (!isfinite(D) || fabsf(D - u0) > (float)PS) frozen = true;
+    }
+  }
+
+  // ---- Bayesian window (Eqs. 3-4)
+  const bool fin = isfinite(D);
+  int kd;
+  float t;
+  split_disp(D, kd, t);
+  const bool v0 = act && fin && sample_ok(x + kd, t, w);
+  const int nvalid = PS * __popc(__ballot_sync(kFull, v0) & gbits);
+  bool vc = act && fin;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    split_disp(D + (float)(i - HALF) * a.step, kd, t);
+    vc = vc && sample_ok(x + kd, t, w);
+  }
+  const int nc = PS * __popc(__ballot_sync(kFull, vc) & gbits);
+  const bool write = live && c == 0;
+  float E[S];
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    split_disp(D + (float)(i - HALF) * a.step, kd, t);
+    float dres[PS];
+    float sd = 0.f;
+#pragma unroll
+    for (int r = 0; r < PS; ++r) {
+      dres[r] = vc ? lerp_packed(__ldg(R2 + (x + kd) + (size_t)r * w), t) - T[r] : 0.f;
+      sd += dres[r];
+    }
+    float md = 0.f;
+    if (a.normalize) {
+      sd = group_sum<G>(sd);
+      md = nc > 0 ? sd / (float)nc : 0.f;
+    }
+    float e = 0.f;
+#pragma unroll
+    for (int r = 0; r < PS; ++r) {
+      const float q = vc ? dres[r] - md : 0.f;
+      e = fmaf(q, q, e);
+    }
+    E[i] = group_sum<G>(e);
+    if (write && a.energies) a.energies[k * S + i] = E[i];
+  }
+  float Emin = E[0], Eo = INFINITY;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    Emin = fminf(Emin, E[i]);
+    if (i != HALF) Eo = fminf(Eo, E[i]);
+  }
+  float z = 0.f;
+#pragma unroll
+  for (int i = 0; i < S; ++i) z += expf(-(E[i] - Emin) / a.kappa);
+  finish_patch(a, k, write, D, u0, last_step, flat, nvalid, nc, E[HALF], Eo, Emin, z, PS);
+}
+
+// ---------------------------------------------------------- generic path
+
+template <int G>
+__global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int c = lane & (G - 1);
+  const unsigned gbits = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const bool live = gid < a.total;
+  const long long k = live ? gid : a.total - 1;
+  const PatchPos pp = patch_pos(a, k);
+  const int ps = a.ps, w = a.w;
+  const bool act = c < ps;
+  const int x = pp.x0 + (act ? c : 0);
+  const long long poff = (long long)pp.b * a.plane + (long long)pp.y0 * w;
+  const float *Lc = a.L + poff + x;
+  const float *Gc = a.G + poff + x;
+  const float2 *R2 = a.R2 + poff;
+
+  float T[G];
+#pragma unroll
+  for (int r = 0; r < G; ++r) T[r] = (act && r < ps) ? __ldg(Lc + (size_t)r * w) : 0.f;
+
+  const float u0 = pp.u0;
+  float D = u0, last_step = 0.f;
   bool frozen = false, flat = false, have = false;
   unsigned prev = 0u;
   float gc[G];
@@ -118,17 +309,16 @@ __global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
     const unsigned m = __ballot_sync(kFull, v) & gbits;
     const bool need = !frozen && (!have || m != prev);
     if (__any_sync(kFull, need)) {
-      // sums of the new valid set (normalised gradient, Hessian, template term)
       float sg = 0.f;
 #pragma unroll
-      for (int r = 0; r < G; ++r) sg += (v && r < ps) ? g[r] : 0.f;
+      for (int r = 0; r < G; ++r) sg += (v && r < ps) ? __ldg(Gc + (size_t)r * w) : 0.f;
       sg = group_sum<G>(sg);
       const int nn = ps * __popc(m);
       const float mg = (a.normalize && nn > 0) ? sg / (float)nn : 0.f;
       float hh = 0.f, ct = 0.f;
 #pragma unroll
       for (int r = 0; r < G; ++r) {
-        const float q = (v && r < ps) ? g[r] - mg : 0.f;
+        const float q = (v && r < ps) ? __ldg(Gc + (size_t)r * w) - mg : 0.f;
         if (need) gc[r] = q;
         hh = fmaf(q, q, hh);
         ct = fmaf(q, T[r], ct);
@@ -149,27 +339,19 @@ __global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
     }
     float acc = 0.f;
     if (v && !frozen) {
-      const float *Rr = Rp + (size_t)y0 * w + i0;
-      const int d1 = (i0 + 1 < w) ? 1 : 0;  // at the last column t == 0
+      const float2 *p = R2 + i0;
 #pragma unroll
-      for (int r = 0; r < G; ++r) {
-        if (r < ps) {
-          const float r0 = __ldg(Rr + (size_t)r * w);
-          const float r1 = __ldg(Rr + (size_t)r * w + d1);
-          acc = fmaf(gc[r], fmaf(t, r1 - r0, r0), acc);
-        }
-      }
+      for (int r = 0; r < G; ++r)
+        if (r < ps) acc = fmaf(gc[r], lerp_packed(__ldg(p + (size_t)r * w), t), acc);
     }
-    const float S = group_sum<G>(acc);
+    const float Ssum = group_sum<G>(acc);
     if (!frozen) {
-      last_step = (S - gcT) / H;
+      last_step = (Ssum - gcT) / H;
       D += last_step;
-      // non-finite, or left the search range: no further steps (dropped below)
       if (!isfinite(D) || fabsf(D - u0) > (float)ps) frozen = true;
     }
   }
 
-  // ---- Bayesian window (Eqs. 3-4) and patch tests
   const bool fin = isfinite(D);
   int kd;
   float t;
@@ -183,26 +365,19 @@ __global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
     vc = vc && sample_ok(x + kd, t, w);
   }
   const int nc = ps * __popc(__ballot_sync(kFull, vc) & gbits);
-
-  float Ec = 0.f, Eo = INFINITY, Emin = INFINITY, z = 0.f;
-  const float inv_kappa = 1.f / a.kappa;
   const bool write = live && c == 0;
-  const long long eoff = k * a.s;
+  // window energies; the normaliser z is accumulated relative to the running
+  // minimum and rescaled when the minimum drops
+  float Ec = 0.f, Eo = INFINITY, Emin = INFINITY, z = 0.f;
   for (int i = 0; i < a.s; ++i) {
     split_disp(D + (float)(i - half) * a.step, kd, t);
-    const int i0 = x + kd;
-    const int d1 = (i0 + 1 < w) ? 1 : 0;
     float dres[G];
     float sd = 0.f;
 #pragma unroll
     for (int r = 0; r < G; ++r) {
-      dres[r] = 0.f;
-      if (vc && r < ps) {
-        const float *Rr = Rp + (size_t)(y0 + r) * w + i0;
-        const float r0 = __ldg(Rr), r1 = __ldg(Rr + d1);
-        dres[r] = fmaf(t, r1 - r0, r0) - T[r];
-        sd += dres[r];
-      }
+      dres[r] = (vc && r < ps) ? lerp_packed(__ldg(R2 + (x + kd) + (size_t)r * w), t) - T[r]
+                               : 0.f;
+      sd += dres[r];
     }
     float md = 0.f;
     if (a.normalize) {
@@ -212,53 +387,31 @@ __global__ void __launch_bounds__(128) search_kernel(const SearchArgs a) {
     float e = 0.f;
 #pragma unroll
     for (int r = 0; r < G; ++r) {
-      if (vc && r < ps) {
-        const float q = dres[r] - md;
-        e = fmaf(q, q, e);
-      }
+      const float q = (vc && r < ps) ? dres[r] - md : 0.f;
+      e = fmaf(q, q, e);
     }
     const float E = group_sum<G>(e);
-    if (write && a.energies) a.energies[eoff + i] = E;
-    if (i == half) Ec = E;
-    else Eo = fminf(Eo, E);
-    // streaming sum of exp(-(E_i - Emin) / kappa)
+    if (write && a.energies) a.energies[k * a.s + i] = E;
+    if (i == half)
+      Ec = E;
+    else
+      Eo = fminf(Eo, E);
     if (E < Emin) {
-      z = (Emin == INFINITY ? 0.f : z * expf(-(Emin - E) * inv_kappa)) + 1.f;
+      z = (Emin == INFINITY ? 0.f : z * expf(-(Emin - E) / a.kappa)) + 1.f;
       Emin = E;
     } else {
-      z += expf(-(E - Emin) * inv_kappa);
+      z += expf(-(E - Emin) / a.kappa);
     }
   }
-
-  uint8_t flags = flat ? kFlagFlat : 0;
-  if (!fin || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
-  if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
-  float post = 0.f;
-  if (nc == 0) {
-    flags |= kFlagEmpty;
-  } else {
-    post = expf(-(Ec - Emin) * inv_kappa) / z;
-    if (a.s > 1 && Eo < Ec - kSaddleTau * fmaxf(Ec, 1.f)) flags |= kFlagSaddle;
-  }
-  if (nvalid < a.nmin_valid) flags |= kFlagGamma;
-  const bool drop = (flags & kDropFlags) != 0;
-
-  if (write) {
-    a.d_star[k] = D;
-    a.weight[k] = drop ? 0.f : post * (float)nvalid / (float)(ps * ps);
-    if (a.u_init) a.u_init[k] = u0;
-    if (a.posterior) a.posterior[k] = post;
-    if (a.flags) a.flags[k] = flags;
-    if (a.n_valid) a.n_valid[k] = nvalid;
-  }
+  finish_patch(a, k, write, D, u0, last_step, flat, nvalid, nc, Ec, Eo, Emin, z, ps);
 }
 
-template <int G>
-cudaError_t launch_g(const SearchArgs &a, cudaStream_t st) {
+template <typename K>
+cudaError_t launch_groups(K kernel, int G, const SearchArgs &a, cudaStream_t st) {
   const int threads = 128;
   const long long lanes = a.total * G;
   const unsigned blocks = (unsigned)((lanes + threads - 1) / threads);
-  search_kernel<G><<<blocks, threads, 0, st>>>(a);
+  kernel<<<blocks, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -284,10 +437,15 @@ void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params 
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
-  if (a.ps <= 4) return launch_g<4>(a, st);
-  if (a.ps <= 8) return launch_g<8>(a, st);
-  if (a.ps <= 16) return launch_g<16>(a, st);
-  return launch_g<32>(a, st);
+  if (a.s == 5) {
+    if (a.ps == 8) return launch_groups(search_fixed_kernel<8, 8, 5>, 8, a, st);
+    if (a.ps == 12) return launch_groups(search_fixed_kernel<12, 16, 5>, 16, a, st);
+    if (a.ps == 16) return launch_groups(search_fixed_kernel<16, 16, 5>, 16, a, st);
+  }
+  if (a.ps <= 4) return launch_groups(search_generic_kernel<4>, 4, a, st);
+  if (a.ps <= 8) return launch_groups(search_generic_kernel<8>, 8, a, st);
+  if (a.ps <= 16) return launch_groups(search_generic_kernel<16>, 16, a, st);
+  return launch_groups(search_generic_kernel<32>, 32, a, st);
 }
 
 }  // namespace bdis

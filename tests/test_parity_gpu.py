@@ -53,6 +53,7 @@ def test_pyramid_and_gradient(orc, shape):
     L, R, G = bd.prepare_level0(dev(left, torch.uint8), dev(right, torch.uint8))
     for b in range(2):
         np.testing.assert_array_equal(host(L)[b], left[b].astype(np.float32))
+        np.testing.assert_array_equal(host(R)[b, ..., 0], right[b].astype(np.float32))
         np.testing.assert_allclose(host(G)[b], orc.sobel_x(left[b]), atol=PYR_ATOL)
     oL = [left[b].astype(np.float64) for b in range(2)]
     oR = [right[b].astype(np.float64) for b in range(2)]
@@ -63,7 +64,11 @@ def test_pyramid_and_gradient(orc, shape):
             assert host(L)[b].shape == oL[b].shape == (orc.level_dim(h, lvl),
                                                         orc.level_dim(w, lvl))
             np.testing.assert_allclose(host(L)[b], oL[b], atol=PYR_ATOL)
-            np.testing.assert_allclose(host(R)[b], oR[b], atol=PYR_ATOL)
+            Rp = host(R)[b]
+            np.testing.assert_allclose(Rp[..., 0], oR[b], atol=PYR_ATOL)
+            # packed difference term: R[x+1] - R[x] of the stored plane, 0 at the end
+            np.testing.assert_array_equal(Rp[:, :-1, 1], Rp[:, 1:, 0] - Rp[:, :-1, 0])
+            assert np.all(Rp[:, -1, 1] == 0.0)
             np.testing.assert_allclose(host(G)[b], orc.sobel_x(oL[b]), atol=PYR_ATOL)
 
 
@@ -88,7 +93,7 @@ def _search_stage(orc, pair, kw, levels):
     for lvl in levels:
         o = st["levels"][lvl]
         coarse = None if o["coarse"] is None else dev(o["coarse"])
-        g = bd.search_level(dev(o["L"]), dev(o["R"]), dev(o["G"]), coarse, gp)
+        g = bd.search_level(dev(o["L"]), bd.pack_right(dev(o["R"])), dev(o["G"]), coarse, gp)
         g = {k: host(v)[0] for k, v in g.items()}
         np.testing.assert_allclose(g["u_init"], o["u_init"], atol=1e-4)
         unstable = oracle_unstable(orc, o, op)
@@ -239,8 +244,8 @@ def test_gpu_flat_pair(matcher):
     out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
     assert np.all(out == 0.0)
     o = synth.make_flat_pair(24, 32)
-    g = bd.search_level(dev(o.left), dev(o.right), torch.zeros((24, 32), device="cuda"), None,
-                        gp)
+    g = bd.search_level(dev(o.left), bd.pack_right(dev(o.right)),
+                        torch.zeros((24, 32), device="cuda"), None, gp)
     assert torch.all(g["flags"] == 1) and torch.all(g["posterior"] == 0.2)
 
 
