@@ -238,6 +238,35 @@ bdis_status bdis_densify_level(int width, int height, int count, const bdis_para
 bdis_status bdis_upsample(const float *map, int map_width, int map_height, int level, int width,
                           int height, int count, float *out, void *stream);
 
+/* ----------------------------------------------------------- no allocation
+ * Some callers cannot allocate GPU memory: a hard real-time loop that froze
+ * its memory map after start-up, a plug-in that runs inside a host process
+ * whose allocator owns the device, or code on a path where cudaMalloc may
+ * synchronise the device or fail at run time. bdis_match_static runs the
+ * same kernels as bdis_match with no handle and no allocation: its scratch
+ * memory (pyramid planes, per-patch arrays) is a fixed array of
+ * BDIS_STATIC_SCRATCH_BYTES compiled into this library, which every GPU that
+ * loads the library holds until the process exits. The paper has no
+ * counterpart; this is a deployment variant of bdis_match.
+ *
+ *   - Arguments, output and errors as bdis_match, on the CURRENT CUDA device
+ *     and the given stream (cudaStream_t, NULL = legacy default stream).
+ *   - No cudaMalloc, cudaFree or other allocating call is made.
+ *   - The first call on a device looks the array's device address up (once
+ *     per device, with that device current). Make that first call before any
+ *     stream capture.
+ *   - Work whose scratch need exceeds BDIS_STATIC_SCRATCH_BYTES is refused
+ *     with BDIS_E_UNSUPPORTED and a message in bdis_last_error_string(). The
+ *     24 MiB hold one 1280x720 pair or three 640x480 pairs at the defaults.
+ *   - All calls on a device share the one array, which keeps the last call's
+ *     contents; nothing in it needs clearing (each kernel writes every
+ *     element it later reads). Calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race on the array: serialise them. */
+#define BDIS_STATIC_SCRATCH_BYTES (24u << 20)
+
+bdis_status bdis_match_static(const bdis_image *left, const bdis_image *right,
+                              const bdis_params *p, float *disparity_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,7 @@ from .api import (  # noqa: F401
     grid,
     image_desc,
     level_dims,
+    match_static,
     pack_right,
     patch_count,
     prepare_level0,

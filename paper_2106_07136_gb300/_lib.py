@@ -18,7 +18,10 @@ EXPORTED = [
     "bdis_workspace_bytes", "bdis_destroy", "bdis_match", "bdis_match_host",
     "bdis_prepare_level0", "bdis_pyramid_level", "bdis_search_level", "bdis_densify_level",
     "bdis_upsample", "bdis_enable_timing", "bdis_read_timing", "bdis_pack_right",
+    "bdis_match_static",
 ]
+
+STATIC_SCRATCH_BYTES = 24 << 20  # BDIS_STATIC_SCRATCH_BYTES
 
 TIMING_CLASSES = ["prepare_level0", "pyramid_level", "search", "densify", "upsample"]
 
@@ -102,6 +105,7 @@ def load():
     lib.bdis_prepare_level0.argtypes = [ip, ip, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.bdis_pyramid_level.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
                                        c_void_p, c_void_p, c_void_p]
+    lib.bdis_match_static.argtypes = [ip, ip, pp, c_void_p, c_void_p]
     lib.bdis_pack_right.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]
     lib.bdis_search_level.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
                                       c_int, c_int, pp, c_void_p, c_void_p,

@@ -158,6 +158,26 @@ class Matcher:
         return out
 
 
+def match_static(left: torch.Tensor, right: torch.Tensor, params: BdisParams = None,
+                 out: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """bdis_match_static: the method without any device allocation inside the
+    library, for callers that cannot allocate GPU memory on this path (the
+    scratch is a fixed array in libbdis.so; work larger than it is refused).
+    Runs on the current device; `out` should be preallocated by such callers."""
+    params = params if params is not None else default_params()
+    squeeze = left.dim() == 2
+    lb, rb = _as_batch(left), _as_batch(right)
+    b, h, w = lb.shape
+    if out is None:
+        out = torch.empty((b, h, w), dtype=torch.float32, device=left.device)
+    if not (out.is_contiguous() and out.dtype == torch.float32 and out.numel() == b * h * w):
+        raise ValueError("out must be a dense float32 tensor of B*H*W elements")
+    li, ri = image_desc(lb), image_desc(rb)
+    check(_lib.load().bdis_match_static(ctypes.byref(li), ctypes.byref(ri), ctypes.byref(params),
+                                        out.data_ptr(), _stream_ptr(stream)), "bdis_match_static")
+    return out.view(b, h, w)[0] if squeeze else out
+
+
 # ------------------------------------------------------------------ steps
 
 def prepare_level0(left: torch.Tensor, right: torch.Tensor, stream=None):

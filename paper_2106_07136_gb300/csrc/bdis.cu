@@ -271,6 +271,44 @@ bdis_status bind_device(const bdis_handle *h) {
 
 }  // namespace
 
+size_t match_scratch_bytes(int w, int h, int count, const bdis_params &p) {
+  return plan(w, h, count, p, false).bytes;
+}
+
+bdis_status check_match_args(const bdis_image *left, const bdis_image *right,
+                             const bdis_params *p, const float *disparity_out) {
+  if (!disparity_out) return BDIS_E_INVALID_ARG;
+  bdis_status s = check_pair(left, right);
+  if (s != BDIS_OK) return s;
+  s = check_params(p);
+  if (s != BDIS_OK) return s;
+  return check_geometry(left->width, left->height, *p);
+}
+
+bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right,
+                                 const float *disparity_out) {
+  if (check_device_ptr(left->data) != BDIS_OK || check_device_ptr(right->data) != BDIS_OK ||
+      check_device_ptr(disparity_out) != BDIS_OK)
+    return BDIS_E_INVALID_ARG;
+  return BDIS_OK;
+}
+
+bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
+                         const bdis_image &left, const bdis_image &right, const bdis_params &p,
+                         float *out) {
+  bdis_handle view;  // borrows the caller's scratch; owns nothing, times nothing
+  view.stream = stream;
+  view.ws = scratch;
+  view.ws_bytes = scratch_bytes;
+  const Layout lay = plan(left.width, left.height, left.count, p, false);
+  if (lay.bytes > scratch_bytes) return BDIS_E_UNSUPPORTED;
+  bdis_status s = run_match(&view, left, right, p, out, lay);
+  view.ws = nullptr;
+  return s;
+}
+
+void set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
 bdis_status record_cuda(cudaError_t e) {
   if (e == cudaSuccess) return BDIS_OK;
   snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e),

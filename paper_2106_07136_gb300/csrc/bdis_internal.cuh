@@ -115,6 +115,17 @@ void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_param
 
 // Record a CUDA error for bdis_last_error_string() and map it to a status.
 bdis_status record_cuda(cudaError_t e);
+void set_last_error(const char *msg);
 bdis_status check_params(const bdis_params *p);
+
+// Pieces of bdis_match for entry points that bring their own scratch memory.
+size_t match_scratch_bytes(int w, int h, int count, const bdis_params &p);
+bdis_status check_match_args(const bdis_image *left, const bdis_image *right,
+                             const bdis_params *p, const float *disparity_out);
+bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right,
+                                 const float *disparity_out);
+bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
+                         const bdis_image &left, const bdis_image &right, const bdis_params &p,
+                         float *out);
 
 }  // namespace bdis
