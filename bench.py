@@ -70,12 +70,10 @@ def make_pairs(first, count):
 # ------------------------------------------------------------ CPU oracle
 
 def _oracle_job(args):
-    idx, ps = args
+    idx, left, right, ps = args
     import oracle
-    import synth
-    pair = synth.make_pair(2, idx)
     t0 = time.perf_counter()
-    out = oracle.match(pair.left, pair.right, oracle.OracleParams.make(**params_kw(ps)))
+    out = oracle.match(left, right, oracle.OracleParams.make(**params_kw(ps)))
     return idx, time.perf_counter() - t0, out
 
 
@@ -86,9 +84,11 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def run_oracle_sample(n_pairs, ps, pool):
+def run_oracle_sample(pairs, ps, pool):
+    """Time the oracle on already generated (left, right) pairs, one per process."""
+    jobs = [(i, lr[0], lr[1], ps) for i, lr in enumerate(pairs)]
     t0 = time.perf_counter()
-    res = pool.map(_oracle_job, [(i, ps) for i in range(n_pairs)])
+    res = pool.map(_oracle_job, jobs, chunksize=1)
     wall = time.perf_counter() - t0
     return wall, sorted(res, key=lambda r: r[0])
 
@@ -149,6 +149,26 @@ def dist_env():
     return rank, world, local
 
 
+def rank_first_pair(rank, unique):
+    """Index of the first seeded pair of a rank: ranks never share pairs."""
+    return rank * unique
+
+
+def reduce_max_ms(ms, device, world):
+    """Slowest rank's timed milliseconds (max over ranks); no data is exchanged."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_pairs_per_s(pairs_per_rank, steps, world, max_ms):
+    return world * pairs_per_rank * steps / (max_ms / 1e3)
+
+
 def search_flops_per_pair(bd, ps, params):
     """Algorithmic flops of the inverse search + window per pair: 8 flops per
     pixel per patch evaluation, (iterations + window samples) evaluations."""
@@ -192,13 +212,15 @@ def run_reference(args):
     if rank != 0:
         return 0
     cores = host_cores()
+    L, R, _ = make_pairs(0, cores)
+    pairs = list(zip(L, R))
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
         for _ in range(args.warmup):
-            run_oracle_sample(cores, args.patch, pool)
+            run_oracle_sample(pairs, args.patch, pool)
         walls = []
         for _ in range(args.steps):
-            wall, _ = run_oracle_sample(cores, args.patch, pool)
+            wall, _ = run_oracle_sample(pairs, args.patch, pool)
             walls.append(wall)
     total = sum(walls)
     value = cores * args.steps / total
@@ -250,7 +272,7 @@ def main():
     ps = args.patch
     params = bd.default_params(**params_kw(ps))
     B, U = args.batch, min(args.unique, args.batch)
-    first = rank * U
+    first = rank_first_pair(rank, U)
     Lh, Rh, Dgt = make_pairs(first, U)
     reps = (B + U - 1) // U
     Lb = np.concatenate([Lh] * reps)[:B]
@@ -286,12 +308,8 @@ def main():
     clk = clocks.stop()
     m.enable_timing(False)
     kt = m.read_timing()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * B * args.steps / (ms / 1e3)
+    ms = reduce_max_ms(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device, world)
+    value = whole_job_pairs_per_s(B, args.steps, world, ms)
     launches = (kt["prepare_level0"][1] + 2 * kt["pyramid_level"][1] + kt["search"][1]
                 + kt["densify"][1] + kt["upsample"][1])
 
@@ -310,13 +328,17 @@ def main():
     s_ms, s_n = kt["search"]
     achieved = flops * B * args.steps / (s_ms / 1e3) / 1e12
     traffic = recorded_traffic(ps)
+    probe = statistics.median(bd.probe_fp32_tflops() for _ in range(3))
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
                 "traffic": None if traffic is None else traffic * B / (s_n / args.steps),
                 "kernel": "search (inverse search + posterior, all scales)",
                 "kernel_ms_per_launch": s_ms / s_n,
                 "algorithmic_flops_per_launch": flops * B / (s_n / args.steps),
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz"}
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                "peak_measured": probe,
+                "peak_measured_source": "FP32 FMA probe (bdis_probe_fp32_tflops) on this GPU",
+                "frac_of_measured": achieved / probe}
     kernel_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                     for k, v in kt.items() if v[1]}
 
@@ -324,7 +346,7 @@ def main():
     cpu = None
     if pool is not None:
         n_cpu = min(cores, U)
-        wall, res = run_oracle_sample(n_cpu, ps, pool)
+        wall, res = run_oracle_sample(list(zip(Lh[:n_cpu], Rh[:n_cpu])), ps, pool)
         pool.close()
         cpu = {"value": n_cpu / wall, "unit": "pairs/s", "cores": n_cpu, "kind": "oracle",
                "sample": f"{n_cpu} of the bench's 640x480 pairs, one per process "

@@ -238,6 +238,12 @@ bdis_status bdis_densify_level(int width, int height, int count, const bdis_para
 bdis_status bdis_upsample(const float *map, int map_width, int map_height, int level, int width,
                           int height, int count, float *out, void *stream);
 
+/* Measurement utility, not part of the method: FP32 FMA throughput of the
+ * current device in TFLOP/s (the roofline denominator of the inverse search).
+ * Runs two launches of an FMA-chain kernel of `iterations` steps per chain on
+ * `stream` and waits for them. */
+bdis_status bdis_probe_fp32_tflops(int iterations, double *tflops, void *stream);
+
 /* ----------------------------------------------------------- no allocation
  * Some callers cannot allocate GPU memory: a hard real-time loop that froze
  * its memory map after start-up, a plug-in that runs inside a host process

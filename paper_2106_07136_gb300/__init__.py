@@ -15,6 +15,7 @@ from .api import (  # noqa: F401
     match_static,
     pack_right,
     patch_count,
+    probe_fp32_tflops,
     prepare_level0,
     pyramid_level,
     search_level,

@@ -178,6 +178,14 @@ def match_static(left: torch.Tensor, right: torch.Tensor, params: BdisParams = N
     return out.view(b, h, w)[0] if squeeze else out
 
 
+def probe_fp32_tflops(iterations: int = 1 << 16, stream=None) -> float:
+    """Measured FP32 FMA throughput of the current GPU (TFLOP/s)."""
+    t = ctypes.c_double()
+    check(_lib.load().bdis_probe_fp32_tflops(int(iterations), ctypes.byref(t), _stream_ptr(stream)),
+          "bdis_probe_fp32_tflops")
+    return t.value
+
+
 # ------------------------------------------------------------------ steps
 
 def prepare_level0(left: torch.Tensor, right: torch.Tensor, stream=None):
