@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=128, help="pairs per step and rank")
     ap.add_argument("--unique", type=int, default=16, help="distinct seeded pairs per rank")
     ap.add_argument("--patch", type=int, default=8)
+    ap.add_argument("--variant", type=int, default=0,
+                    help="search lane layout: 1 column per lane, 2 wide; 0 = library default")
     ap.add_argument("--latency-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -271,6 +273,8 @@ def main():
 
     ps = args.patch
     params = bd.default_params(**params_kw(ps))
+    if args.variant:
+        bd.set_search_variant(args.variant)
     B, U = args.batch, min(args.unique, args.batch)
     first = rank_first_pair(rank, U)
     Lh, Rh, Dgt = make_pairs(first, U)
@@ -366,6 +370,7 @@ def main():
                                f"patch {ps}, overlap 0.75, 12 it, scales 4..0, gamma 0.75",
                    "pairs_per_step_per_gpu": B, "unique_pairs_per_gpu": U,
                    "patches_per_pair": n_patches,
+                   "search_variant": bd.get_search_variant(),
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
         "mpix_per_s": value * W * H / 1e6,

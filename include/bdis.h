@@ -238,6 +238,14 @@ bdis_status bdis_densify_level(int width, int height, int count, const bdis_para
 bdis_status bdis_upsample(const float *map, int map_width, int map_height, int level, int width,
                           int height, int count, float *out, void *stream);
 
+/* Tuning: lane layout of the inverse-search kernel for patch sizes 8, 12 and
+ * 16 with the paper's 5-sample window. 1 = one patch column per lane (a
+ * group of 8 or 16 lanes per patch); 2 = the wide layout (2 columns per lane
+ * for sizes 8 and 16, 3 for size 12). Results are identical up to float
+ * rounding; the choice only moves speed. Process-wide; default 2. */
+bdis_status bdis_set_search_variant(int columns_per_lane);
+int bdis_get_search_variant(void);
+
 /* Measurement utility, not part of the method: FP32 FMA throughput of the
  * current device in TFLOP/s (the roofline denominator of the inverse search).
  * Runs two launches of an FMA-chain kernel of `iterations` steps per chain on

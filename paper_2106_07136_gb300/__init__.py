@@ -16,6 +16,8 @@ from .api import (  # noqa: F401
     pack_right,
     patch_count,
     probe_fp32_tflops,
+    set_search_variant,
+    get_search_variant,
     prepare_level0,
     pyramid_level,
     search_level,

@@ -18,7 +18,8 @@ EXPORTED = [
     "bdis_workspace_bytes", "bdis_destroy", "bdis_match", "bdis_match_host",
     "bdis_prepare_level0", "bdis_pyramid_level", "bdis_search_level", "bdis_densify_level",
     "bdis_upsample", "bdis_enable_timing", "bdis_read_timing", "bdis_pack_right",
-    "bdis_match_static", "bdis_probe_fp32_tflops",
+    "bdis_match_static", "bdis_probe_fp32_tflops", "bdis_set_search_variant",
+    "bdis_get_search_variant",
 ]
 
 STATIC_SCRATCH_BYTES = 24 << 20  # BDIS_STATIC_SCRATCH_BYTES
@@ -105,6 +106,8 @@ def load():
     lib.bdis_prepare_level0.argtypes = [ip, ip, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.bdis_pyramid_level.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
                                        c_void_p, c_void_p, c_void_p]
+    lib.bdis_set_search_variant.argtypes = [c_int]
+    lib.bdis_get_search_variant.restype = c_int
     lib.bdis_probe_fp32_tflops.argtypes = [c_int, P(ctypes.c_double), c_void_p]
     lib.bdis_match_static.argtypes = [ip, ip, pp, c_void_p, c_void_p]
     lib.bdis_pack_right.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]

@@ -178,6 +178,15 @@ def match_static(left: torch.Tensor, right: torch.Tensor, params: BdisParams = N
     return out.view(b, h, w)[0] if squeeze else out
 
 
+def set_search_variant(columns_per_lane: int):
+    """Lane layout of the fixed-size search kernel: 1 (column per lane) or 2 (wide)."""
+    check(_lib.load().bdis_set_search_variant(int(columns_per_lane)), "bdis_set_search_variant")
+
+
+def get_search_variant() -> int:
+    return int(_lib.load().bdis_get_search_variant())
+
+
 def probe_fp32_tflops(iterations: int = 1 << 16, stream=None) -> float:
     """Measured FP32 FMA throughput of the current GPU (TFLOP/s)."""
     t = ctypes.c_double()

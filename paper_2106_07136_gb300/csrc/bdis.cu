@@ -438,6 +438,14 @@ void bdis_destroy(bdis_handle *h) {
   delete h;
 }
 
+bdis_status bdis_set_search_variant(int columns_per_lane) {
+  if (columns_per_lane != 1 && columns_per_lane != 2) return BDIS_E_INVALID_ARG;
+  set_search_cols_per_lane(columns_per_lane);
+  return BDIS_OK;
+}
+
+int bdis_get_search_variant(void) { return search_cols_per_lane(); }
+
 bdis_status bdis_enable_timing(bdis_handle *h, int on) {
   if (!h) return BDIS_E_INVALID_ARG;
   h->timing = on != 0;

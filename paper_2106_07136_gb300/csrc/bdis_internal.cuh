@@ -77,6 +77,7 @@ struct SearchArgs {
   int iters, s;
   float step, kappa;
   int nmin_valid, normalize;
+  int cols_per_lane;  // fast path: columns of a patch per lane (1, or 2-3)
   float *d_star, *weight;
   float *u_init, *posterior, *energies;
   uint8_t *flags;
@@ -108,6 +109,10 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st);
 cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, int h, int count,
                             float *out, cudaStream_t st);
+
+// Columns per lane of the fast search path (1 or the wide variant); tunable.
+int search_cols_per_lane();
+void set_search_cols_per_lane(int cpl);
 
 // Fill SearchArgs / DensifyArgs geometry from parameters (host).
 void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p);

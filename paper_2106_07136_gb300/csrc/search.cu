@@ -124,68 +124,100 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
 
 // ------------------------------------------------------------- fast path
 
-template <int PS, int G, int S>
-__global__ void __launch_bounds__(128, PS <= 8 ? 8 : 4) search_fixed_kernel(const SearchArgs a) {
-  static_assert(PS <= G && G <= 32 && (G & (G - 1)) == 0, "group size");
-  static_assert(S >= 1 && S % 2 == 1, "window");
-  constexpr int HALF = (S - 1) / 2;
+constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 1) / 2); }
+
+// Patch size PS and a 5-sample window 0.5 px apart fixed at compile time.
+// Each lane owns CPL adjacent columns of its patch (G lanes per patch), so the
+// per-step work that does not scale with pixels (sample split, validity vote,
+// reductions, the update) is shared by CPL * PS pixels. Pairs are on
+// blockIdx.y, patches of a pair on blockIdx.x.
+template <int PS, int CPL, int MINB>
+__global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArgs a) {
+  constexpr int LANES = (PS + CPL - 1) / CPL;
+  constexpr int G = pow2_at_least(LANES);
+  constexpr int S = 5, HALF = 2;
+  static_assert(G <= 32, "group size");
   const int lane = threadIdx.x & 31;
   const int c = lane & (G - 1);
   const unsigned gbits = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  const long long gid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const bool live = gid < a.total;
-  const long long k = live ? gid : a.total - 1;  // past the end: redo the last, store nothing
-  const PatchPos pp = patch_pos(a, k);
-  const int w = a.w;
-  const bool act = (PS == G) || c < PS;
-  const int x = pp.x0 + (act ? c : 0);
-  const long long poff = (long long)pp.b * a.plane + (long long)pp.y0 * w;
-  const float *Lc = a.L + poff + x;
-  const float *Gc = a.G + poff + x;
+  const int kk = blockIdx.x * (blockDim.x / G) + (int)(threadIdx.x / G);
+  const bool live = kk < a.np;
+  const int kp = live ? kk : a.np - 1;  // past the end: redo the last patch, store nothing
+  const int b = blockIdx.y;
+  const long long k = (long long)b * a.np + kp;
+  const int pj = kp / a.nx, pi = kp - pj * a.nx;
+  const int w = a.w, x0 = grid_origin(pi, a.nx, w, PS, a.stride);
+  const int y0 = grid_origin(pj, a.ny, a.h, PS, a.stride);
+  float u0 = 0.f;
+  if (a.coarse) {
+    const float cx = (float)x0 + (PS - 1) * 0.5f, cy = (float)y0 + (PS - 1) * 0.5f;
+    u0 = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, cx * 0.5f,
+                                cy * 0.5f);
+  }
+  const int xl = x0 + c * CPL;  // first column of this lane
+  bool act[CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) act[j] = (c * CPL + j) < PS;
+  const long long poff = (long long)b * a.plane + (long long)y0 * w;
+  const float *Lc = a.L + poff + xl;
+  const float *Gc = a.G + poff + xl;
   const float2 *R2 = a.R2 + poff;  // row y0 of the packed right plane
 
-  float T[PS];
+  float T[CPL][PS];
 #pragma unroll
-  for (int r = 0; r < PS; ++r) T[r] = act ? __ldg(Lc + (size_t)r * w) : 0.f;
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int r = 0; r < PS; ++r) T[j][r] = act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f;
 
   // ---- inverse-search iterations (Eq. 1)
-  const float u0 = pp.u0;
   float D = u0, last_step = 0.f;
   bool frozen = false, flat = false, have = false;
   unsigned prev = 0u;
-  float gc[PS];
+  float gc[CPL][PS];
 #pragma unroll
-  for (int r = 0; r < PS; ++r) gc[r] = 0.f;
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int r = 0; r < PS; ++r) gc[j][r] = 0.f;
   float H = 0.f, invH = 0.f, gcT = 0.f;
   int n = 0;
   for (int it = 0; it < a.iters; ++it) {
     int kd;
     float t;
     split_disp(D, kd, t);
-    const int i0 = x + kd;
-    const bool v = act && sample_ok(i0, t, w);
-    const unsigned m = __ballot_sync(kFull, v) & gbits;
-    const bool need = !frozen && (!have || m != prev);
+    const int ib = xl + kd;
+    bool v[CPL];
+    unsigned code = 0u;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      v[j] = act[j] && sample_ok(ib + j, t, w);
+      code |= (unsigned)v[j] << j;
+    }
+    const bool need_lane = !frozen && (!have || code != prev);
+    const bool need = (__ballot_sync(kFull, need_lane) & gbits) != 0u;  // whole group recomputes
     if (__any_sync(kFull, need)) {
       // sums of the new valid set: centred gradient, Hessian, template term
-      float g[PS];
+      float g[CPL][PS];
       float sg = 0.f;
 #pragma unroll
-      for (int r = 0; r < PS; ++r) {
-        g[r] = v ? __ldg(Gc + (size_t)r * w) : 0.f;
-        sg += g[r];
-      }
+      for (int j = 0; j < CPL; ++j)
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+          g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
+          sg += g[j][r];
+        }
       sg = group_sum<G>(sg);
-      const int nn = PS * __popc(m);
+      const int nn = PS * (int)group_sum<G>((float)__popc(code));
       const float mg = (a.normalize && nn > 0) ? sg / (float)nn : 0.f;
       float hh = 0.f, ct = 0.f;
 #pragma unroll
-      for (int r = 0; r < PS; ++r) {
-        const float q = v ? g[r] - mg : 0.f;
-        if (need) gc[r] = q;
-        hh = fmaf(q, q, hh);
-        ct = fmaf(q, T[r], ct);
-      }
+      for (int j = 0; j < CPL; ++j)
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+          const float q = v[j] ? g[j][r] - mg : 0.f;
+          if (need) gc[j][r] = q;
+          hh = fmaf(q, q, hh);
+          ct = fmaf(q, T[j][r], ct);
+        }
       hh = group_sum<G>(hh);
       ct = group_sum<G>(ct);
       if (need) {
@@ -193,7 +225,7 @@ __global__ void __launch_bounds__(128, PS <= 8 ? 8 : 4) search_fixed_kernel(cons
         invH = hh > 0.f ? 1.f / hh : 0.f;
         gcT = ct;
         n = nn;
-        prev = m;
+        prev = code;
         have = true;
       }
     }
@@ -202,10 +234,16 @@ __global__ void __launch_bounds__(128, PS <= 8 ? 8 : 4) search_fixed_kernel(cons
       flat = true;
     }
     float acc = 0.f;
-    if (v && !frozen) {
-      const float2 *p = R2 + i0;
+    if (!frozen) {
 #pragma unroll
-      for (int r = 0; r < PS; ++r) acc = fmaf(gc[r], lerp_packed(__ldg(p + (size_t)r * w), t), acc);
+      for (int j = 0; j < CPL; ++j) {
+        if (v[j]) {
+          const float2 *p = R2 + ib + j;
+#pragma unroll
+          for (int r = 0; r < PS; ++r)
+            acc = fmaf(gc[j][r], lerp_packed(__ldg(p + (size_t)r * w), t), acc);
+        }
+      }
     }
     const float Ssum = group_sum<G>(acc);
     if (!frozen) {
@@ -216,42 +254,66 @@ __global__ void __launch_bounds__(128, PS <= 8 ? 8 : 4) search_fixed_kernel(cons
     }
   }
 
-  // ---- Bayesian window (Eqs. 3-4)
+  // ---- Bayesian window (Eqs. 3-4): samples at D* + {-1, -0.5, 0, 0.5, 1}
   const bool fin = isfinite(D);
   int kd;
   float t;
   split_disp(D, kd, t);
-  const bool v0 = act && fin && sample_ok(x + kd, t, w);
-  const int nvalid = PS * __popc(__ballot_sync(kFull, v0) & gbits);
-  bool vc = act && fin;
+  const int ib = xl + kd;
+  // sample at D + delta sits at column base ib + off[delta] with fraction tt[delta]
+  const bool hi = t >= 0.5f;
+  const float th = hi ? t - 0.5f : t + 0.5f;
+  const int off[S] = {1, hi ? 1 : 0, 0, hi ? 0 : -1, -1};
+  const float tt[S] = {t, th, t, th, t};
+  bool vc[CPL];
+  int nv_lane = 0, nc_lane = 0;
 #pragma unroll
-  for (int i = 0; i < S; ++i) {
-    split_disp(D + (float)(i - HALF) * a.step, kd, t);
-    vc = vc && sample_ok(x + kd, t, w);
+  for (int j = 0; j < CPL; ++j) {
+    nv_lane += (act[j] && fin && sample_ok(ib + j, t, w)) ? 1 : 0;
+    vc[j] = act[j] && fin && (ib + j >= 1) && sample_ok(ib + j + 1, t, w);
+    nc_lane += vc[j] ? 1 : 0;
   }
-  const int nc = PS * __popc(__ballot_sync(kFull, vc) & gbits);
+  const int nvalid = PS * (int)group_sum<G>((float)nv_lane);
+  const int nc = PS * (int)group_sum<G>((float)nc_lane);
+  // One pass over the rows: per column j, residuals are taken relative to a
+  // shift cs[j] (the column's first-row residual at D*), which removes the
+  // brightness offset between the views; the group then merges the shifted
+  // sums exactly: sum (d - md)^2 = S2 - 2 (md - cs) S1 + n (md - cs)^2.
+  float cs[CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+    cs[j] = vc[j] ? lerp_packed(__ldg(R2 + ib + j), t) - T[j][0] : 0.f;
   const bool write = live && c == 0;
   float E[S];
 #pragma unroll
   for (int i = 0; i < S; ++i) {
-    split_disp(D + (float)(i - HALF) * a.step, kd, t);
-    float dres[PS];
-    float sd = 0.f;
+    float S1[CPL], S2[CPL];
 #pragma unroll
-    for (int r = 0; r < PS; ++r) {
-      dres[r] = vc ? lerp_packed(__ldg(R2 + (x + kd) + (size_t)r * w), t) - T[r] : 0.f;
-      sd += dres[r];
+    for (int j = 0; j < CPL; ++j) {
+      S1[j] = 0.f;
+      S2[j] = 0.f;
+      if (vc[j]) {
+        const float2 *p = R2 + ib + j + off[i];
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+          const float d = lerp_packed(__ldg(p + (size_t)r * w), tt[i]) - (T[j][r] + cs[j]);
+          S1[j] += d;
+          S2[j] = fmaf(d, d, S2[j]);
+        }
+      }
     }
-    float md = 0.f;
-    if (a.normalize) {
-      sd = group_sum<G>(sd);
-      md = nc > 0 ? sd / (float)nc : 0.f;
-    }
+    float s1 = 0.f;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) s1 += S1[j] + (float)PS * cs[j];
+    s1 = group_sum<G>(s1);
+    const float md = (a.normalize && nc > 0) ? s1 / (float)nc : 0.f;
     float e = 0.f;
 #pragma unroll
-    for (int r = 0; r < PS; ++r) {
-      const float q = vc ? dres[r] - md : 0.f;
-      e = fmaf(q, q, e);
+    for (int j = 0; j < CPL; ++j) {
+      if (vc[j]) {
+        const float u = md - cs[j];
+        e += fmaf(-2.f * u, S1[j], fmaf((float)PS * u, u, S2[j]));
+      }
     }
     E[i] = group_sum<G>(e);
     if (write && a.energies) a.energies[k * S + i] = E[i];
@@ -406,8 +468,18 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
   finish_patch(a, k, write, D, u0, last_step, flat, nvalid, nc, Ec, Eo, Emin, z, ps);
 }
 
+template <int PS, int CPL, int MINB>
+cudaError_t launch_fixed(const SearchArgs &a, cudaStream_t st) {
+  constexpr int G = pow2_at_least((PS + CPL - 1) / CPL);
+  const int threads = 128, per_block = threads / G;
+  const int count = (int)(a.total / a.np);
+  const dim3 grid((unsigned)((a.np + per_block - 1) / per_block), (unsigned)count);
+  search_fixed_kernel<PS, CPL, MINB><<<grid, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename K>
-cudaError_t launch_groups(K kernel, int G, const SearchArgs &a, cudaStream_t st) {
+cudaError_t launch_groups(K kernel, int G, const SearchArgs &a, cudaStream_t st) {  // 1-D grid
   const int threads = 128;
   const long long lanes = a.total * G;
   const unsigned blocks = (unsigned)((lanes + threads - 1) / threads);
@@ -416,6 +488,13 @@ cudaError_t launch_groups(K kernel, int G, const SearchArgs &a, cudaStream_t st)
 }
 
 }  // namespace
+
+namespace {
+int g_cols_per_lane = 2;  // process-wide choice of the fast-path variant
+}  // namespace
+
+int search_cols_per_lane() { return g_cols_per_lane; }
+void set_search_cols_per_lane(int cpl) { g_cols_per_lane = cpl; }
 
 void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p) {
   a.w = w;
@@ -433,14 +512,17 @@ void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params 
   a.kappa = 2.f * p.sigma_r * p.sigma_r * (float)(p.window_samples * p.window_samples);
   a.nmin_valid = gamma_min_count(p.gamma, p.patch_size);
   a.normalize = p.normalize ? 1 : 0;
+  a.cols_per_lane = search_cols_per_lane();
 }
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
-  if (a.s == 5) {
-    if (a.ps == 8) return launch_groups(search_fixed_kernel<8, 8, 5>, 8, a, st);
-    if (a.ps == 12) return launch_groups(search_fixed_kernel<12, 16, 5>, 16, a, st);
-    if (a.ps == 16) return launch_groups(search_fixed_kernel<16, 16, 5>, 16, a, st);
+  const int count = (int)(a.total / a.np);
+  if (a.s == 5 && a.step == 0.5f && count <= 65535) {
+    const int cpl = a.cols_per_lane;
+    if (a.ps == 8) return cpl == 1 ? launch_fixed<8, 1, 8>(a, st) : launch_fixed<8, 2, 5>(a, st);
+    if (a.ps == 12) return cpl == 1 ? launch_fixed<12, 1, 4>(a, st) : launch_fixed<12, 3, 3>(a, st);
+    if (a.ps == 16) return cpl == 1 ? launch_fixed<16, 1, 4>(a, st) : launch_fixed<16, 2, 3>(a, st);
   }
   if (a.ps <= 4) return launch_groups(search_generic_kernel<4>, 4, a, st);
   if (a.ps <= 8) return launch_groups(search_generic_kernel<8>, 8, a, st);

@@ -119,8 +119,17 @@ def test_search_stage_cfg1(orc, cfg1):
     _search_stage(orc, cfg1, CFG1, levels=[2, 1, 0])
 
 
-@pytest.mark.parametrize("ps", [8, 12])
-def test_search_stage_cfg2(orc, cfg2, ps):
+@pytest.fixture
+def search_variant(request):
+    old = bd.get_search_variant()
+    bd.set_search_variant(request.param)
+    yield request.param
+    bd.set_search_variant(old)
+
+
+@pytest.mark.parametrize("search_variant", [1, 2], indirect=True)
+@pytest.mark.parametrize("ps", [8, 12, 16])
+def test_search_stage_cfg2(orc, cfg2, ps, search_variant):
     _search_stage(orc, cfg2, dict(CFG2, patch_size=ps), levels=[4, 2, 0])
 
 
@@ -172,8 +181,9 @@ def test_e2e_cfg1(orc, cfg1, matcher):
     assert_e2e(out, ref, "cfg1")
 
 
+@pytest.mark.parametrize("search_variant", [1, 2], indirect=True)
 @pytest.mark.parametrize("ps", [8, 12])
-def test_e2e_cfg2(orc, cfg2, matcher, ps):
+def test_e2e_cfg2(orc, cfg2, matcher, ps, search_variant):
     gp, op = params(orc, **dict(CFG2, patch_size=ps))
     ref = orc.match(cfg2.left, cfg2.right, op)
     out = host(matcher.match(dev(cfg2.left, torch.uint8), dev(cfg2.right, torch.uint8), gp))
