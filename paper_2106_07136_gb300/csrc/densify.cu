@@ -1,17 +1,22 @@
 // densify.cu -- fusion of the patch disparities into a dense map (Sec. 2.3).
 //
-// Each pixel gathers its covering patches straight from the regular grid (no
+// Each pixel takes its covering patches straight from the regular grid (no
 // scatter, no atomics): w = weight_k * m(x - x0_k) * m(y - y0_k), where the
 // Gaussian mask m (Eq. 5, sigma_s) is separable and depends only on the
-// position inside the patch, so it is tabulated once per block. The pixel's
-// disparity is sum w D*_k / sum w (the normalised form of Eq. 2 with the
-// combined posterior as weight). Pixels without a kept patch are NaN at the
-// finest level (Sec. 3.2: not estimated); coarser levels carry the value
-// their patches started from.
+// position inside the patch. The pixel's disparity is sum w D*_k / sum w (the
+// normalised form of Eq. 2 with the combined posterior as weight). Pixels
+// without a kept patch are NaN at the finest level (Sec. 3.2: not
+// estimated); coarser levels carry the value their patches started from.
 //
-// Roofline: one thread per pixel; reads (ps/stride)^2 patch records per
-// pixel, mostly from L1/L2 (neighbouring pixels share patches); DRAM bytes per
-// pixel: 4 written plus the patch arrays (8 B per patch) read once.
+// Because the mask is separable, a block computes a 32x32 tile in two passes
+// through shared memory: first, for every patch row that touches the tile
+// and every tile column, the x-weighted sums over the covering patches of
+// that row (sum m_x w D and sum m_x w); then, per pixel, the y-weighted sum of
+// those over its covering rows. Work per pixel drops from (ps/stride)^2 to
+// about 2 ps/stride multiply-adds per quantity.
+//
+// Roofline: DRAM bytes per pixel: 4 written (+4 read for the coarse map where
+// carried) plus the patch arrays (8 B per patch) read once per tile.
 #include "bdis_internal.cuh"
 
 namespace bdis {
@@ -39,51 +44,84 @@ __device__ __forceinline__ void cover_range(int x, int n_px, int ps, int stride,
   last = (x >= n_px - ps) ? 1 : 0;
 }
 
+constexpr int kTileX = 32, kTileY = 32, kMaxRows = kTileY + kMaxPatch;
+
 __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
   __shared__ float mask[kMaxPatch];
-  if (threadIdx.x < a.ps) {
-    const float m = (float)threadIdx.x - (a.ps - 1) * 0.5f;
-    mask[threadIdx.x] = expf(-(m * m) / a.two_s2);
+  __shared__ float sA[kMaxRows][kTileX], sB[kMaxRows][kTileX];
+  const int tid = threadIdx.x;
+  if (tid < a.ps) {
+    const float m = (float)tid - (a.ps - 1) * 0.5f;
+    mask[tid] = expf(-(m * m) / a.two_s2);
   }
-  __syncthreads();
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= a.total) return;
-  const int b = (int)(idx / a.plane);
-  const int rem = (int)(idx - (long long)b * a.plane);
-  const int y = rem / a.w, x = rem - (rem / a.w) * a.w;
-  int ilo, ihi, ilast, jlo, jhi, jlast;
-  cover_range(x, a.w, a.ps, a.stride, a.nx, ilo, ihi, ilast);
-  cover_range(y, a.h, a.ps, a.stride, a.ny, jlo, jhi, jlast);
+  const int b = blockIdx.z;
+  const int X0 = blockIdx.x * kTileX, Y0 = blockIdx.y * kTileY;
+  const int ylast = min(Y0 + kTileY, a.h) - 1;
+  // patch rows touching the tile: regular rows [jlo, jhi] and maybe the last
+  int jlo, jhi, jl_unused, hlast_lo, hlast_hi;
+  cover_range(Y0, a.h, a.ps, a.stride, a.ny, jlo, jl_unused, hlast_lo);
+  cover_range(ylast, a.h, a.ps, a.stride, a.ny, jl_unused, jhi, hlast_hi);
+  const int nreg = max(0, jhi - jlo + 1);
+  const int has_last = hlast_hi;  // the last row covers the bottom of the tile if any
+  const int nrows = nreg + has_last;
   const float *wp = a.weight + (long long)b * a.np;
   const float *dp = a.d_star + (long long)b * a.np;
-  float num = 0.f, den = 0.f;
-  for (int jj = jlo; jj <= jhi + jlast; ++jj) {
-    const int j = jj > jhi ? a.ny - 1 : jj;
-    const int y0 = grid_origin(j, a.ny, a.h, a.ps, a.stride);
-    const float my = mask[y - y0];
-    for (int ii = ilo; ii <= ihi + ilast; ++ii) {
-      const int i = ii > ihi ? a.nx - 1 : ii;
-      const int x0 = grid_origin(i, a.nx, a.w, a.ps, a.stride);
-      const int kk = j * a.nx + i;
-      const float wk = __ldg(wp + kk);
-      if (wk > 0.f) {
-        const float q = wk * my * mask[x - x0];
-        num = fmaf(q, __ldg(dp + kk), num);
-        den += q;
+  __syncthreads();
+
+  // pass 1: x-weighted sums per (patch row, tile column)
+  for (int q = tid; q < nrows * kTileX; q += blockDim.x) {
+    const int jj = q / kTileX, xx = q - jj * kTileX;
+    const int x = X0 + xx;
+    float A = 0.f, B = 0.f;
+    if (x < a.w) {
+      const int j = jj < nreg ? jlo + jj : a.ny - 1;
+      int ilo, ihi, ilast;
+      cover_range(x, a.w, a.ps, a.stride, a.nx, ilo, ihi, ilast);
+      const float *wr = wp + (long long)j * a.nx;
+      const float *dr = dp + (long long)j * a.nx;
+      for (int ii = ilo; ii <= ihi + ilast; ++ii) {
+        const int i = ii > ihi ? a.nx - 1 : ii;
+        const float wk = __ldg(wr + i);
+        if (wk > 0.f) {
+          const float q2 = wk * mask[x - grid_origin(i, a.nx, a.w, a.ps, a.stride)];
+          A = fmaf(q2, __ldg(dr + i), A);
+          B += q2;
+        }
       }
     }
+    sA[jj][xx] = A;
+    sB[jj][xx] = B;
   }
-  float out;
-  if (den > 0.f)
-    out = num / den;
-  else if (a.is_finest)
-    out = __int_as_float(0x7fc00000);  // NaN: not estimated
-  else if (a.coarse)
-    out = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, x * 0.5f,
-                                 y * 0.5f);
-  else
-    out = 0.f;
-  a.out[idx] = out;
+  __syncthreads();
+
+  // pass 2: y-weighted sums over the covering rows of each pixel
+  const int xx = tid & (kTileX - 1);
+  const int x = X0 + xx;
+  for (int yy = tid / kTileX; yy < kTileY; yy += blockDim.x / kTileX) {
+    const int y = Y0 + yy;
+    if (x >= a.w || y >= a.h) continue;
+    int lo, hi, last;
+    cover_range(y, a.h, a.ps, a.stride, a.ny, lo, hi, last);
+    float num = 0.f, den = 0.f;
+    for (int j = lo; j <= hi + last; ++j) {
+      const int row = j > hi ? a.ny - 1 : j;  // past the regular rows: the last row
+      const int jj = j > hi ? nreg : j - jlo;
+      const float my = mask[y - grid_origin(row, a.ny, a.h, a.ps, a.stride)];
+      num = fmaf(my, sA[jj][xx], num);
+      den = fmaf(my, sB[jj][xx], den);
+    }
+    float out;
+    if (den > 0.f)
+      out = num / den;
+    else if (a.is_finest)
+      out = __int_as_float(0x7fc00000);  // NaN: not estimated
+    else if (a.coarse)
+      out = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, x * 0.5f,
+                                   y * 0.5f);
+    else
+      out = 0.f;
+    a.out[(long long)b * a.plane + (long long)y * a.w + x] = out;
+  }
 }
 
 // Full-size map from level f: bilinear over finite neighbours with positive
@@ -132,8 +170,10 @@ void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_param
 
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
-  const int threads = 256;
-  densify_kernel<<<(unsigned)((a.total + threads - 1) / threads), threads, 0, st>>>(a);
+  const int count = (int)(a.total / a.plane);
+  const dim3 grid((unsigned)((a.w + kTileX - 1) / kTileX), (unsigned)((a.h + kTileY - 1) / kTileY),
+                  (unsigned)count);
+  densify_kernel<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 
