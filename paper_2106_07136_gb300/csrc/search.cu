@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
       frozen = true;
       flat = true;
     }
-    float acc = 0.f;
+    // four partial sums break the FMA dependency chain
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
     if (!frozen) {
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
@@ -241,11 +242,11 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
           const float2 *p = R2 + ib + j;
 #pragma unroll
           for (int r = 0; r < PS; ++r)
-            acc = fmaf(gc[j][r], lerp_packed(__ldg(p + (size_t)r * w), t), acc);
+            acc[r & 3] = fmaf(gc[j][r], lerp_packed(__ldg(p + (size_t)r * w), t), acc[r & 3]);
         }
       }
     }
-    const float Ssum = group_sum<G>(acc);
+    const float Ssum = group_sum<G>((acc[0] + acc[1]) + (acc[2] + acc[3]));
     if (!frozen) {
       last_step = (Ssum - gcT) * invH;
       D += last_step;
@@ -290,17 +291,24 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
     float S1[CPL], S2[CPL];
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
-      S1[j] = 0.f;
-      S2[j] = 0.f;
+      // two partial sums per quantity (even / odd rows) shorten the chains
+      float s1a = 0.f, s1b = 0.f, s2a = 0.f, s2b = 0.f;
       if (vc[j]) {
         const float2 *p = R2 + ib + j + off[i];
 #pragma unroll
         for (int r = 0; r < PS; ++r) {
           const float d = lerp_packed(__ldg(p + (size_t)r * w), tt[i]) - (T[j][r] + cs[j]);
-          S1[j] += d;
-          S2[j] = fmaf(d, d, S2[j]);
+          if (r & 1) {
+            s1b += d;
+            s2b = fmaf(d, d, s2b);
+          } else {
+            s1a += d;
+            s2a = fmaf(d, d, s2a);
+          }
         }
       }
+      S1[j] = s1a + s1b;
+      S2[j] = s2a + s2b;
     }
     float s1 = 0.f;
 #pragma unroll
@@ -520,7 +528,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
   const int count = (int)(a.total / a.np);
   if (a.s == 5 && a.step == 0.5f && count <= 65535) {
     const int cpl = a.cols_per_lane;
-    if (a.ps == 8) return cpl == 1 ? launch_fixed<8, 1, 8>(a, st) : launch_fixed<8, 2, 5>(a, st);
+    if (a.ps == 8) return cpl == 1 ? launch_fixed<8, 1, 8>(a, st) : launch_fixed<8, 2, 6>(a, st);
     if (a.ps == 12) return cpl == 1 ? launch_fixed<12, 1, 4>(a, st) : launch_fixed<12, 3, 3>(a, st);
     if (a.ps == 16) return cpl == 1 ? launch_fixed<16, 1, 4>(a, st) : launch_fixed<16, 2, 3>(a, st);
   }
