@@ -320,7 +320,7 @@ def main():
     gpu_maps = out[:U].cpu().numpy()
     extras = {}
     if not args.no_extras and rank == 0:
-        extras = measure_extras(args, bd, m, params, left, right, Lh, Rh, device, stream)
+        extras = measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream)
 
     if rank != 0:
         m.close()
@@ -390,7 +390,7 @@ def main():
     return 0
 
 
-def measure_extras(args, bd, m, params, left, right, Lh, Rh, device, stream):
+def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream):
     import torch
     res = {}
     B = left.shape[0]
@@ -440,6 +440,22 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, device, stream):
     res["variants"] = {"patch12": {"value": B * kk / (ev0.elapsed_time(ev1) / 1e3),
                                    "unit": "pairs/s", "patches_per_pair": bd.patch_count(W, H, p12),
                                    "l2": "not flushed (back-to-back steps)"}}
+    # DIS fusion (Eq. 2), the baseline the paper compares against, same workload
+    pd = bd.default_params(**dict(params_kw(args.patch), fusion=1))
+    for _ in range(3):
+        m.match(left, right, pd, out=out)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(kk):
+        m.match(left, right, pd, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    import synth
+    U = Lh.shape[0]
+    res["variants"]["dis_fusion"] = {
+        "value": B * kk / (ev0.elapsed_time(ev1) / 1e3), "unit": "pairs/s",
+        "accuracy_vs_ground_truth": synth.error_stats(out[:U].cpu().numpy(), Dgt),
+        "l2": "not flushed (back-to-back steps)"}
     return res
 
 

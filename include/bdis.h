@@ -83,7 +83,14 @@ typedef struct {
  *   gamma           minimum fraction of patch pixels whose right-image
  *                   sample lies inside the image (paper: 0.75 at 640x480,
  *                   0.25 at 288x360);
- *   normalize       1: subtract the patch means (DIS's normalisation). */
+ *   normalize       1: subtract the patch means (DIS's normalisation);
+ *   fusion          BDIS_FUSION_BDIS: the Bayesian posterior and Gaussian mask
+ *                   (Sec. 2.2-2.3); BDIS_FUSION_DIS: the baseline the paper
+ *                   compares against, every patch fused by its inverse
+ *                   squared residual (Eq. 2; a patch that left its search
+ *                   range falls back to its start). */
+enum { BDIS_FUSION_BDIS = 0, BDIS_FUSION_DIS = 1 };
+
 typedef struct {
     int patch_size;
     float overlap;
@@ -96,6 +103,7 @@ typedef struct {
     float window_step;
     float gamma;
     int normalize;
+    int fusion;
 } bdis_params;
 
 /* Optional per-patch outputs of bdis_search_level. Any pointer may be NULL.
@@ -111,7 +119,8 @@ typedef struct {
 typedef struct bdis_handle bdis_handle;
 
 /* Paper defaults (Sec. 3): patch 8, overlap 0.75, 12 iterations, scales 4..0,
- * sigma_r = sigma_s = 4, 5 samples 0.5 px apart, gamma 0.75, normalize 1. */
+ * sigma_r = sigma_s = 4, 5 samples 0.5 px apart, gamma 0.75, normalize 1,
+ * BDIS fusion. */
 void bdis_default_params(bdis_params *p);
 
 const char *bdis_status_string(bdis_status s);
@@ -225,13 +234,16 @@ bdis_status bdis_search_level(const float *L, const float *R, const float *G, in
 
 /* Densification of one level (Sec. 2.3): each pixel is the mean of its kept
  * covering patches' D* weighted by weight_k * exp(-|x - c_k|^2 / (2 sigma_s^2)).
- * Pixels without a kept patch get NaN when is_finest, otherwise twice the
- * coarse map at half their position (0 when coarse is NULL). out: count x h
- * x w device. */
+ * With DIS fusion the per-pixel weight is weight_k / max(r^2, 1) with r the
+ * residual R(x - D*_k) - L(x) (Eq. 2), over patches whose sample is inside
+ * the right image; L and R (the level's left plane and packed right plane)
+ * are then required, and may be NULL otherwise. Pixels without a kept patch
+ * get NaN when is_finest, otherwise twice the coarse map at half their
+ * position (0 when coarse is NULL). out: count x h x w device. */
 bdis_status bdis_densify_level(int width, int height, int count, const bdis_params *p,
                                const float *d_star, const float *weight, const float *coarse,
-                               int coarse_width, int coarse_height, int is_finest, float *out,
-                               void *stream);
+                               int coarse_width, int coarse_height, int is_finest,
+                               const float *L, const float *R, float *out, void *stream);
 
 /* Bring a map of level f to full size: bilinear over finite neighbours,
  * values times 2^f; NaN where no finite neighbour has weight. */

@@ -30,4 +30,6 @@ from .oracle import (  # noqa: F401
     FLAG_EMPTY,
     FLAG_UNCONVERGED,
     DISCARD_FLAGS,
+    FUSION_BDIS,
+    FUSION_DIS,
 )

@@ -18,7 +18,8 @@
  *     the valid-pixel threshold gamma (Sec. 3, Sec. 3.2);
  *   - densification with the spatial Gaussian mask (Sec. 2.3, Eq. 5 and the
  *     combined pixel-wise posterior that follows it);
- *   - uncovered pixels are left unestimated (Sec. 3.2).
+ *   - uncovered pixels are left unestimated (Sec. 3.2);
+ *   - DIS mode: the paper's baseline fusion by inverse residual (Eq. 2).
  *
  * Where the paper leaves a detail open, the reading taken here is named at
  * the point of use (R1..R12); the same list is kept in the design notes.
@@ -30,7 +31,8 @@
  *                                        closed form, bisection fixed point,
  *                                        brute-force SSD, flat texture)
  *   orc_densify_level                   pinned (constant field, single and
- *                                        two-patch closed forms)
+ *                                        two-patch closed forms; DIS weights
+ *                                        on an exact linear texture)
  *   orc_match                           pinned through the exact-shift and
  *                                        linear-texture pairs; on mixed
  *                                        scenes the result is "parity
@@ -55,7 +57,11 @@ typedef struct {
     double window_step;  /* spacing of the candidates in pixels */
     double gamma;        /* minimum fraction of valid pixels in a patch */
     int normalize;       /* 1: patch mean normalisation (DIS default) */
+    int fusion;          /* 0: BDIS (Eqs. 3-5), 1: DIS inverse-residual fusion (Eq. 2) */
 } orc_params;
+
+#define ORC_FUSION_BDIS 0
+#define ORC_FUSION_DIS 1
 
 /* Per-patch flags. Only FLAG_FLAT does not discard the patch. */
 enum {
@@ -362,6 +368,12 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
     res->posterior = post;
     /* Sec. 3.2: patches with invalid pixels get a lower probability (R9) */
     res->weight = discard ? 0.0 : post * (double)n_valid / (double)(ps * ps);
+    if (p->fusion == ORC_FUSION_DIS) {
+        /* R14: DIS fuses every patch (Eq. 2, all covering patches); a patch
+         * that left its search range falls back to where it started. */
+        if (flags & ORC_FLAG_DIVERGED) res->d_star = u_init;
+        res->weight = 1.0;
+    }
     res->flags = flags;
     res->n_valid = n_valid;
     if (energies)
@@ -418,7 +430,7 @@ void orc_search_level(const double *L, const double *R, const double *G, int w, 
  * else twice the coarser map), so finer patches still get an initial value. */
 void orc_densify_level(int w, int h, const orc_params *p, const double *d_star,
                        const double *weight, const double *coarse, int cw, int ch,
-                       int is_finest, double *out)
+                       int is_finest, const double *L, const double *R, double *out)
 {
     const int ps = p->patch_size;
     const int stride = orc_grid_stride(ps, p->overlap);
@@ -436,8 +448,20 @@ void orc_densify_level(int w, int h, const orc_params *p, const double *d_star,
             for (int r = 0; r < ps; ++r)
                 for (int c = 0; c < ps; ++c) {
                     int x = x0 + c, y = y0 + r;
-                    double d2 = (x - cx) * (x - cx) + (y - cy) * (y - cy);
-                    double wk = weight[k] * exp(-d2 / two_s2);
+                    double wk;
+                    if (p->fusion == ORC_FUSION_DIS) {
+                        /* Eq. 2: inverse squared photometric residual of the
+                         * patch's disparity at this pixel, floored at 1 (R14) */
+                        int ok;
+                        double Rs = sample_row(R, w, y, x - d_star[k], &ok);
+                        if (!ok) continue;
+                        double res_px = Rs - L[(size_t)y * w + x];
+                        double r2 = res_px * res_px;
+                        wk = weight[k] / (r2 > 1.0 ? r2 : 1.0);
+                    } else {
+                        double d2 = (x - cx) * (x - cx) + (y - cy) * (y - cy);
+                        wk = weight[k] * exp(-d2 / two_s2);
+                    }
                     num[(size_t)y * w + x] += wk * d_star[k];
                     den[(size_t)y * w + x] += wk;
                 }
@@ -498,7 +522,8 @@ int orc_match(const double *left, const double *right, int w, int h, const orc_p
     const int top = p->coarsest_scale, fin = p->finest_scale;
     if (ps < 2 || ps > 32 || top < fin || fin < 0 || top > 15 || p->iterations < 0 ||
         p->window_samples < 1 || p->window_samples > 63 || p->window_samples % 2 == 0 ||
-        !(p->overlap >= 0.0 && p->overlap < 1.0))
+        !(p->overlap >= 0.0 && p->overlap < 1.0) ||
+        (p->fusion != ORC_FUSION_BDIS && p->fusion != ORC_FUSION_DIS))
         return -1;
     if (orc_level_dim(w, top) < ps || orc_level_dim(h, top) < ps) return -1;
 
@@ -532,7 +557,7 @@ int orc_match(const double *left, const double *right, int w, int h, const orc_p
         orc_sobel_x(Lp[l], W, H, G);
         orc_search_level(Lp[l], Rp[l], G, W, H, coarse, cw, ch, p, NULL, dst, NULL, wgt, NULL,
                          NULL, NULL);
-        orc_densify_level(W, H, p, dst, wgt, coarse, cw, ch, l == fin, dense);
+        orc_densify_level(W, H, p, dst, wgt, coarse, cw, ch, l == fin, Lp[l], Rp[l], dense);
         free(G);
         free(dst);
         free(wgt);

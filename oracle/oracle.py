@@ -24,6 +24,7 @@ FLAG_SADDLE = 4
 FLAG_GAMMA = 8
 FLAG_EMPTY = 16
 FLAG_UNCONVERGED = 32
+FUSION_BDIS, FUSION_DIS = 0, 1
 DISCARD_FLAGS = FLAG_DIVERGED | FLAG_SADDLE | FLAG_GAMMA | FLAG_EMPTY | FLAG_UNCONVERGED
 
 
@@ -44,13 +45,14 @@ class OracleParams(ctypes.Structure):
         ("window_step", ctypes.c_double),
         ("gamma", ctypes.c_double),
         ("normalize", ctypes.c_int),
+        ("fusion", ctypes.c_int),
     ]
 
     @classmethod
     def make(cls, **kw):
         d = dict(patch_size=8, overlap=0.75, iterations=12, coarsest_scale=4, finest_scale=0,
                  sigma_r=4.0, sigma_s=4.0, window_samples=5, window_step=0.5, gamma=0.75,
-                 normalize=1)
+                 normalize=1, fusion=FUSION_BDIS)
         d.update(kw)
         return cls(**d)
 
@@ -95,7 +97,7 @@ def load():
                                          ctypes.c_void_p, dp]
         lib.orc_search_level.argtypes = [dp, dp, dp, i, i, dp, i, i, pp, dp, dp, dp, dp, ip, ip,
                                          dp]
-        lib.orc_densify_level.argtypes = [i, i, pp, dp, dp, dp, i, i, i, dp]
+        lib.orc_densify_level.argtypes = [i, i, pp, dp, dp, dp, i, i, i, dp, dp, dp]
         lib.orc_upsample.argtypes = [dp, i, i, i, i, i, dp]
         lib.orc_match.argtypes = [dp, dp, i, i, pp, dp]
         lib.orc_match_u8.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i, i, pp, dp]
@@ -210,17 +212,24 @@ def search_level(L, R, G, coarse, params: OracleParams) -> dict:
     return out
 
 
-def densify_level(shape, params: OracleParams, d_star, weight, coarse, is_finest):
+def densify_level(shape, params: OracleParams, d_star, weight, coarse, is_finest, L=None,
+                  R=None):
+    """Dense map of one level; L and R (the level's planes) are needed for DIS fusion."""
     h, w = shape
     d_star, weight = _f64(d_star), _f64(weight)
     out = np.empty((h, w))
+    if params.fusion == FUSION_DIS and (L is None or R is None):
+        raise ValueError("DIS fusion needs the level's L and R planes")
     if coarse is None:
         cp, cw, ch = None, 0, 0
     else:
         coarse = _f64(coarse)
         cp, cw, ch = _dp(coarse), coarse.shape[1], coarse.shape[0]
+    Lc = None if L is None else _f64(L)
+    Rc = None if R is None else _f64(R)
     load().orc_densify_level(w, h, ctypes.byref(params), _dp(d_star), _dp(weight), cp, cw, ch,
-                             int(bool(is_finest)), _dp(out))
+                             int(bool(is_finest)), None if Lc is None else _dp(Lc),
+                             None if Rc is None else _dp(Rc), _dp(out))
     return out
 
 
@@ -263,7 +272,7 @@ def match_stages(left, right, params: OracleParams) -> dict:
         G = sobel_x(Ls[lvl])
         srch = search_level(Ls[lvl], Rs[lvl], G, coarse, params)
         dense = densify_level(Ls[lvl].shape, params, srch["d_star"], srch["weight"], coarse,
-                              lvl == fin)
+                              lvl == fin, Ls[lvl], Rs[lvl])
         levels[lvl] = dict(L=Ls[lvl], R=Rs[lvl], G=G, coarse=coarse, dense=dense, **srch)
         coarse = dense
     out = coarse if fin == 0 else upsample(coarse, fin, left.shape)

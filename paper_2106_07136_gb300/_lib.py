@@ -10,6 +10,7 @@ c_int, c_float, c_size_t, c_void_p = ctypes.c_int, ctypes.c_float, ctypes.c_size
 
 BDIS_OK, BDIS_E_INVALID_ARG, BDIS_E_NOMEM, BDIS_E_CUDA, BDIS_E_TIMEOUT, BDIS_E_UNSUPPORTED = range(6)
 BDIS_U8, BDIS_F32 = 0, 1
+BDIS_FUSION_BDIS, BDIS_FUSION_DIS = 0, 1
 
 # Every symbol include/bdis.h declares.
 EXPORTED = [
@@ -32,7 +33,7 @@ class BdisParams(ctypes.Structure):
         ("patch_size", c_int), ("overlap", c_float), ("iterations", c_int),
         ("coarsest_scale", c_int), ("finest_scale", c_int), ("sigma_r", c_float),
         ("sigma_s", c_float), ("window_samples", c_int), ("window_step", c_float),
-        ("gamma", c_float), ("normalize", c_int),
+        ("gamma", c_float), ("normalize", c_int), ("fusion", c_int),
     ]
 
     def as_dict(self):
@@ -115,7 +116,8 @@ def load():
                                       c_int, c_int, pp, c_void_p, c_void_p,
                                       P(BdisPatchDebug), c_void_p]
     lib.bdis_densify_level.argtypes = [c_int, c_int, c_int, pp, c_void_p, c_void_p, c_void_p,
-                                       c_int, c_int, c_int, c_void_p, c_void_p]
+                                       c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                       c_void_p]
     lib.bdis_upsample.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p,
                                   c_void_p]
     lib.bdis_enable_timing.argtypes = [c_void_p, c_int]

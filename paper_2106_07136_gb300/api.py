@@ -277,7 +277,9 @@ def search_level(L, R, G, coarse, params: BdisParams, debug: bool = True, stream
     return out
 
 
-def densify_level(shape, params: BdisParams, d_star, weight, coarse, is_finest, stream=None):
+def densify_level(shape, params: BdisParams, d_star, weight, coarse, is_finest, L=None, R=None,
+                  stream=None):
+    """Dense map of one level; L and packed R of the level are needed for DIS fusion."""
     d_star, weight = _as_batch(d_star).contiguous(), _as_batch(weight).contiguous()
     b = d_star.shape[0]
     h, w = shape
@@ -287,8 +289,12 @@ def densify_level(shape, params: BdisParams, d_star, weight, coarse, is_finest, 
         cp, cw, ch = coarse.data_ptr(), coarse.shape[2], coarse.shape[1]
     else:
         cp, cw, ch = None, 0, 0
+    Lp = None if L is None else _as_batch(L).contiguous()
+    Rp = None if R is None else _packed(R)
     check(_lib.load().bdis_densify_level(w, h, b, ctypes.byref(params), d_star.data_ptr(),
                                          weight.data_ptr(), cp, cw, ch, int(bool(is_finest)),
+                                         None if Lp is None else Lp.data_ptr(),
+                                         None if Rp is None else Rp.data_ptr(),
                                          out.data_ptr(), _stream_ptr(stream)),
           "bdis_densify_level")
     return out

@@ -240,6 +240,8 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
     da.ch = ch;
     da.cplane = (long long)cw * ch;
     da.is_finest = (l == p.finest_scale);
+    da.L = F(lay.L[l]);
+    da.R2 = F2(lay.R[l]);
     da.out = (l == 0) ? out : F(lay.D[l]);
     {
       Timed tm(h, 3);
@@ -321,7 +323,8 @@ bdis_status check_params(const bdis_params *p) {
   if (p->patch_size < 1 || !(p->overlap >= 0.f && p->overlap < 1.f) || p->iterations < 0 ||
       p->finest_scale < 0 || p->finest_scale > p->coarsest_scale || p->window_samples < 1 ||
       p->window_samples % 2 == 0 || !(p->sigma_r > 0.f) || !(p->sigma_s > 0.f) ||
-      !(p->window_step >= 0.f) || !(p->gamma >= 0.f && p->gamma <= 1.f))
+      !(p->window_step >= 0.f) || !(p->gamma >= 0.f && p->gamma <= 1.f) ||
+      (p->fusion != BDIS_FUSION_BDIS && p->fusion != BDIS_FUSION_DIS))
     return BDIS_E_INVALID_ARG;
   if (p->patch_size < 4 || p->patch_size > kMaxPatch || p->window_samples > kMaxWindow ||
       p->coarsest_scale > 15)
@@ -348,6 +351,7 @@ void bdis_default_params(bdis_params *p) {
   p->window_step = 0.5f;
   p->gamma = 0.75f;
   p->normalize = 1;
+  p->fusion = BDIS_FUSION_BDIS;
 }
 
 const char *bdis_status_string(bdis_status s) {
@@ -593,13 +597,14 @@ bdis_status bdis_search_level(const float *L, const float *R, const float *G, in
 
 bdis_status bdis_densify_level(int width, int height, int count, const bdis_params *p,
                                const float *d_star, const float *weight, const float *coarse,
-                               int coarse_width, int coarse_height, int is_finest, float *out,
-                               void *stream) {
+                               int coarse_width, int coarse_height, int is_finest,
+                               const float *L, const float *R, float *out, void *stream) {
   bdis_status s = check_params(p);
   if (s != BDIS_OK) return s;
   if (!d_star || !weight || !out || count < 1 || width < p->patch_size ||
       height < p->patch_size)
     return BDIS_E_INVALID_ARG;
+  if (p->fusion == BDIS_FUSION_DIS && (!L || !R || !aligned8(R))) return BDIS_E_INVALID_ARG;
   if (coarse && (coarse_width < 1 || coarse_height < 1)) return BDIS_E_INVALID_ARG;
   DensifyArgs a{};
   fill_densify_args(a, width, height, count, *p);
@@ -610,6 +615,8 @@ bdis_status bdis_densify_level(int width, int height, int count, const bdis_para
   a.ch = coarse ? coarse_height : 0;
   a.cplane = (long long)a.cw * a.ch;
   a.is_finest = is_finest ? 1 : 0;
+  a.L = L;
+  a.R2 = reinterpret_cast<const float2 *>(R);
   a.out = out;
   return record_cuda(launch_densify(a, static_cast<cudaStream_t>(stream)));
 }

@@ -78,6 +78,7 @@ struct SearchArgs {
   float step, kappa;
   int nmin_valid, normalize;
   int cols_per_lane;  // fast path: columns of a patch per lane (1, or 2-3)
+  int fusion;         // BDIS_FUSION_*
   float *d_star, *weight;
   float *u_init, *posterior, *energies;
   uint8_t *flags;
@@ -95,6 +96,9 @@ struct DensifyArgs {
   int cw, ch;
   long long cplane;
   int is_finest;
+  int fusion;
+  const float *L;     // DIS fusion: the level's left plane
+  const float2 *R2;   // DIS fusion: the level's packed right plane
   float *out;
 };
 

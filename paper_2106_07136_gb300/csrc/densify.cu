@@ -124,6 +124,57 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
   }
 }
 
+// DIS fusion (Eq. 2): per pixel, every covering patch whose sample x - D*_k is
+// inside the right image, weighted by weight_k / max(r^2, 1) with r the
+// photometric residual R(x - D*_k) - L(x). The weights depend on the pixel
+// and the patch jointly, so this is a direct gather over the covering patches.
+__global__ void __launch_bounds__(256) densify_dis_kernel(const DensifyArgs a) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= a.total) return;
+  const int b = (int)(idx / a.plane);
+  const int rem = (int)(idx - (long long)b * a.plane);
+  const int y = rem / a.w, x = rem - (rem / a.w) * a.w;
+  int ilo, ihi, ilast, jlo, jhi, jlast;
+  cover_range(x, a.w, a.ps, a.stride, a.nx, ilo, ihi, ilast);
+  cover_range(y, a.h, a.ps, a.stride, a.ny, jlo, jhi, jlast);
+  const float *wp = a.weight + (long long)b * a.np;
+  const float *dp = a.d_star + (long long)b * a.np;
+  const float2 *Rrow = a.R2 + (long long)b * a.plane + (long long)y * a.w;
+  const float Lx = __ldg(a.L + (long long)b * a.plane + (long long)y * a.w + x);
+  float num = 0.f, den = 0.f;
+  for (int jj = jlo; jj <= jhi + jlast; ++jj) {
+    const int j = jj > jhi ? a.ny - 1 : jj;
+    for (int ii = ilo; ii <= ihi + ilast; ++ii) {
+      const int i = ii > ihi ? a.nx - 1 : ii;
+      const int kk = j * a.nx + i;
+      const float wk = __ldg(wp + kk);
+      if (!(wk > 0.f)) continue;
+      const float D = __ldg(dp + kk);
+      const float nd = fminf(fmaxf(-D, -1.0e7f), 1.0e7f);
+      const float f = floorf(nd);
+      const int i0 = x + (int)f;
+      const float t = nd - f;
+      if (!(i0 >= 0 && (i0 < a.w - 1 || (i0 == a.w - 1 && t == 0.f)))) continue;
+      const float2 q = __ldg(Rrow + i0);
+      const float r = fmaf(t, q.y, q.x) - Lx;
+      const float wpx = wk / fmaxf(r * r, 1.f);
+      num = fmaf(wpx, D, num);
+      den += wpx;
+    }
+  }
+  float out;
+  if (den > 0.f)
+    out = num / den;
+  else if (a.is_finest)
+    out = __int_as_float(0x7fc00000);
+  else if (a.coarse)
+    out = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, x * 0.5f,
+                                 y * 0.5f);
+  else
+    out = 0.f;
+  a.out[idx] = out;
+}
+
 // Full-size map from level f: bilinear over finite neighbours with positive
 // weight, values times 2^f.
 __global__ void upsample_kernel(const float *__restrict__ M, int mw, int mh, float scale, int w,
@@ -166,10 +217,16 @@ void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_param
   a.ny = grid_count(h, p.patch_size, a.stride);
   a.np = a.nx * a.ny;
   a.two_s2 = 2.f * p.sigma_s * p.sigma_s;
+  a.fusion = p.fusion;
 }
 
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
+  if (a.fusion == BDIS_FUSION_DIS) {
+    const int threads = 256;
+    densify_dis_kernel<<<(unsigned)((a.total + threads - 1) / threads), threads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const int count = (int)(a.total / a.plane);
   const dim3 grid((unsigned)((a.w + kTileX - 1) / kTileX), (unsigned)((a.h + kTileY - 1) / kTileY),
                   (unsigned)count);

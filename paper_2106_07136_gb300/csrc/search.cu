@@ -113,10 +113,35 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
   if (nvalid < a.nmin_valid) flags |= kFlagGamma;
   const bool drop = (flags & kDropFlags) != 0;
   if (write) {
-    a.d_star[k] = D;
-    a.weight[k] = drop ? 0.f : post * (float)nvalid / (float)(ps * ps);
+    if (a.fusion == BDIS_FUSION_DIS) {
+      // DIS fuses every patch (Eq. 2); a runaway patch falls back to its start
+      a.d_star[k] = (flags & kFlagDiverged) ? u0 : D;
+      a.weight[k] = 1.f;
+    } else {
+      a.d_star[k] = D;
+      a.weight[k] = drop ? 0.f : post * (float)nvalid / (float)(ps * ps);
+    }
     if (a.u_init) a.u_init[k] = u0;
     if (a.posterior) a.posterior[k] = post;
+    if (a.flags) a.flags[k] = flags;
+    if (a.n_valid) a.n_valid[k] = nvalid;
+  }
+}
+
+// DIS fusion needs neither the window nor the posterior: flags from the
+// iterations and the gamma count only.
+__device__ __forceinline__ void finish_patch_dis(const SearchArgs &a, long long k, bool write,
+                                                 float D, float u0, float last_step, bool flat,
+                                                 int nvalid, int ps) {
+  uint8_t flags = flat ? kFlagFlat : 0;
+  if (!isfinite(D) || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
+  if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
+  if (nvalid < a.nmin_valid) flags |= kFlagGamma;
+  if (write) {
+    a.d_star[k] = (flags & kFlagDiverged) ? u0 : D;
+    a.weight[k] = 1.f;
+    if (a.u_init) a.u_init[k] = u0;
+    if (a.posterior) a.posterior[k] = 0.f;
     if (a.flags) a.flags[k] = flags;
     if (a.n_valid) a.n_valid[k] = nvalid;
   }
@@ -275,6 +300,10 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
     nc_lane += vc[j] ? 1 : 0;
   }
   const int nvalid = PS * (int)group_sum<G>((float)nv_lane);
+  if (a.fusion == BDIS_FUSION_DIS) {
+    finish_patch_dis(a, k, live && c == 0, D, u0, last_step, flat, nvalid, PS);
+    return;
+  }
   const int nc = PS * (int)group_sum<G>((float)nc_lane);
   // One pass over the rows: per column j, residuals are taken relative to a
   // shift cs[j] (the column's first-row residual at D*), which removes the
@@ -428,6 +457,10 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
   split_disp(D, kd, t);
   const bool v0 = act && fin && sample_ok(x + kd, t, w);
   const int nvalid = ps * __popc(__ballot_sync(kFull, v0) & gbits);
+  if (a.fusion == BDIS_FUSION_DIS) {
+    finish_patch_dis(a, k, live && c == 0, D, u0, last_step, flat, nvalid, ps);
+    return;
+  }
   const int half = (a.s - 1) / 2;
   bool vc = act && fin;
   for (int i = 0; i < a.s; ++i) {
@@ -521,6 +554,7 @@ void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params 
   a.nmin_valid = gamma_min_count(p.gamma, p.patch_size);
   a.normalize = p.normalize ? 1 : 0;
   a.cols_per_lane = search_cols_per_lane();
+  a.fusion = p.fusion;
 }
 
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {

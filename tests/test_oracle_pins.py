@@ -420,26 +420,12 @@ def test_float32_scale_sensitivity_is_bounded(orc):
     than 0.05 px (basin boundaries, saddle and convergence thresholds), but
     no more than 0.1% of them. This is why the float32 kernels are held to
     99.9% of pixels within 0.01 px and at most 0.1% beyond 0.05 px."""
+    from gpu_helpers import oracle_perturbed_match
     pair = synth.make_cfg2()
     p = orc.OracleParams.make()
-    Ls, Rs = [pair.left.astype(float)], [pair.right.astype(float)]
-    for _ in range(p.coarsest_scale):
-        Ls.append(orc.downsample(Ls[-1]))
-        Rs.append(orc.downsample(Rs[-1]))
-
-    def run(rng):
-        coarse = None
-        for lvl in range(p.coarsest_scale, -1, -1):
-            c = coarse
-            if rng is not None and c is not None:
-                c = c * (1 + rng.uniform(-1, 1, c.shape) * 1e-6)
-            s = orc.search_level(Ls[lvl], Rs[lvl], orc.sobel_x(Ls[lvl]), c, p)
-            coarse = orc.densify_level(Ls[lvl].shape, p, s["d_star"], s["weight"], c, lvl == 0)
-        return coarse
-
-    a = run(None)
+    a = oracle_perturbed_match(orc, pair.left, pair.right, p)
     assert np.array_equal(np.isnan(a), np.isnan(orc.match(pair.left, pair.right, p)))
-    b = run(np.random.default_rng(1))
+    b = oracle_perturbed_match(orc, pair.left, pair.right, p, seed=1)
     both = np.isfinite(a) & np.isfinite(b)
     over = int((np.abs(a - b)[both] > 0.05).sum())
     flips = int((np.isnan(a) != np.isnan(b)).sum())
@@ -448,9 +434,71 @@ def test_float32_scale_sensitivity_is_bounded(orc):
     assert (np.abs(a - b)[both] <= 0.01).mean() >= 0.999
 
 
+def test_bayesian_weighting_is_better_conditioned_than_dis(orc):
+    """Sec. 2.2's point in numerical terms: with the posterior and the patch
+    tests the estimate barely moves under float32-sized perturbations of the
+    coarse levels; DIS fusion (Eq. 2), which keeps every patch, moves tens of
+    times more pixels by more than 0.05 px."""
+    from gpu_helpers import oracle_perturbed_match
+    pair = synth.make_cfg2()
+    over = {}
+    for fusion in (orc.FUSION_BDIS, orc.FUSION_DIS):
+        p = orc.OracleParams.make(fusion=fusion)
+        a = oracle_perturbed_match(orc, pair.left, pair.right, p)
+        b = oracle_perturbed_match(orc, pair.left, pair.right, p, seed=1)
+        both = np.isfinite(a) & np.isfinite(b)
+        over[fusion] = int((np.abs(a - b)[both] > 0.05).sum())
+    assert over[orc.FUSION_DIS] > 10 * max(over[orc.FUSION_BDIS], 1)
+
+
 def test_rejects_bad_arguments(orc):
     pair = synth.make_cfg1()
     for kw in [dict(window_samples=4), dict(overlap=1.0), dict(coarsest_scale=6),
                dict(finest_scale=3, coarsest_scale=2), dict(iterations=-1)]:
         with pytest.raises(ValueError):
             orc.match(pair.left, pair.right, small_params(orc, **kw))
+
+
+# ------------------------------------------------------------ DIS mode, Eq. 2
+
+def test_dis_fusion_closed_form_on_linear_texture(orc):
+    """Eq. 2: each covering patch is weighted by 1 / max(r^2, 1) with r the
+    photometric residual of its disparity at the pixel. On L = a(y) x + b(y),
+    R = L(x + d), a patch at D = d + e has r = -a(y) e exactly."""
+    h, w, d, e = 8, 16, 1.5, 0.3
+    pair = synth.make_linear_texture_pair(h, w, d, a0=0.5, a1=2.0, dtype=np.float64)
+    p = small_params(orc, overlap=0.5, fusion=orc.FUSION_DIS)  # origins 0, 4, 8
+    weight = np.array([[1.0, 1.0, 0.0]])
+    dstar = np.array([[d, d + e, 0.0]])
+    out = orc.densify_level((h, w), p, dstar, weight, None, True, pair.left, pair.right)
+    for y in range(h):
+        a = 0.5 + 2.0 * y
+        wb = 1.0 / max(a * a * e * e, 1.0)
+        for x in range(4, 8):
+            np.testing.assert_allclose(out[y, x], (d + wb * (d + e)) / (1.0 + wb), rtol=1e-12)
+        assert np.all(np.isnan(out[y, :2]))  # x - d < 0: no valid sample, not estimated
+        np.testing.assert_allclose(out[y, 2:4], d, rtol=1e-12)  # only the exact patch
+        np.testing.assert_allclose(out[y, 8:12], d + e, rtol=1e-12)  # only the offset patch
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_dis_integer_shift_recovered_exactly(orc, k):
+    pair = synth.make_integer_shift_pair(48, 64, k)
+    out = orc.match(pair.left, pair.right, small_params(orc, fusion=orc.FUSION_DIS))
+    est = np.isfinite(out) & np.isfinite(pair.disp)
+    assert est.sum() > 0.95 * np.isfinite(pair.disp).sum()
+    assert np.max(np.abs(out[est] - k)) < 1e-3
+
+
+def test_bdis_beats_dis_on_surgical_like_pair(orc):
+    """The paper's comparison (Table 1): the Bayesian weighting lowers the
+    error against DIS's residual fusion. On the surgical-like synthetic pair
+    BDIS must have a lower mean absolute error and fewer bad-1 pixels among
+    those it estimates."""
+    pair = synth.make_cfg2()
+    b = synth.error_stats(orc.match(pair.left, pair.right, orc.OracleParams.make()), pair.disp)
+    dis = synth.error_stats(orc.match(pair.left, pair.right,
+                                      orc.OracleParams.make(fusion=orc.FUSION_DIS)), pair.disp)
+    assert b["mean_abs"] < dis["mean_abs"]
+    assert b["median_abs"] < dis["median_abs"]
+    assert dis["valid"] >= b["valid"]  # DIS estimates more pixels (Table 1's valid counts)

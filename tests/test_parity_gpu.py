@@ -10,8 +10,9 @@ import torch
 
 import paper_2106_07136_gb300 as bd
 import synth
-from gpu_helpers import (DENSE_ATOL, DROP, DSTAR_ATOL, POST_ATOL, PYR_ATOL, assert_e2e, dev,
-                         explained_flag_mismatch, host, oracle_unstable)
+from gpu_helpers import (DENSE_ATOL, DROP, DSTAR_ATOL, POST_ATOL, PYR_ATOL, assert_e2e,
+                         assert_e2e_within_self_sensitivity, dev, explained_flag_mismatch, host,
+                         oracle_unstable)
 
 pytestmark = pytest.mark.gpu
 
@@ -300,3 +301,38 @@ def test_full_hd_frame(orc, matcher):
     ref = orc.match(pair.left, pair.right, op)
     out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
     assert_e2e(out, ref, "1920x1080")
+
+
+# ----------------------------------------------------- DIS fusion (Eq. 2)
+
+def test_dis_search_and_densify_stages(orc, cfg1):
+    kw = dict(CFG1, fusion=1)
+    gp, op = params(orc, **kw)
+    st = orc.match_stages(cfg1.left, cfg1.right, op)
+    for lvl in (2, 0):
+        o = st["levels"][lvl]
+        coarse = None if o["coarse"] is None else dev(o["coarse"])
+        R2 = bd.pack_right(dev(o["R"]))
+        g = bd.search_level(dev(o["L"]), R2, dev(o["G"]), coarse, gp)
+        g = {k: host(v)[0] for k, v in g.items()}
+        assert np.all(g["weight"] == 1.0) and np.all(o["weight"] == 1.0)
+        unstable = oracle_unstable(orc, o, op)
+        same = ~unstable & ((o["flags"] & 2) == ((g["flags"].astype(int)) & 2))
+        assert same.mean() > 0.998
+        np.testing.assert_allclose(g["d_star"][same], o["d_star"][same], atol=DSTAR_ATOL)
+        # densify with the oracle's patches on both sides
+        ref = orc.densify_level(o["L"].shape, op, o["d_star"], o["weight"], o["coarse"], lvl == 0,
+                                o["L"], o["R"])
+        out = host(bd.densify_level(o["L"].shape, gp, dev(o["d_star"]), dev(o["weight"]), coarse,
+                                    lvl == 0, dev(o["L"]), R2))[0]
+        assert np.array_equal(np.isnan(out), np.isnan(ref))
+        np.testing.assert_allclose(out[~np.isnan(ref)], ref[~np.isnan(ref)], atol=DENSE_ATOL)
+
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_dis_e2e(orc, cfg1, cfg2, matcher, which):
+    pair, kw = (cfg1, CFG1) if which == "cfg1" else (cfg2, CFG2)
+    gp, op = params(orc, **dict(kw, fusion=1))
+    ref = orc.match(pair.left, pair.right, op)
+    out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
+    assert_e2e_within_self_sensitivity(out, ref, orc, pair.left, pair.right, op, f"dis {which}")
