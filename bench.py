@@ -452,11 +452,55 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     torch.cuda.synchronize()
     import synth
     U = Lh.shape[0]
+    res["variants"]["mixed_batch_graph"] = measure_mixed_batch(args, bd, device, stream)
     res["variants"]["dis_fusion"] = {
         "value": B * kk / (ev0.elapsed_time(ev1) / 1e3), "unit": "pairs/s",
         "accuracy_vs_ground_truth": synth.error_stats(out[:U].cpu().numpy(), Dgt),
         "l2": "not flushed (back-to-back steps)"}
     return res
+
+
+MIXED_GROUPS = [(64, 240, 320), (96, 480, 640), (64, 720, 1280), (32, 1080, 1920)]
+
+
+def measure_mixed_batch(args, bd, device, stream, unique=4):
+    """256 pairs of four sizes (disparity range width/10, scales 4..0) as one
+    autotuned CUDA-graph plan; pairs/s over graph launches."""
+    import torch
+    import synth
+    groups = []
+    for gi, (b, h, w) in enumerate(MIXED_GROUPS):
+        pairs = [synth.make_cfg2(seed=synth.stereo.pair_seed(3, 100 * gi + i), h=h, w=w)
+                 for i in range(unique)]
+        L = np.stack([pairs[i % unique].left for i in range(b)])
+        R = np.stack([pairs[i % unique].right for i in range(b)])
+        groups.append((torch.from_numpy(L).to(device), torch.from_numpy(R).to(device),
+                       torch.empty((b, h, w), dtype=torch.float32, device=device)))
+    params = bd.default_params(**params_kw(args.patch))
+    t0 = time.perf_counter()
+    plan = bd.Plan(groups, params, autotune=True, device=device, stream=stream)
+    build_s = time.perf_counter() - t0
+    for _ in range(3):
+        plan.run(stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(3, args.steps // 3)
+    ev0.record(stream)
+    for _ in range(k):
+        plan.run(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / k
+    n = sum(g[0] for g in MIXED_GROUPS)
+    mpix = sum(g[0] * g[1] * g[2] for g in MIXED_GROUPS) / 1e6
+    choice = {f"{w}x{h}": plan.choice(gi, 0) for gi, (_, h, w) in enumerate(MIXED_GROUPS)}
+    out = {"value": n / (ms / 1e3), "unit": "pairs/s", "mpix_per_s": mpix / (ms / 1e3),
+           "ms_per_step": ms, "pairs": n,
+           "groups": [f"{b}x{w}x{h}" for b, h, w in MIXED_GROUPS],
+           "workspace_gb": plan.workspace_bytes / 1e9, "plan_build_s": build_s,
+           "level0_choices": choice, "l2": "not flushed (back-to-back graph launches)"}
+    plan.close()
+    return out
 
 
 if __name__ == "__main__":

@@ -264,6 +264,43 @@ int bdis_get_search_variant(void);
  * `stream` and waits for them. */
 bdis_status bdis_probe_fp32_tflops(int iterations, double *tflops, void *stream);
 
+/* ------------------------------------------------------------ batch plans
+ * Mixed-resolution batches (the method is per pair, Sec. 2; this is how many
+ * pairs of several sizes share the GPU). A plan fixes `n_groups` groups, each
+ * a batch of equally sized pairs with its device images and output, all
+ * bound by ADDRESS: refill the images and rerun. Each group gets its own
+ * workspace (so groups run concurrently); the whole sequence is captured once
+ * into a CUDA graph with one branch per group, and bdis_plan_run is a single
+ * graph launch on `stream`. With BDIS_PLAN_AUTOTUNE, creation first runs each
+ * group once and times, per level, the candidate search lane layouts (1 or 2
+ * columns per lane) and block sizes (64, 128) and the densify tile heights
+ * (8, 16, 32) on that data, keeping the fastest; results are the same up to
+ * float rounding whatever is chosen. bdis_plan_create synchronises `stream`
+ * (autotuning reads the inputs) and may take a second; run is asynchronous. */
+#define BDIS_PLAN_AUTOTUNE 1
+
+typedef struct {
+    bdis_image left, right;  /* device, as for bdis_match */
+    float *disparity_out;    /* device, count x height x width */
+} bdis_group;
+
+typedef struct {
+    int search_columns_per_lane; /* 0 = default */
+    int search_block_threads;    /* 0 = default (128) */
+    int densify_tile_height;     /* 0 = default (32) */
+    size_t workspace_bytes;      /* of the whole group */
+} bdis_plan_choice;
+
+typedef struct bdis_plan bdis_plan;
+
+bdis_status bdis_plan_create(int device, const bdis_group *groups, int n_groups,
+                             const bdis_params *p, int flags, void *stream, bdis_plan **out);
+bdis_status bdis_plan_run(bdis_plan *plan, void *stream);
+/* Launch choices for one group and pyramid level (after autotuning). */
+bdis_status bdis_plan_info(const bdis_plan *plan, int group, int level, bdis_plan_choice *out);
+size_t bdis_plan_workspace_bytes(const bdis_plan *plan);
+void bdis_plan_destroy(bdis_plan *plan);
+
 /* ----------------------------------------------------------- no allocation
  * Some callers cannot allocate GPU memory: a hard real-time loop that froze
  * its memory map after start-up, a plug-in that runs inside a host process

@@ -7,6 +7,7 @@ every call raises.
 """
 from .api import (  # noqa: F401
     Matcher,
+    Plan,
     default_params,
     densify_level,
     grid,

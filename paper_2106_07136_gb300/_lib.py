@@ -20,8 +20,11 @@ EXPORTED = [
     "bdis_prepare_level0", "bdis_pyramid_level", "bdis_search_level", "bdis_densify_level",
     "bdis_upsample", "bdis_enable_timing", "bdis_read_timing", "bdis_pack_right",
     "bdis_match_static", "bdis_probe_fp32_tflops", "bdis_set_search_variant",
-    "bdis_get_search_variant",
+    "bdis_get_search_variant", "bdis_plan_create", "bdis_plan_run", "bdis_plan_info",
+    "bdis_plan_workspace_bytes", "bdis_plan_destroy",
 ]
+
+BDIS_PLAN_AUTOTUNE = 1
 
 STATIC_SCRATCH_BYTES = 24 << 20  # BDIS_STATIC_SCRATCH_BYTES
 
@@ -50,6 +53,15 @@ class BdisImage(ctypes.Structure):
 class BdisPatchDebug(ctypes.Structure):
     _fields_ = [("u_init", c_void_p), ("posterior", c_void_p), ("energies", c_void_p),
                 ("flags", c_void_p), ("n_valid", c_void_p)]
+
+
+class BdisGroup(ctypes.Structure):
+    _fields_ = [("left", BdisImage), ("right", BdisImage), ("disparity_out", c_void_p)]
+
+
+class BdisPlanChoice(ctypes.Structure):
+    _fields_ = [("search_columns_per_lane", c_int), ("search_block_threads", c_int),
+                ("densify_tile_height", c_int), ("workspace_bytes", c_size_t)]
 
 
 class BdisTiming(ctypes.Structure):
@@ -107,6 +119,14 @@ def load():
     lib.bdis_prepare_level0.argtypes = [ip, ip, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.bdis_pyramid_level.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
                                        c_void_p, c_void_p, c_void_p]
+    lib.bdis_plan_create.argtypes = [c_int, P(BdisGroup), c_int, pp, c_int, c_void_p,
+                                     P(c_void_p)]
+    lib.bdis_plan_run.argtypes = [c_void_p, c_void_p]
+    lib.bdis_plan_info.argtypes = [c_void_p, c_int, c_int, P(BdisPlanChoice)]
+    lib.bdis_plan_workspace_bytes.argtypes = [c_void_p]
+    lib.bdis_plan_workspace_bytes.restype = c_size_t
+    lib.bdis_plan_destroy.argtypes = [c_void_p]
+    lib.bdis_plan_destroy.restype = None
     lib.bdis_set_search_variant.argtypes = [c_int]
     lib.bdis_get_search_variant.restype = c_int
     lib.bdis_probe_fp32_tflops.argtypes = [c_int, P(ctypes.c_double), c_void_p]

@@ -195,6 +195,66 @@ def probe_fp32_tflops(iterations: int = 1 << 16, stream=None) -> float:
     return t.value
 
 
+class Plan:
+    """Mixed-resolution batch as one CUDA graph (bdis_plan_create / run).
+
+    groups: list of (left, right, out) CUDA tensors, each (B, H, W) with one
+    size per group; the plan binds their addresses, so refill them in place
+    between runs."""
+
+    def __init__(self, groups, params: BdisParams = None, autotune: bool = True, device=None,
+                 stream=None):
+        self._lib = _lib.load()
+        params = params if params is not None else default_params()
+        self._keep = []
+        arr = (_lib.BdisGroup * len(groups))()
+        for i, (left, right, out) in enumerate(groups):
+            lb, rb = _as_batch(left), _as_batch(right)
+            if not (out.is_contiguous() and out.dtype == torch.float32
+                    and out.numel() == lb.numel()):
+                raise ValueError("each output must be a dense float32 tensor like its images")
+            arr[i].left = image_desc(lb)
+            arr[i].right = image_desc(rb)
+            arr[i].disparity_out = out.data_ptr()
+            self._keep += [lb, rb, out]
+        dev = torch.device("cuda", torch.cuda.current_device()) if device is None else \
+            torch.device(device)
+        h = ctypes.c_void_p()
+        check(self._lib.bdis_plan_create(dev.index or 0, arr, len(groups), ctypes.byref(params),
+                                         _lib.BDIS_PLAN_AUTOTUNE if autotune else 0,
+                                         _stream_ptr(stream), ctypes.byref(h)),
+              "bdis_plan_create")
+        self._h = h
+        self.n_groups = len(groups)
+        self.levels = range(params.finest_scale, params.coarsest_scale + 1)
+
+    def run(self, stream=None):
+        check(self._lib.bdis_plan_run(self._h, _stream_ptr(stream)), "bdis_plan_run")
+
+    def choice(self, group: int, level: int) -> dict:
+        c = _lib.BdisPlanChoice()
+        check(self._lib.bdis_plan_info(self._h, group, level, ctypes.byref(c)), "bdis_plan_info")
+        return {"search_columns_per_lane": c.search_columns_per_lane,
+                "search_block_threads": c.search_block_threads,
+                "densify_tile_height": c.densify_tile_height,
+                "workspace_bytes": int(c.workspace_bytes)}
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._lib.bdis_plan_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bdis_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ------------------------------------------------------------------ steps
 
 def prepare_level0(left: torch.Tensor, right: torch.Tensor, stream=None):

@@ -40,17 +40,9 @@ constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
-// Device workspace of one bdis_match call. Offsets from the workspace base.
-struct Layout {
-  int levels = 0;  // coarsest + 1
-  int lw[16] = {0}, lh[16] = {0};
-  size_t L[16] = {0}, R[16] = {0}, G[16] = {0}, D[16] = {0};
-  size_t d_star = 0, weight = 0;
-  size_t in_left = 0, in_right = 0, out = 0;  // host-path staging
-  size_t bytes = 0;
-};
+}  // namespace
 
-Layout plan(int w, int h, int count, const bdis_params &p, bool host_staging) {
+Layout plan_layout(int w, int h, int count, const bdis_params &p, bool host_staging) {
   Layout lay;
   size_t off = 0;
   auto take = [&](size_t n) {
@@ -85,6 +77,8 @@ Layout plan(int w, int h, int count, const bdis_params &p, bool host_staging) {
   lay.bytes = off;
   return lay;
 }
+
+namespace {
 
 bdis_status ensure_workspace(bdis_handle *h, size_t bytes) {
   if (bytes <= h->ws_bytes) return BDIS_OK;
@@ -189,9 +183,51 @@ struct Timed {
   }
 };
 
+// Arguments of the search and densify launches of level l (the coarser map
+// of level l+1 seeds the patches; level 0 densifies into `out`).
+SearchArgs level_search_args(char *base, const Layout &lay, const bdis_params &p, int count,
+                             int l) {
+  auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
+  SearchArgs sa{};
+  fill_search_args(sa, lay.lw[l], lay.lh[l], count, p);
+  sa.L = F(lay.L[l]);
+  sa.R2 = reinterpret_cast<const float2 *>(base + lay.R[l]);
+  sa.G = F(lay.G[l]);
+  if (l < p.coarsest_scale) {
+    sa.coarse = F(lay.D[l + 1]);
+    sa.cw = lay.lw[l + 1];
+    sa.ch = lay.lh[l + 1];
+    sa.cplane = (long long)sa.cw * sa.ch;
+  }
+  sa.d_star = F(lay.d_star);
+  sa.weight = F(lay.weight);
+  return sa;
+}
+
+DensifyArgs level_densify_args(char *base, const Layout &lay, const bdis_params &p, int count,
+                               int l, float *out) {
+  auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
+  DensifyArgs da{};
+  fill_densify_args(da, lay.lw[l], lay.lh[l], count, p);
+  da.d_star = F(lay.d_star);
+  da.weight = F(lay.weight);
+  if (l < p.coarsest_scale) {
+    da.coarse = F(lay.D[l + 1]);
+    da.cw = lay.lw[l + 1];
+    da.ch = lay.lh[l + 1];
+    da.cplane = (long long)da.cw * da.ch;
+  }
+  da.is_finest = (l == p.finest_scale);
+  da.L = F(lay.L[l]);
+  da.R2 = reinterpret_cast<const float2 *>(base + lay.R[l]);
+  da.out = (l == 0) ? out : F(lay.D[l]);
+  return da;
+}
+
 // The whole method on device images already checked; `out` dense device.
 bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &right,
-                      const bdis_params &p, float *out, const Layout &lay) {
+                      const bdis_params &p, float *out, const Layout &lay,
+                      const Tuning *tune = nullptr) {
   char *base = static_cast<char *>(h->ws);
   auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
   auto F2 = [&](size_t off) { return reinterpret_cast<float2 *>(base + off); };
@@ -211,47 +247,24 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
     }
     if (e != cudaSuccess) return record_cuda(e);
   }
-  const float *coarse = nullptr;
-  int cw = 0, ch = 0;
   for (int l = p.coarsest_scale; l >= p.finest_scale; --l) {
-    const int w = lay.lw[l], hh = lay.lh[l];
-    SearchArgs sa{};
-    fill_search_args(sa, w, hh, count, p);
-    sa.L = F(lay.L[l]);
-    sa.R2 = F2(lay.R[l]);
-    sa.G = F(lay.G[l]);
-    sa.coarse = coarse;
-    sa.cw = cw;
-    sa.ch = ch;
-    sa.cplane = (long long)cw * ch;
-    sa.d_star = F(lay.d_star);
-    sa.weight = F(lay.weight);
+    SearchArgs sa = level_search_args(base, lay, p, count, l);
+    if (tune) apply_tuning(sa, tune->level[l]);
     {
       Timed tm(h, 2);
       e = launch_search(sa, st);
     }
     if (e != cudaSuccess) return record_cuda(e);
-    DensifyArgs da{};
-    fill_densify_args(da, w, hh, count, p);
-    da.d_star = F(lay.d_star);
-    da.weight = F(lay.weight);
-    da.coarse = coarse;
-    da.cw = cw;
-    da.ch = ch;
-    da.cplane = (long long)cw * ch;
-    da.is_finest = (l == p.finest_scale);
-    da.L = F(lay.L[l]);
-    da.R2 = F2(lay.R[l]);
-    da.out = (l == 0) ? out : F(lay.D[l]);
+    DensifyArgs da = level_densify_args(base, lay, p, count, l, out);
+    if (tune) apply_tuning(da, tune->level[l]);
     {
       Timed tm(h, 3);
       e = launch_densify(da, st);
     }
     if (e != cudaSuccess) return record_cuda(e);
-    coarse = da.out;
-    cw = w;
-    ch = hh;
   }
+  const float *coarse = p.finest_scale == 0 ? out : F(lay.D[p.finest_scale]);
+  const int cw = lay.lw[p.finest_scale], ch = lay.lh[p.finest_scale];
   if (p.finest_scale > 0) {
     Timed tm(h, 4);
     e = launch_upsample(coarse, cw, ch, p.finest_scale, left.width, left.height, count, out, st);
@@ -274,7 +287,7 @@ bdis_status bind_device(const bdis_handle *h) {
 }  // namespace
 
 size_t match_scratch_bytes(int w, int h, int count, const bdis_params &p) {
-  return plan(w, h, count, p, false).bytes;
+  return plan_layout(w, h, count, p, false).bytes;
 }
 
 bdis_status check_match_args(const bdis_image *left, const bdis_image *right,
@@ -297,16 +310,85 @@ bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right
 
 bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
                          const bdis_image &left, const bdis_image &right, const bdis_params &p,
-                         float *out) {
+                         float *out, const Tuning *tune) {
   bdis_handle view;  // borrows the caller's scratch; owns nothing, times nothing
   view.stream = stream;
   view.ws = scratch;
   view.ws_bytes = scratch_bytes;
-  const Layout lay = plan(left.width, left.height, left.count, p, false);
+  const Layout lay = plan_layout(left.width, left.height, left.count, p, false);
   if (lay.bytes > scratch_bytes) return BDIS_E_UNSUPPORTED;
-  bdis_status s = run_match(&view, left, right, p, out, lay);
+  (void)0;
+  bdis_status s = run_match(&view, left, right, p, out, lay, tune);
   view.ws = nullptr;
   return s;
+}
+
+namespace {
+
+// Mean milliseconds of `reps` back-to-back calls of fn on st, after one warm-up.
+template <typename Fn>
+float time_launches(cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, int reps, Fn fn,
+                    cudaError_t *err) {
+  cudaError_t e = fn();
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = fn();
+  cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  *err = e;
+  return ms / reps;
+}
+
+}  // namespace
+
+bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t st,
+                           const bdis_image &left, const bdis_image &right,
+                           const bdis_params &p, float *out, Tuning *tune) {
+  *tune = Tuning{};
+  // one full run fills every level's planes and the coarse maps the levels read
+  bdis_status s = run_match_in(scratch, scratch_bytes, st, left, right, p, out, nullptr);
+  if (s != BDIS_OK) return s;
+  const Layout lay = plan_layout(left.width, left.height, left.count, p, false);
+  char *base = static_cast<char *>(scratch);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const bool fixed = p.window_samples == 5 && p.window_step == 0.5f &&
+                     (p.patch_size == 8 || p.patch_size == 12 || p.patch_size == 16);
+  const int reps = 3;
+  for (int l = p.coarsest_scale; l >= p.finest_scale && e == cudaSuccess; --l) {
+    // search: lane layout x block size
+    float best = 1e30f;
+    for (int cpl = 1; cpl <= (fixed ? 2 : 1) && e == cudaSuccess; ++cpl)
+      for (int bt = 64; bt <= 128 && e == cudaSuccess; bt *= 2) {
+        SearchArgs sa = level_search_args(base, lay, p, left.count, l);
+        sa.cols_per_lane = cpl;
+        sa.block_threads = bt;
+        const float ms = time_launches(st, e0, e1, reps, [&] { return launch_search(sa, st); }, &e);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          tune->level[l].search_cpl = cpl;
+          tune->level[l].search_threads = bt;
+        }
+      }
+    // densify: tile height (the separable BDIS kernel only)
+    if (p.fusion == BDIS_FUSION_BDIS) {
+      best = 1e30f;
+      for (int ty = 8; ty <= 32 && e == cudaSuccess; ty *= 2) {
+        DensifyArgs da = level_densify_args(base, lay, p, left.count, l, out);
+        da.tile_y = ty;
+        const float ms = time_launches(st, e0, e1, reps, [&] { return launch_densify(da, st); }, &e);
+        if (e == cudaSuccess && ms < best) {
+          best = ms;
+          tune->level[l].densify_tile_y = ty;
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return record_cuda(e);
 }
 
 void set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
@@ -423,7 +505,7 @@ bdis_status bdis_reserve(bdis_handle *h, int width, int height, int count, const
   if (s != BDIS_OK) return s;
   s = bind_device(h);
   if (s != BDIS_OK) return s;
-  return ensure_workspace(h, plan(width, height, count, *p, false).bytes);
+  return ensure_workspace(h, plan_layout(width, height, count, *p, false).bytes);
 }
 
 size_t bdis_workspace_bytes(const bdis_handle *h) { return h ? h->ws_bytes : 0; }
@@ -495,7 +577,7 @@ bdis_status bdis_match(bdis_handle *h, const bdis_image *left, const bdis_image 
   if (check_device_ptr(left->data) != BDIS_OK || check_device_ptr(right->data) != BDIS_OK ||
       check_device_ptr(disparity_out) != BDIS_OK)
     return BDIS_E_INVALID_ARG;
-  const Layout lay = plan(left->width, left->height, left->count, *p, false);
+  const Layout lay = plan_layout(left->width, left->height, left->count, *p, false);
   s = ensure_workspace(h, lay.bytes);
   if (s != BDIS_OK) return s;
   return run_match(h, *left, *right, *p, disparity_out, lay);
@@ -511,7 +593,7 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
   if (s != BDIS_OK) return s;
   s = bind_device(h);
   if (s != BDIS_OK) return s;
-  const Layout lay = plan(width, height, count, *p, true);
+  const Layout lay = plan_layout(width, height, count, *p, true);
   s = ensure_workspace(h, lay.bytes);
   if (s != BDIS_OK) return s;
   char *base = static_cast<char *>(h->ws);

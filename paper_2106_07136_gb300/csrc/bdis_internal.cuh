@@ -64,6 +64,29 @@ inline int gamma_min_count(float gamma, int ps) {
   return n;
 }
 
+// Per-level launch choices (0 = the library default). The autotuner of
+// bdis_plan_create fills them by timing the candidates on the real data.
+struct LevelTuning {
+  int search_cpl = 0;      // fast search path: 1 column per lane, or 2 (wide)
+  int search_threads = 0;  // search block size: 64 or 128
+  int densify_tile_y = 0;  // densify tile height: 8, 16 or 32
+};
+struct Tuning {
+  LevelTuning level[16];
+};
+
+// Device workspace of one match call. Offsets from the workspace base.
+struct Layout {
+  int levels = 0;  // coarsest + 1
+  int lw[16] = {0}, lh[16] = {0};
+  size_t L[16] = {0}, R[16] = {0}, G[16] = {0}, D[16] = {0};
+  size_t d_star = 0, weight = 0;
+  size_t in_left = 0, in_right = 0, out = 0;  // host-path staging
+  size_t bytes = 0;
+};
+
+Layout plan_layout(int w, int h, int count, const bdis_params &p, bool host_staging);
+
 struct SearchArgs {
   const float *L, *G;
   const float2 *R2;  // packed right plane: (R[x], R[x+1] - R[x]) per pixel
@@ -78,6 +101,7 @@ struct SearchArgs {
   float step, kappa;
   int nmin_valid, normalize;
   int cols_per_lane;  // fast path: columns of a patch per lane (1, or 2-3)
+  int block_threads;  // 0 = 128
   int fusion;         // BDIS_FUSION_*
   float *d_star, *weight;
   float *u_init, *posterior, *energies;
@@ -97,6 +121,7 @@ struct DensifyArgs {
   long long cplane;
   int is_finest;
   int fusion;
+  int tile_y;         // 0 = 32
   const float *L;     // DIS fusion: the level's left plane
   const float2 *R2;   // DIS fusion: the level's packed right plane
   float *out;
@@ -135,6 +160,19 @@ bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right
                                  const float *disparity_out);
 bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
                          const bdis_image &left, const bdis_image &right, const bdis_params &p,
-                         float *out);
+                         float *out, const Tuning *tune = nullptr);
+// Fill `tune` for every searched level by timing the candidate launches on
+// the given data (after one full run that fills the level planes).
+bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t stream,
+                           const bdis_image &left, const bdis_image &right,
+                           const bdis_params &p, float *out, Tuning *tune);
+
+inline void apply_tuning(SearchArgs &a, const LevelTuning &t) {
+  if (t.search_cpl) a.cols_per_lane = t.search_cpl;
+  if (t.search_threads) a.block_threads = t.search_threads;
+}
+inline void apply_tuning(DensifyArgs &a, const LevelTuning &t) {
+  if (t.densify_tile_y) a.tile_y = t.densify_tile_y;
+}
 
 }  // namespace bdis

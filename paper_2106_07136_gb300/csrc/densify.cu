@@ -55,8 +55,9 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
     mask[tid] = expf(-(m * m) / a.two_s2);
   }
   const int b = blockIdx.z;
-  const int X0 = blockIdx.x * kTileX, Y0 = blockIdx.y * kTileY;
-  const int ylast = min(Y0 + kTileY, a.h) - 1;
+  const int tile_y = a.tile_y > 0 ? a.tile_y : kTileY;  // 8, 16 or 32
+  const int X0 = blockIdx.x * kTileX, Y0 = blockIdx.y * tile_y;
+  const int ylast = min(Y0 + tile_y, a.h) - 1;
   // patch rows touching the tile: regular rows [jlo, jhi] and maybe the last
   int jlo, jhi, jl_unused, hlast_lo, hlast_hi;
   cover_range(Y0, a.h, a.ps, a.stride, a.ny, jlo, jl_unused, hlast_lo);
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
   // pass 2: y-weighted sums over the covering rows of each pixel
   const int xx = tid & (kTileX - 1);
   const int x = X0 + xx;
-  for (int yy = tid / kTileX; yy < kTileY; yy += blockDim.x / kTileX) {
+  for (int yy = tid / kTileX; yy < tile_y; yy += blockDim.x / kTileX) {
     const int y = Y0 + yy;
     if (x >= a.w || y >= a.h) continue;
     int lo, hi, last;
@@ -228,7 +229,8 @@ cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const int count = (int)(a.total / a.plane);
-  const dim3 grid((unsigned)((a.w + kTileX - 1) / kTileX), (unsigned)((a.h + kTileY - 1) / kTileY),
+  const int tile_y = a.tile_y > 0 ? a.tile_y : kTileY;
+  const dim3 grid((unsigned)((a.w + kTileX - 1) / kTileX), (unsigned)((a.h + tile_y - 1) / tile_y),
                   (unsigned)count);
   densify_kernel<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();

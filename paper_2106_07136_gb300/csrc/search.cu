@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
 template <int PS, int CPL, int MINB>
 cudaError_t launch_fixed(const SearchArgs &a, cudaStream_t st) {
   constexpr int G = pow2_at_least((PS + CPL - 1) / CPL);
-  const int threads = 128, per_block = threads / G;
+  const int threads = a.block_threads == 64 ? 64 : 128, per_block = threads / G;
   const int count = (int)(a.total / a.np);
   const dim3 grid((unsigned)((a.np + per_block - 1) / per_block), (unsigned)count);
   search_fixed_kernel<PS, CPL, MINB><<<grid, threads, 0, st>>>(a);
