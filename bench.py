@@ -453,11 +453,53 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     import synth
     U = Lh.shape[0]
     res["variants"]["mixed_batch_graph"] = measure_mixed_batch(args, bd, device, stream)
+    res["serving"] = measure_serving(args, bd, device)
     res["variants"]["dis_fusion"] = {
         "value": B * kk / (ev0.elapsed_time(ev1) / 1e3), "unit": "pairs/s",
         "accuracy_vs_ground_truth": synth.error_stats(out[:U].cpu().numpy(), Dgt),
         "l2": "not flushed (back-to-back steps)"}
     return res
+
+
+def measure_serving(args, bd, device, seconds=3.0, rate=2000.0, videos=4, frames=4):
+    """64 synthetic stereo video streams (32 at 1280x1024, 32 at 640x480) with
+    Poisson arrivals at `rate` pairs/s, served with continuous batching and
+    per-stream warm starts; p50/p99 latency from arrival to the disparity
+    being back in host memory."""
+    import torch
+    import synth
+    from paper_2106_07136_gb300 import serve
+    shapes = [(1024, 1280), (480, 640)]
+    clips = {}
+    for si, (h, w) in enumerate(shapes):
+        for v in range(videos):
+            vs = synth.VideoStream(seed=synth.stereo.pair_seed(5, 100 * si + v), h=h, w=w)
+            clips[(si, v)] = [(torch.from_numpy(f.left).pin_memory(),
+                               torch.from_numpy(f.right).pin_memory())
+                              for f in (vs.next() for _ in range(frames))]
+    n_streams = 64
+    frames_by_stream = {sid: clips[(sid % 2, (sid // 2) % videos)] for sid in range(n_streams)}
+    params = bd.default_params(**params_kw(args.patch))
+    server = serve.StereoServer(shapes, params, device=device, max_batch=16, inflight=3,
+                                keep_results=False)
+    admitted = [server.admit(sid, shapes[sid % 2]) for sid in range(n_streams)]
+    n = int(rate * seconds)
+    rng = np.random.Generator(np.random.PCG64(2026))
+    order = [int(x) for x in rng.integers(0, n_streams, size=n)]
+    arrivals = serve.poisson_arrivals(rate, n, seed=2027)
+    # warm-up: one frame per stream, untimed
+    serve.simulate(server, frames_by_stream, np.zeros(n_streams), list(range(n_streams)))
+    server.completed.clear()
+    reqs, wall = serve.simulate(server, frames_by_stream, arrivals, order)
+    server.close()
+    stats = serve.StereoServer.latency_stats(reqs)
+    mpix = sum(shapes[r.stream_id % 2][0] * shapes[r.stream_id % 2][1] for r in reqs) / 1e6
+    return {"offered_pairs_per_s": rate, "value": len(reqs) / wall, "unit": "pairs/s",
+            "mpix_per_s": mpix / wall, "streams": n_streams, "admitted": int(sum(admitted)),
+            "latency": stats, "requests": len(reqs), "seconds": wall,
+            "workload": "32 streams 1280x1024 + 32 streams 640x480, drifting disparity, "
+                        "Poisson arrivals, continuous batching (max batch 16, 3 in flight), "
+                        "warm start from the previous frame"}
 
 
 MIXED_GROUPS = [(64, 240, 320), (96, 480, 640), (64, 720, 1280), (32, 1080, 1920)]

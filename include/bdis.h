@@ -184,6 +184,17 @@ bdis_status bdis_read_timing(bdis_handle *h, bdis_timing *out);
 bdis_status bdis_match(bdis_handle *h, const bdis_image *left, const bdis_image *right,
                        const bdis_params *p, float *disparity_out);
 
+/* Warm start (for video): as bdis_match, but the coarsest searched level
+ * starts from `prev`, a previous disparity of the same scene (device, count x
+ * H x W float, NaN allowed; e.g. the last frame's output), instead of 0. The
+ * seed map at level coarsest+1 is the mean of prev's finite values over the
+ * 2^(coarsest+1) block centred on each sample point, divided by
+ * 2^(coarsest+1), or 0 where none is finite; it seeds the coarsest patches
+ * and the pixels that level carries. prev may alias disparity_out (it is
+ * read before the output is written). prev NULL = bdis_match. */
+bdis_status bdis_match_warm(bdis_handle *h, const bdis_image *left, const bdis_image *right,
+                            const bdis_params *p, const float *prev, float *disparity_out);
+
 /* Same, with HOST buffers: left/right are `count` dense width x height uint8
  * images in host memory, disparity_out a dense host float array. The call
  * copies in, matches, copies out and waits for the stream. Pinned host memory
@@ -244,6 +255,12 @@ bdis_status bdis_densify_level(int width, int height, int count, const bdis_para
                                const float *d_star, const float *weight, const float *coarse,
                                int coarse_width, int coarse_height, int is_finest,
                                const float *L, const float *R, float *out, void *stream);
+
+/* The warm-start seed map alone: level `level` (1..16) of a count x H x W
+ * previous disparity, as described at bdis_match_warm. out: count x
+ * ceil(H/2^level) x ceil(W/2^level). */
+bdis_status bdis_warm_map(const float *prev, int width, int height, int level, int count,
+                          float *out, void *stream);
 
 /* Bring a map of level f to full size: bilinear over finite neighbours,
  * values times 2^f; NaN where no finite neighbour has weight. */

@@ -23,6 +23,7 @@ from .oracle import (  # noqa: F401
     upsample,
     match,
     match_stages,
+    warm_map,
     FLAG_FLAT,
     FLAG_DIVERGED,
     FLAG_SADDLE,

@@ -518,6 +518,12 @@ void orc_upsample(const double *M, int mw, int mh, int f, int w, int h, double *
 int orc_match(const double *left, const double *right, int w, int h, const orc_params *p,
               double *out)
 {
+    return orc_match_warm(left, right, w, h, p, NULL, out);
+}
+
+int orc_match_warm(const double *left, const double *right, int w, int h, const orc_params *p,
+                   const double *prev, double *out)
+{
     const int ps = p->patch_size;
     const int top = p->coarsest_scale, fin = p->finest_scale;
     if (ps < 2 || ps > 32 || top < fin || fin < 0 || top > 15 || p->iterations < 0 ||
@@ -546,6 +552,12 @@ int orc_match(const double *left, const double *right, int w, int h, const orc_p
 
     double *coarse = NULL;
     int cw = 0, ch = 0;
+    if (prev) {
+        cw = orc_level_dim(w, top + 1);
+        ch = orc_level_dim(h, top + 1);
+        coarse = (double *)malloc(sizeof(double) * cw * ch);
+        orc_warm_map(prev, w, h, top + 1, coarse);
+    }
     for (int l = top; l >= fin; --l) {
         int W = lw[l], H = lh[l];
         int stride = orc_grid_stride(ps, p->overlap);
@@ -581,6 +593,38 @@ int orc_match(const double *left, const double *right, int w, int h, const orc_p
     free(lh);
     return 0;
 }
+
+/* R15 warm start: the map that seeds the coarsest searched level L from a
+ * previous disparity P of the same scene (full size, NaN = not estimated).
+ * With s = 2^(L+1), output pixel (X, Y) of level L+1 is the mean of the
+ * finite values of P over the s x s block centred on full-size pixel
+ * (sX, sY) (rows and columns sX - s/2 .. sX + s/2 - 1, clipped to the
+ * image), divided by s; 0 where the block has no finite value. */
+void orc_warm_map(const double *P, int w, int h, int level, double *out)
+{
+    const int s = 1 << level;
+    const int mw = orc_level_dim(w, level), mh = orc_level_dim(h, level);
+    for (int Y = 0; Y < mh; ++Y)
+        for (int X = 0; X < mw; ++X) {
+            double sum = 0.0;
+            int n = 0;
+            for (int y = Y * s - s / 2; y < Y * s + s / 2 + (s == 1); ++y)
+                for (int x = X * s - s / 2; x < X * s + s / 2 + (s == 1); ++x) {
+                    if (x < 0 || y < 0 || x >= w || y >= h) continue;
+                    double v = P[(size_t)y * w + x];
+                    if (!isfinite(v)) continue;
+                    sum += v;
+                    n++;
+                }
+            out[(size_t)Y * mw + X] = n ? sum / n / s : 0.0;
+        }
+}
+
+/* The method with a warm start (R15): identical to orc_match except that the
+ * coarsest searched level starts from orc_warm_map(prev) instead of 0 (its
+ * patches' initial values and its carried pixels). prev NULL = orc_match. */
+int orc_match_warm(const double *left, const double *right, int w, int h, const orc_params *p,
+                   const double *prev, double *out);
 
 /* uint8 entry: converts to gray levels as doubles (step 1 of the oracle). */
 int orc_match_u8(const uint8_t *left, const uint8_t *right, int w, int h, const orc_params *p,

@@ -101,6 +101,8 @@ def load():
         lib.orc_upsample.argtypes = [dp, i, i, i, i, i, dp]
         lib.orc_match.argtypes = [dp, dp, i, i, pp, dp]
         lib.orc_match_u8.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i, i, pp, dp]
+        lib.orc_match_warm.argtypes = [dp, dp, i, i, pp, dp, dp]
+        lib.orc_warm_map.argtypes = [dp, i, i, i, dp]
         _lib = lib
     return _lib
 
@@ -241,10 +243,27 @@ def upsample(M, f, shape):
     return out
 
 
-def match(left, right, params: OracleParams) -> np.ndarray:
-    """Full method on one pair (uint8 or float images). Returns (H, W) float64, NaN = not estimated."""
+def warm_map(prev, level):
+    """R15: the level-`level` seed map made from a previous full-size disparity."""
+    prev = _f64(prev)
+    h, w = prev.shape
+    out = np.empty((level_dim(h, level), level_dim(w, level)))
+    load().orc_warm_map(_dp(prev), w, h, int(level), _dp(out))
+    return out
+
+
+def match(left, right, params: OracleParams, prev=None) -> np.ndarray:
+    """Full method on one pair (uint8 or float images). Returns (H, W) float64, NaN = not
+    estimated. `prev`: a previous disparity of the same scene to warm-start from (R15)."""
     h, w = left.shape
     out = np.empty((h, w))
+    if prev is not None:
+        lf, rf, pf = _f64(left), _f64(right), _f64(prev)
+        rc_ = load().orc_match_warm(_dp(lf), _dp(rf), w, h, ctypes.byref(params), _dp(pf),
+                                    _dp(out))
+        if rc_ != 0:
+            raise ValueError(f"oracle rejected the arguments (code {rc_})")
+        return out
     if left.dtype == np.uint8 and right.dtype == np.uint8:
         lc = np.ascontiguousarray(left)
         rc = np.ascontiguousarray(right)

@@ -23,5 +23,6 @@ from .api import (  # noqa: F401
     pyramid_level,
     search_level,
     upsample,
+    warm_map,
 )
 from ._lib import BdisError, BdisParams, library_path, load  # noqa: F401

@@ -21,14 +21,15 @@ EXPORTED = [
     "bdis_upsample", "bdis_enable_timing", "bdis_read_timing", "bdis_pack_right",
     "bdis_match_static", "bdis_probe_fp32_tflops", "bdis_set_search_variant",
     "bdis_get_search_variant", "bdis_plan_create", "bdis_plan_run", "bdis_plan_info",
-    "bdis_plan_workspace_bytes", "bdis_plan_destroy",
+    "bdis_plan_workspace_bytes", "bdis_plan_destroy", "bdis_match_warm", "bdis_warm_map",
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
 
 STATIC_SCRATCH_BYTES = 24 << 20  # BDIS_STATIC_SCRATCH_BYTES
 
-TIMING_CLASSES = ["prepare_level0", "pyramid_level", "search", "densify", "upsample"]
+TIMING_CLASSES = ["prepare_level0", "pyramid_level", "search", "densify", "upsample",
+                  "warm_map"]
 
 
 class BdisParams(ctypes.Structure):
@@ -119,6 +120,8 @@ def load():
     lib.bdis_prepare_level0.argtypes = [ip, ip, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.bdis_pyramid_level.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
                                        c_void_p, c_void_p, c_void_p]
+    lib.bdis_match_warm.argtypes = [c_void_p, ip, ip, pp, c_void_p, c_void_p]
+    lib.bdis_warm_map.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]
     lib.bdis_plan_create.argtypes = [c_int, P(BdisGroup), c_int, pp, c_int, c_void_p,
                                      P(c_void_p)]
     lib.bdis_plan_run.argtypes = [c_void_p, c_void_p]

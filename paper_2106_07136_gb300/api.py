@@ -134,6 +134,30 @@ class Matcher:
                                    ctypes.byref(params), out.data_ptr()), "bdis_match")
         return out[0] if squeeze else out
 
+    def match_warm(self, left: torch.Tensor, right: torch.Tensor, prev: torch.Tensor,
+                   params: BdisParams = None, out: torch.Tensor = None) -> torch.Tensor:
+        """bdis_match with the coarsest level seeded from `prev` (same shape as the
+        output; may be `out` itself). prev None = match."""
+        params = params if params is not None else default_params()
+        squeeze = left.dim() == 2
+        lb, rb = _as_batch(left), _as_batch(right)
+        b, h, w = lb.shape
+        if out is None:
+            out = torch.empty((b, h, w), dtype=torch.float32, device=left.device)
+        if not (out.is_contiguous() and out.dtype == torch.float32 and out.numel() == b * h * w):
+            raise ValueError("out must be a dense float32 tensor of B*H*W elements")
+        pp = None
+        if prev is not None:
+            if not (prev.is_contiguous() and prev.dtype == torch.float32
+                    and prev.numel() == b * h * w):
+                raise ValueError("prev must be a dense float32 tensor of B*H*W elements")
+            pp = prev.data_ptr()
+        li, ri = image_desc(lb), image_desc(rb)
+        check(self._lib.bdis_match_warm(self._h, ctypes.byref(li), ctypes.byref(ri),
+                                        ctypes.byref(params), pp, out.data_ptr()),
+              "bdis_match_warm")
+        return out.view(b, h, w)[0] if squeeze else out
+
     def match_host(self, left, right, params: BdisParams = None, out=None):
         """Host buffers in and out (numpy arrays or CPU tensors, pinned for DMA).
 
@@ -357,6 +381,17 @@ def densify_level(shape, params: BdisParams, d_star, weight, coarse, is_finest, 
                                          None if Rp is None else Rp.data_ptr(),
                                          out.data_ptr(), _stream_ptr(stream)),
           "bdis_densify_level")
+    return out
+
+
+def warm_map(prev: torch.Tensor, level: int, stream=None) -> torch.Tensor:
+    """Warm-start seed map of `level` from a (B, H, W) previous disparity."""
+    prev = _as_batch(prev).contiguous()
+    b, h, w = prev.shape
+    out = torch.empty((b, (h + (1 << level) - 1) >> level, (w + (1 << level) - 1) >> level),
+                      dtype=torch.float32, device=prev.device)
+    check(_lib.load().bdis_warm_map(prev.data_ptr(), w, h, level, b, out.data_ptr(),
+                                    _stream_ptr(stream)), "bdis_warm_map")
     return out
 
 

@@ -69,6 +69,9 @@ Layout plan_layout(int w, int h, int count, const bdis_params &p, bool host_stag
   }
   lay.d_star = take(max_np * count * sizeof(float));
   lay.weight = take(max_np * count * sizeof(float));
+  lay.warm_w = level_dim(w, p.coarsest_scale + 1);
+  lay.warm_h = level_dim(h, p.coarsest_scale + 1);
+  lay.warm = take((size_t)lay.warm_w * lay.warm_h * count * sizeof(float));
   if (host_staging) {
     lay.in_left = take((size_t)w * h * count);
     lay.in_right = take((size_t)w * h * count);
@@ -186,7 +189,7 @@ struct Timed {
 // Arguments of the search and densify launches of level l (the coarser map
 // of level l+1 seeds the patches; level 0 densifies into `out`).
 SearchArgs level_search_args(char *base, const Layout &lay, const bdis_params &p, int count,
-                             int l) {
+                             int l, bool warm = false) {
   auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
   SearchArgs sa{};
   fill_search_args(sa, lay.lw[l], lay.lh[l], count, p);
@@ -198,6 +201,11 @@ SearchArgs level_search_args(char *base, const Layout &lay, const bdis_params &p
     sa.cw = lay.lw[l + 1];
     sa.ch = lay.lh[l + 1];
     sa.cplane = (long long)sa.cw * sa.ch;
+  } else if (warm) {
+    sa.coarse = F(lay.warm);
+    sa.cw = lay.warm_w;
+    sa.ch = lay.warm_h;
+    sa.cplane = (long long)sa.cw * sa.ch;
   }
   sa.d_star = F(lay.d_star);
   sa.weight = F(lay.weight);
@@ -205,7 +213,7 @@ SearchArgs level_search_args(char *base, const Layout &lay, const bdis_params &p
 }
 
 DensifyArgs level_densify_args(char *base, const Layout &lay, const bdis_params &p, int count,
-                               int l, float *out) {
+                               int l, float *out, bool warm = false) {
   auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
   DensifyArgs da{};
   fill_densify_args(da, lay.lw[l], lay.lh[l], count, p);
@@ -215,6 +223,11 @@ DensifyArgs level_densify_args(char *base, const Layout &lay, const bdis_params 
     da.coarse = F(lay.D[l + 1]);
     da.cw = lay.lw[l + 1];
     da.ch = lay.lh[l + 1];
+    da.cplane = (long long)da.cw * da.ch;
+  } else if (warm) {
+    da.coarse = F(lay.warm);
+    da.cw = lay.warm_w;
+    da.ch = lay.warm_h;
     da.cplane = (long long)da.cw * da.ch;
   }
   da.is_finest = (l == p.finest_scale);
@@ -227,13 +240,20 @@ DensifyArgs level_densify_args(char *base, const Layout &lay, const bdis_params 
 // The whole method on device images already checked; `out` dense device.
 bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &right,
                       const bdis_params &p, float *out, const Layout &lay,
-                      const Tuning *tune = nullptr) {
+                      const Tuning *tune = nullptr, const float *prev = nullptr) {
   char *base = static_cast<char *>(h->ws);
   auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
   auto F2 = [&](size_t off) { return reinterpret_cast<float2 *>(base + off); };
   const int count = left.count;
   cudaStream_t st = h->stream;
   cudaError_t e;
+  if (prev) {
+    // first, before the output (which may alias prev) is written
+    Timed tm(h, 5);
+    e = launch_warm_map(prev, left.width, left.height, p.coarsest_scale + 1, count,
+                        F(lay.warm), st);
+    if (e != cudaSuccess) return record_cuda(e);
+  }
   {
     Timed tm(h, 0);
     e = launch_prepare_level0(left, right, F(lay.L[0]), F2(lay.R[0]), F(lay.G[0]), st);
@@ -248,14 +268,14 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
     if (e != cudaSuccess) return record_cuda(e);
   }
   for (int l = p.coarsest_scale; l >= p.finest_scale; --l) {
-    SearchArgs sa = level_search_args(base, lay, p, count, l);
+    SearchArgs sa = level_search_args(base, lay, p, count, l, prev != nullptr);
     if (tune) apply_tuning(sa, tune->level[l]);
     {
       Timed tm(h, 2);
       e = launch_search(sa, st);
     }
     if (e != cudaSuccess) return record_cuda(e);
-    DensifyArgs da = level_densify_args(base, lay, p, count, l, out);
+    DensifyArgs da = level_densify_args(base, lay, p, count, l, out, prev != nullptr);
     if (tune) apply_tuning(da, tune->level[l]);
     {
       Timed tm(h, 3);
@@ -310,7 +330,7 @@ bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right
 
 bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
                          const bdis_image &left, const bdis_image &right, const bdis_params &p,
-                         float *out, const Tuning *tune) {
+                         float *out, const Tuning *tune, const float *prev) {
   bdis_handle view;  // borrows the caller's scratch; owns nothing, times nothing
   view.stream = stream;
   view.ws = scratch;
@@ -318,7 +338,7 @@ bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t strea
   const Layout lay = plan_layout(left.width, left.height, left.count, p, false);
   if (lay.bytes > scratch_bytes) return BDIS_E_UNSUPPORTED;
   (void)0;
-  bdis_status s = run_match(&view, left, right, p, out, lay, tune);
+  bdis_status s = run_match(&view, left, right, p, out, lay, tune, prev);
   view.ws = nullptr;
   return s;
 }
@@ -581,6 +601,34 @@ bdis_status bdis_match(bdis_handle *h, const bdis_image *left, const bdis_image 
   s = ensure_workspace(h, lay.bytes);
   if (s != BDIS_OK) return s;
   return run_match(h, *left, *right, *p, disparity_out, lay);
+}
+
+bdis_status bdis_match_warm(bdis_handle *h, const bdis_image *left, const bdis_image *right,
+                            const bdis_params *p, const float *prev, float *disparity_out) {
+  if (!h || !disparity_out) return BDIS_E_INVALID_ARG;
+  bdis_status s = check_pair(left, right);
+  if (s != BDIS_OK) return s;
+  s = check_params(p);
+  if (s != BDIS_OK) return s;
+  s = check_geometry(left->width, left->height, *p);
+  if (s != BDIS_OK) return s;
+  s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  if (check_device_ptr(left->data) != BDIS_OK || check_device_ptr(right->data) != BDIS_OK ||
+      check_device_ptr(disparity_out) != BDIS_OK || (prev && check_device_ptr(prev) != BDIS_OK))
+    return BDIS_E_INVALID_ARG;
+  const Layout lay = plan_layout(left->width, left->height, left->count, *p, false);
+  s = ensure_workspace(h, lay.bytes);
+  if (s != BDIS_OK) return s;
+  return run_match(h, *left, *right, *p, disparity_out, lay, nullptr, prev);
+}
+
+bdis_status bdis_warm_map(const float *prev, int width, int height, int level, int count,
+                          float *out, void *stream) {
+  if (!prev || !out || width < 1 || height < 1 || level < 1 || level > 16 || count < 1)
+    return BDIS_E_INVALID_ARG;
+  return record_cuda(launch_warm_map(prev, width, height, level, count, out,
+                                     static_cast<cudaStream_t>(stream)));
 }
 
 bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right, int width,

@@ -81,6 +81,8 @@ struct Layout {
   int lw[16] = {0}, lh[16] = {0};
   size_t L[16] = {0}, R[16] = {0}, G[16] = {0}, D[16] = {0};
   size_t d_star = 0, weight = 0;
+  size_t warm = 0;  // seed map of the coarsest level from a previous disparity
+  int warm_w = 0, warm_h = 0;
   size_t in_left = 0, in_right = 0, out = 0;  // host-path staging
   size_t bytes = 0;
 };
@@ -136,6 +138,8 @@ cudaError_t launch_pack_right(const float *R, int w, int h, int count, float2 *R
                               cudaStream_t st);
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st);
+cudaError_t launch_warm_map(const float *prev, int w, int h, int level, int count, float *out,
+                            cudaStream_t st);
 cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, int h, int count,
                             float *out, cudaStream_t st);
 
@@ -160,7 +164,8 @@ bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right
                                  const float *disparity_out);
 bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
                          const bdis_image &left, const bdis_image &right, const bdis_params &p,
-                         float *out, const Tuning *tune = nullptr);
+                         float *out, const Tuning *tune = nullptr,
+                         const float *prev = nullptr);
 // Fill `tune` for every searched level by timing the candidate launches on
 // the given data (after one full run that fills the level planes).
 bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t stream,

@@ -205,7 +205,47 @@ __global__ void upsample_kernel(const float *__restrict__ M, int mw, int mh, flo
   out[idx] = sw > 0.f ? scale * s / sw : __int_as_float(0x7fc00000);
 }
 
+// R15 warm start: level-`level` seed map from a previous full-size disparity:
+// mean of its finite values over the 2^level block centred on the sample
+// point, divided by 2^level; 0 where none is finite.
+__global__ void warm_map_kernel(const float *__restrict__ P, int w, int h, int level, int mw,
+                                int mh, long long total, float *__restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const long long mplane = (long long)mw * mh;
+  const int b = (int)(idx / mplane);
+  const int rem = (int)(idx - (long long)b * mplane);
+  const int Y = rem / mw, X = rem - (rem / mw) * mw;
+  const int s = 1 << level;
+  const int half = s / 2;
+  const int x0 = max(X * s - half, 0), x1 = min(X * s + half + (s == 1 ? 1 : 0), w);
+  const int y0 = max(Y * s - half, 0), y1 = min(Y * s + half + (s == 1 ? 1 : 0), h);
+  const float *Pb = P + (long long)b * w * h;
+  float sum = 0.f;
+  int n = 0;
+  for (int y = y0; y < y1; ++y)
+    for (int x = x0; x < x1; ++x) {
+      const float v = __ldg(Pb + (size_t)y * w + x);
+      if (isfinite(v)) {
+        sum += v;
+        ++n;
+      }
+    }
+  out[idx] = n ? sum / (float)n / (float)s : 0.f;
+}
+
 }  // namespace
+
+cudaError_t launch_warm_map(const float *prev, int w, int h, int level, int count, float *out,
+                            cudaStream_t st) {
+  const int mw = level_dim(w, level), mh = level_dim(h, level);
+  const long long total = (long long)mw * mh * count;
+  if (total == 0) return cudaSuccess;
+  const int threads = 128;
+  warm_map_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
+      prev, w, h, level, mw, mh, total, out);
+  return cudaGetLastError();
+}
 
 void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_params &p) {
   a.w = w;

@@ -14,5 +14,6 @@ from .stereo import (  # noqa: F401
     make_integer_shift_pair,
     make_flat_pair,
     SEED_BASE,
+    VideoStream,
 )
 from .evaluate import error_stats  # noqa: F401

@@ -227,3 +227,53 @@ def make_flat_pair(h, w, value=100) -> StereoPair:
     """Constant images: no texture, every disparity explains the pair equally."""
     left = np.full((h, w), value, dtype=np.uint8)
     return StereoPair(left, left.copy(), np.full((h, w), np.nan), "flat")
+
+
+class VideoStream:
+    """Seeded synthetic stereo video (a stream of the serving workload).
+
+    One textured scene (as in make_cfg2: textureless rectangles, dark
+    regions, right-view highlights) wider than the frame; each frame pans the
+    view by up to 2 px and moves each disparity bump centre by 1-3 px in its
+    own direction, so consecutive disparity fields drift smoothly.
+    """
+
+    def __init__(self, seed, h, w, dmax=None, margin=64):
+        self.rng = np.random.Generator(np.random.PCG64(seed))
+        self.h, self.w, self.margin = h, w, margin
+        self.dmax = dmax if dmax is not None else w / 10.0
+        base = make_cfg2(seed=seed, h=h, w=w + margin, dmax=self.dmax)
+        self.scene = base.left.astype(np.float64)
+        rng = self.rng
+        self.bumps = [dict(cx=rng.uniform(0, w), cy=rng.uniform(0, h),
+                           a=rng.uniform(-0.2, 0.2) * self.dmax,
+                           s=rng.uniform(0.05, 0.12) * w,
+                           dx=rng.uniform(-1, 1), dy=rng.uniform(-1, 1))
+                      for _ in range(6)]
+        self.p0 = rng.uniform(0.10, 0.30) * self.dmax
+        self.p1 = rng.uniform(0.45, 0.65) * self.dmax
+        self.offset = margin // 2
+        self.frame_index = 0
+
+    def _field(self):
+        yy, xx = np.mgrid[0:self.h, 0:self.w].astype(np.float64)
+        d = self.p0 + (self.p1 - self.p0) * xx / max(self.w - 1, 1)
+        for b in self.bumps:
+            d += b["a"] * np.exp(-((xx - b["cx"]) ** 2 + (yy - b["cy"]) ** 2) / (2 * b["s"] ** 2))
+        return np.clip(d, 0.0, self.dmax)
+
+    def next(self) -> StereoPair:
+        rng = self.rng
+        if self.frame_index > 0:
+            self.offset = int(np.clip(self.offset + rng.integers(-2, 3), 0, self.margin))
+            for b in self.bumps:
+                step = rng.uniform(1.0, 3.0)
+                norm = max(np.hypot(b["dx"], b["dy"]), 1e-9)
+                b["cx"] += step * b["dx"] / norm
+                b["cy"] += step * b["dy"] / norm
+        scene = self.scene[:, self.offset:self.offset + self.w]
+        d = self._field()
+        right = _warp_right(scene, d) + rng.normal(0.0, 2.0, size=(self.h, self.w))
+        self.frame_index += 1
+        return StereoPair(_to_u8(scene), _to_u8(right), _left_ground_truth(d),
+                          f"video/{self.frame_index}")

@@ -502,3 +502,52 @@ def test_bdis_beats_dis_on_surgical_like_pair(orc):
     assert b["mean_abs"] < dis["mean_abs"]
     assert b["median_abs"] < dis["median_abs"]
     assert dis["valid"] >= b["valid"]  # DIS estimates more pixels (Table 1's valid counts)
+
+
+# ------------------------------------------------------- warm start (serving)
+
+def test_warm_map_closed_forms(orc):
+    """R15: block means of the finite previous disparities, divided by 2^level."""
+    h, w = 50, 70
+    yy, xx = np.mgrid[0:h, 0:w].astype(float)
+    c = np.full((h, w), 6.4)
+    m = orc.warm_map(c, 2)
+    np.testing.assert_allclose(m, 6.4 / 4, rtol=1e-14)
+    # a ramp in x: centred block means of x are the block centres (s X - 1/2)
+    # away from the border, so the map is (4 X - 0.5) / 4 there
+    m = orc.warm_map(xx, 2)
+    X = np.arange(m.shape[1], dtype=float)
+    expect = np.broadcast_to(((4 * X - 0.5) / 4)[1:-2], m[1:-1, 1:-2].shape)
+    np.testing.assert_allclose(m[1:-1, 1:-2], expect, rtol=1e-12)
+    nanblock = c.copy()
+    nanblock[:, :] = np.nan
+    assert np.all(orc.warm_map(nanblock, 3) == 0.0)  # nothing finite: cold start
+
+
+def test_warm_start_from_truth_keeps_the_result(orc):
+    """Seeding the coarsest level with the true previous disparity of an exact
+    shift gives the same exact answer as the cold start."""
+    k = 3
+    pair = synth.make_integer_shift_pair(48, 64, k)
+    p = small_params(orc)
+    prev = np.full(pair.shape, float(k))
+    out = orc.match(pair.left, pair.right, p, prev=prev)
+    est = np.isfinite(out) & np.isfinite(pair.disp)
+    assert est.sum() > 0.95 * np.isfinite(pair.disp).sum()
+    assert np.max(np.abs(out[est] - k)) < 1e-3
+
+
+def test_warm_start_reaches_beyond_the_cold_basin(orc):
+    """A shift too large for the coarse-to-fine start from 0 (20 px with two
+    scales: 5 px at the coarsest level, beyond its 8 px patches' reach after
+    the divergence rule) is recovered when the previous frame seeds it."""
+    k = 20
+    pair = synth.make_integer_shift_pair(48, 96, k)
+    p = small_params(orc, coarsest_scale=1, gamma=0.25)
+    warm = orc.match(pair.left, pair.right, p, prev=np.full(pair.shape, k - 0.7))
+    est = np.isfinite(warm) & np.isfinite(pair.disp)
+    assert est.sum() > 0.9 * np.isfinite(pair.disp).sum()
+    assert np.median(np.abs(warm[est] - k)) < 1e-3
+    cold = orc.match(pair.left, pair.right, p)
+    good_cold = np.isfinite(cold) & (np.abs(cold - k) < 1e-3)
+    assert good_cold.sum() < 0.5 * est.sum()
