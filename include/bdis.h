@@ -318,6 +318,44 @@ bdis_status bdis_plan_info(const bdis_plan *plan, int group, int level, bdis_pla
 size_t bdis_plan_workspace_bytes(const bdis_plan *plan);
 void bdis_plan_destroy(bdis_plan *plan);
 
+/* ------------------------------------------------- learned coarse proposal
+ * Not in the paper (its coarsest level starts from 0, Sec. 2.1): a small
+ * network proposes the coarsest disparity and BDIS refines it. Six 3x3
+ * convolutions with dilations 1, 2, 4, 4, 2, 1; 2 -> 32 -> 32 -> 32 -> 32 ->
+ * 32 -> 1 channels, ReLU between layers; input [(L - 128) / 64, (R - 128) /
+ * 64] of a pyramid level, output that level's disparity in its pixels. BF16
+ * weights and activations, FP32 accumulation, on the tensor cores.
+ * Master weights are FP32 in this order, layer by layer: W[co][ky*3+kx][ci]
+ * (bdis_net_weight_count() floats in all), then b[co]. */
+typedef struct bdis_net bdis_net;
+
+int bdis_net_weight_count(void);
+
+/* weights: host, bdis_net_weight_count() floats (copied). */
+bdis_status bdis_net_create(int device, const float *weights, bdis_net **out);
+
+/* Proposal for count x h x w level planes: L (float), R (float with element
+ * stride r_stride: 1 plain, 2 packed) -> disparity (float, level pixels).
+ * All device. Activations are held by the network object (grown on demand). */
+bdis_status bdis_net_forward(bdis_net *net, const float *L, const float *R, int r_stride,
+                             int width, int height, int count, float *disparity, void *stream);
+
+/* Loss (Huber, delta 1, mean over all count*h*w pixels; NaN labels count 0)
+ * and its gradient with respect to the master weights, without updating.
+ * loss_out / grad_out: host pointers or NULL (then nothing is copied). */
+bdis_status bdis_net_gradient(bdis_net *net, const float *L, const float *R, int r_stride,
+                              int width, int height, int count, const float *label,
+                              float *loss_out, float *grad_out, void *stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that gradient. */
+bdis_status bdis_net_train_step(bdis_net *net, const float *L, const float *R, int r_stride,
+                                int width, int height, int count, const float *label, float lr,
+                                float *loss_out, void *stream);
+
+/* Copy the FP32 master weights to host memory (waits for the device). */
+bdis_status bdis_net_get_weights(bdis_net *net, float *weights_out);
+void bdis_net_destroy(bdis_net *net);
+
 /* ----------------------------------------------------------- no allocation
  * Some callers cannot allocate GPU memory: a hard real-time loop that froze
  * its memory map after start-up, a plug-in that runs inside a host process

@@ -8,6 +8,9 @@ every call raises.
 from .api import (  # noqa: F401
     Matcher,
     Plan,
+    ProposalNet,
+    net_init_weights,
+    net_weight_count,
     default_params,
     densify_level,
     grid,

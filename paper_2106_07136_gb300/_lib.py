@@ -22,6 +22,8 @@ EXPORTED = [
     "bdis_match_static", "bdis_probe_fp32_tflops", "bdis_set_search_variant",
     "bdis_get_search_variant", "bdis_plan_create", "bdis_plan_run", "bdis_plan_info",
     "bdis_plan_workspace_bytes", "bdis_plan_destroy", "bdis_match_warm", "bdis_warm_map",
+    "bdis_net_weight_count", "bdis_net_create", "bdis_net_forward", "bdis_net_gradient",
+    "bdis_net_train_step", "bdis_net_get_weights", "bdis_net_destroy",
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
@@ -120,6 +122,19 @@ def load():
     lib.bdis_prepare_level0.argtypes = [ip, ip, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.bdis_pyramid_level.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
                                        c_void_p, c_void_p, c_void_p]
+    fp = P(c_float)
+    lib.bdis_net_weight_count.restype = c_int
+    lib.bdis_net_create.argtypes = [c_int, c_void_p, P(c_void_p)]
+    lib.bdis_net_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                     c_void_p, c_void_p]
+    lib.bdis_net_gradient.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                      c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.bdis_net_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
+                                        c_void_p, c_float, c_void_p, c_void_p]
+    lib.bdis_net_get_weights.argtypes = [c_void_p, c_void_p]
+    lib.bdis_net_destroy.argtypes = [c_void_p]
+    lib.bdis_net_destroy.restype = None
+    del fp
     lib.bdis_match_warm.argtypes = [c_void_p, ip, ip, pp, c_void_p, c_void_p]
     lib.bdis_warm_map.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]
     lib.bdis_plan_create.argtypes = [c_int, P(BdisGroup), c_int, pp, c_int, c_void_p,

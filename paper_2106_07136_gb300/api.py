@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import ctypes
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -270,6 +271,93 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             self._lib.bdis_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+NET_DILATIONS = (1, 2, 4, 4, 2, 1)
+NET_CHANNELS = ((2, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1))
+
+
+def net_weight_count() -> int:
+    return int(_lib.load().bdis_net_weight_count())
+
+
+def net_init_weights(seed: int = 0) -> np.ndarray:
+    """He-initialised master weights (host float32), layer by layer W[co][tap][ci], b[co]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    for (ci, co) in NET_CHANNELS:
+        std = np.sqrt(2.0 / (9 * ci))
+        parts.append(rng.normal(0.0, std, size=co * 9 * ci))
+        parts.append(np.zeros(co))
+    w = np.concatenate(parts).astype(np.float32)
+    assert w.size == net_weight_count()
+    return w
+
+
+class ProposalNet:
+    """The learned coarse proposal (bdis_net_*): forward, gradient, Adam steps."""
+
+    def __init__(self, weights=None, device=None):
+        self._lib = _lib.load()
+        w = net_init_weights() if weights is None else np.ascontiguousarray(weights, np.float32)
+        if w.size != net_weight_count():
+            raise ValueError("wrong number of weights")
+        dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+        h = ctypes.c_void_p()
+        check(self._lib.bdis_net_create(dev, w.ctypes.data, ctypes.byref(h)), "bdis_net_create")
+        self._h = h
+
+    @staticmethod
+    def _planes(L, R):
+        L = _as_batch(L).contiguous()
+        if R.dim() >= 3 and R.shape[-1] == 2 and R.dim() == L.dim() + 1:
+            return L, _packed(R), 2
+        return L, _as_batch(R).contiguous(), 1
+
+    def forward(self, L, R, stream=None) -> torch.Tensor:
+        L, Rp, rs = self._planes(L, R)
+        b, h, w = L.shape
+        out = torch.empty((b, h, w), dtype=torch.float32, device=L.device)
+        check(self._lib.bdis_net_forward(self._h, L.data_ptr(), Rp.data_ptr(), rs, w, h, b,
+                                         out.data_ptr(), _stream_ptr(stream)), "bdis_net_forward")
+        return out
+
+    def gradient(self, L, R, label, stream=None):
+        L, Rp, rs = self._planes(L, R)
+        b, h, w = L.shape
+        label = _as_batch(label).contiguous()
+        loss = ctypes.c_float()
+        grad = np.empty(net_weight_count(), dtype=np.float32)
+        check(self._lib.bdis_net_gradient(self._h, L.data_ptr(), Rp.data_ptr(), rs, w, h, b,
+                                          label.data_ptr(), ctypes.byref(loss), grad.ctypes.data,
+                                          _stream_ptr(stream)), "bdis_net_gradient")
+        return loss.value, grad
+
+    def train_step(self, L, R, label, lr, stream=None) -> float:
+        L, Rp, rs = self._planes(L, R)
+        b, h, w = L.shape
+        label = _as_batch(label).contiguous()
+        loss = ctypes.c_float()
+        check(self._lib.bdis_net_train_step(self._h, L.data_ptr(), Rp.data_ptr(), rs, w, h, b,
+                                            label.data_ptr(), float(lr), ctypes.byref(loss),
+                                            _stream_ptr(stream)), "bdis_net_train_step")
+        return loss.value
+
+    def weights(self) -> np.ndarray:
+        w = np.empty(net_weight_count(), dtype=np.float32)
+        check(self._lib.bdis_net_get_weights(self._h, w.ctypes.data), "bdis_net_get_weights")
+        return w
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.bdis_net_destroy(self._h)
             self._h = None
 
     def __del__(self):

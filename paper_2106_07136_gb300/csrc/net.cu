@@ -1,0 +1,630 @@
+// net.cu -- the learned coarse proposal: a 6-layer 3x3 convolutional network
+// on the level-3 pyramid pair, BF16 weights and activations, FP32
+// accumulation, forward and training kernels on the tensor cores.
+//
+// Not part of the paper: the paper's method starts its coarsest level from 0
+// (Sec. 2.1); this network proposes a start instead, and BDIS refines it.
+//
+// Architecture (all 3x3, zero padding, dilations 1, 2, 4, 4, 2, 1 so the
+// receptive field spans +-14 level-3 pixels):
+//   x0 = [(L - 128) / 64, (R - 128) / 64]           2 channels (padded to 16)
+//   a1..a5 = relu(conv(a_{i-1}) + b_i)              32 channels
+//   d = conv(a5) + b6                               1 channel (padded to 16), level-3 px
+// Activations are NHWC bf16 (channels innermost).
+//
+// Every convolution is an implicit GEMM on mma.sync.m16n8k16 (bf16 in, f32
+// accumulate): rows = pixels, columns = output channels, K = 9 taps x input
+// channels. The data-gradient of a layer is the same kernel run on the
+// output gradient with transposed, tap-flipped weights and the previous
+// layer's ReLU mask fused into the store; the weight-gradient is a GEMM with
+// rows = output channels, columns = (tap, input channel), K = pixels,
+// reduced across blocks with float atomics.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "bdis_internal.cuh"
+
+namespace {
+
+constexpr int kLayers = 6;
+constexpr int kDil[kLayers] = {1, 2, 4, 4, 2, 1};
+constexpr int kCin[kLayers] = {2, 32, 32, 32, 32, 32};    // real channels
+constexpr int kCout[kLayers] = {32, 32, 32, 32, 32, 1};
+constexpr int kCinP[kLayers] = {16, 32, 32, 32, 32, 32};  // padded (multiples of 16)
+constexpr int kCoutP[kLayers] = {32, 32, 32, 32, 32, 16};
+
+constexpr int master_w_offset(int l) {
+  int off = 0;
+  for (int i = 0; i < l; ++i) off += kCout[i] * 9 * kCin[i] + kCout[i];
+  return off;
+}
+constexpr int kMasterCount = master_w_offset(kLayers);
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+__device__ __forceinline__ uint32_t pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  __nv_bfloat162 v;
+  v.x = lo;
+  v.y = hi;
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// D (16x8 f32) += A (16x16 bf16, row) * B (16x8 bf16, col)
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// ------------------------------------------------------------ input pack
+
+// x0[p][0] = (L - 128)/64, x0[p][1] = (R - 128)/64, channels 2..15 zero.
+__global__ void pack_input_kernel(const float *__restrict__ L, const float *__restrict__ R,
+                                  int r_stride, long long total, __nv_bfloat16 *__restrict__ x0) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= total) return;
+  uint4 *dst = reinterpret_cast<uint4 *>(x0 + p * 16);
+  const float l = (__ldg(L + p) - 128.f) * (1.f / 64.f);
+  const float r = (__ldg(R + p * r_stride) - 128.f) * (1.f / 64.f);
+  uint4 v0 = make_uint4(pack_bf16(l, r), 0u, 0u, 0u);
+  dst[0] = v0;
+  dst[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// ------------------------------------------------------------ conv (mma)
+
+enum ConvMode { kFwdRelu = 0, kFwdLinearF32 = 1, kBwdDataMasked = 2 };
+
+// One warp computes 16 consecutive pixels x COUT channels; a block of 4 warps
+// 64 pixels. Weights (COUT x 9 x CIN bf16) live in shared memory.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(128) conv_mma_kernel(
+    const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wt,
+    const float *__restrict__ bias, int dil, int H, int W, long long total,
+    const __nv_bfloat16 *__restrict__ mask, void *__restrict__ out) {
+  static_assert(CIN % 16 == 0 && COUT % 8 == 0, "tile");
+  __shared__ __align__(16) __nv_bfloat16 ws[COUT * 9 * CIN];
+  for (int i = threadIdx.x * 8; i < COUT * 9 * CIN; i += blockDim.x * 8)
+    *reinterpret_cast<uint4 *>(ws + i) = *reinterpret_cast<const uint4 *>(wt + i);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long p0 = ((long long)blockIdx.x * 4 + warp) * 16;
+  const int g = lane >> 2, q = lane & 3;
+  // the two pixel rows this thread feeds: p0 + g and p0 + g + 8
+  long long pr[2] = {p0 + g, p0 + g + 8};
+  int pb[2], py[2], px[2];
+  bool pv[2];
+  const long long plane = (long long)H * W;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    pv[i] = pr[i] < total;
+    const long long pp = pv[i] ? pr[i] : 0;
+    pb[i] = (int)(pp / plane);
+    const int rem = (int)(pp - (long long)pb[i] * plane);
+    py[i] = rem / W;
+    px[i] = rem - py[i] * W;
+  }
+  float acc[COUT / 8][4];
+#pragma unroll
+  for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+#pragma unroll 1
+  for (int tap = 0; tap < 9; ++tap) {
+    const int dy = (tap / 3 - 1) * dil, dx = (tap % 3 - 1) * dil;
+    const __nv_bfloat16 *src[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int yy = py[i] + dy, xx = px[i] + dx;
+      const bool ok = pv[i] && yy >= 0 && yy < H && xx >= 0 && xx < W;
+      src[i] = ok ? in + (((long long)pb[i] * H + yy) * W + xx) * CIN : nullptr;
+    }
+#pragma unroll
+    for (int kb = 0; kb < CIN / 16; ++kb) {
+      const int c0 = kb * 16 + q * 2;
+      uint32_t a[4];
+      a[0] = src[0] ? *reinterpret_cast<const uint32_t *>(src[0] + c0) : 0u;
+      a[1] = src[1] ? *reinterpret_cast<const uint32_t *>(src[1] + c0) : 0u;
+      a[2] = src[0] ? *reinterpret_cast<const uint32_t *>(src[0] + c0 + 8) : 0u;
+      a[3] = src[1] ? *reinterpret_cast<const uint32_t *>(src[1] + c0 + 8) : 0u;
+#pragma unroll
+      for (int n = 0; n < COUT / 8; ++n) {
+        const __nv_bfloat16 *wr = ws + ((n * 8 + g) * 9 + tap) * CIN + c0;
+        uint32_t b[2];
+        b[0] = *reinterpret_cast<const uint32_t *>(wr);
+        b[1] = *reinterpret_cast<const uint32_t *>(wr + 8);
+        mma_bf16(acc[n], a, b);
+      }
+    }
+  }
+  // epilogue: acc[n][0..1] -> pixel row g, channels n*8 + 2q + {0,1}; [2..3] -> row g+8
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    if (!pv[i]) continue;
+    const long long p = pr[i];
+#pragma unroll
+    for (int n = 0; n < COUT / 8; ++n) {
+      const int c = n * 8 + q * 2;
+      float v0 = acc[n][2 * i], v1 = acc[n][2 * i + 1];
+      if (MODE == kFwdRelu) {
+        v0 = fmaxf(v0 + bias[c], 0.f);
+        v1 = fmaxf(v1 + bias[c + 1], 0.f);
+        *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(out) + p * COUT + c) =
+            pack_bf16(v0, v1);
+      } else if (MODE == kFwdLinearF32) {
+        float *o = reinterpret_cast<float *>(out) + p * COUT + c;
+        o[0] = v0 + bias[c];
+        o[1] = v1 + bias[c + 1];
+      } else {  // data gradient times the previous layer's ReLU derivative
+        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask + p * COUT + c);
+        v0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
+        v1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
+        *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(out) + p * COUT + c) =
+            pack_bf16(v0, v1);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- weight gradient
+
+// dW[co][tap][ci] += sum_p G[p][co] * X[p shifted by tap][ci]; db[co] += sum_p G[p][co].
+// A block takes a run of 64 pixels at a time (grid-stride) and keeps the
+// whole COUT x (9 CIN) gradient in registers over its runs, then adds it to
+// global memory once. Rows = co (A = G^T), columns = (tap, ci), K = pixels.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) conv_wgrad_kernel(
+    const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ G, int dil, int H,
+    int W, long long total, float *__restrict__ dW, float *__restrict__ db) {
+  constexpr int PIX = 64;
+  constexpr int NCOL = 9 * CIN;          // GEMM columns
+  constexpr int NT = NCOL / 8;           // n-tiles
+  constexpr int MT = COUT / 16;          // m-tiles (COUT multiple of 16)
+  constexpr int NT_W = (NT + 3) / 4;     // n-tiles per warp
+  static_assert(COUT % 16 == 0 && CIN % 16 == 0, "tile");
+  __shared__ __align__(16) __nv_bfloat16 gs[PIX][COUT];
+  __shared__ __align__(16) __nv_bfloat16 xs[9][PIX][CIN];
+  __shared__ float dbs[COUT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const long long plane = (long long)H * W;
+  for (int c = threadIdx.x; c < COUT; c += blockDim.x) dbs[c] = 0.f;
+  float acc[MT][NT_W][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < NT_W; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+  float dbl = 0.f;  // bias partial of channel threadIdx.x (when < COUT)
+  for (long long base = (long long)blockIdx.x * PIX; base < total;
+       base += (long long)gridDim.x * PIX) {
+    __syncthreads();
+    // stage G (PIX x COUT) and the nine shifted copies of X (PIX x CIN), zero padded
+    for (int i = threadIdx.x; i < PIX * COUT / 2; i += blockDim.x) {
+      const int pix = i / (COUT / 2), c2 = (i - pix * (COUT / 2)) * 2;
+      const long long p = base + pix;
+      uint32_t v = 0u;
+      if (p < total) v = *reinterpret_cast<const uint32_t *>(G + p * COUT + c2);
+      *reinterpret_cast<uint32_t *>(&gs[pix][c2]) = v;
+    }
+    for (int i = threadIdx.x; i < 9 * PIX * CIN / 2; i += blockDim.x) {
+      const int tap = i / (PIX * CIN / 2);
+      const int rem = i - tap * (PIX * CIN / 2);
+      const int pix = rem / (CIN / 2), c2 = (rem - pix * (CIN / 2)) * 2;
+      const long long p = base + pix;
+      uint32_t v = 0u;
+      if (p < total) {
+        const int b = (int)(p / plane);
+        const int r2 = (int)(p - (long long)b * plane);
+        const int y = r2 / W + (tap / 3 - 1) * dil, x = r2 % W + (tap % 3 - 1) * dil;
+        if (y >= 0 && y < H && x >= 0 && x < W)
+          v = *reinterpret_cast<const uint32_t *>(X + (((long long)b * H + y) * W + x) * CIN + c2);
+      }
+      *reinterpret_cast<uint32_t *>(&xs[tap][pix][c2]) = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < COUT) {
+      float s = 0.f;
+      for (int pix = 0; pix < PIX; ++pix) s += __bfloat162float(gs[pix][threadIdx.x]);
+      dbl += s;
+    }
+#pragma unroll
+    for (int k0 = 0; k0 < PIX; k0 += 16) {
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        // A[co][pix]: rows co = m*16 + g (+8), cols pix = k0 + 2q (+1) (+8)
+        const int co = m * 16 + g;
+        uint32_t a[4];
+        a[0] = pack_raw(gs[k0 + 2 * q][co], gs[k0 + 2 * q + 1][co]);
+        a[1] = pack_raw(gs[k0 + 2 * q][co + 8], gs[k0 + 2 * q + 1][co + 8]);
+        a[2] = pack_raw(gs[k0 + 2 * q + 8][co], gs[k0 + 2 * q + 9][co]);
+        a[3] = pack_raw(gs[k0 + 2 * q + 8][co + 8], gs[k0 + 2 * q + 9][co + 8]);
+#pragma unroll
+        for (int n = 0; n < NT_W; ++n) {
+          const int nt = warp * NT_W + n;
+          if (nt >= NT) break;
+          // B[pix][col]: col = nt*8 + g -> (tap, ci); rows pix = k0 + 2q (+1) (+8)
+          const int col = nt * 8 + g, tap = col / CIN, ci = col - tap * CIN;
+          uint32_t b[2];
+          b[0] = pack_raw(xs[tap][k0 + 2 * q][ci], xs[tap][k0 + 2 * q + 1][ci]);
+          b[1] = pack_raw(xs[tap][k0 + 2 * q + 8][ci], xs[tap][k0 + 2 * q + 9][ci]);
+          mma_bf16(acc[m][n], a, b);
+        }
+      }
+    }
+  }
+  // C[co][col]: acc[m][n][0..1] -> row m*16+g, cols nt*8 + 2q + {0,1}; [2..3] -> row +8
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < NT_W; ++n) {
+      const int nt = warp * NT_W + n;
+      if (nt >= NT) break;
+      const int col = nt * 8 + q * 2;
+      const int co = m * 16 + g;
+      // dW layout [co][tap][ci] == [co][col]
+      atomicAdd(dW + (long long)co * NCOL + col, acc[m][n][0]);
+      atomicAdd(dW + (long long)co * NCOL + col + 1, acc[m][n][1]);
+      atomicAdd(dW + (long long)(co + 8) * NCOL + col, acc[m][n][2]);
+      atomicAdd(dW + (long long)(co + 8) * NCOL + col + 1, acc[m][n][3]);
+    }
+  if (threadIdx.x < COUT) atomicAdd(db + threadIdx.x, dbl);
+}
+
+// ------------------------------------------------------ loss, weights, adam
+
+// Huber (delta 1) loss of channel 0 of z6 (p x 16 f32) against label
+// (NaN = no label), averaged over all pixels; its gradient into g6 (p x 16 bf16).
+__global__ void loss_kernel(const float *__restrict__ z6, const float *__restrict__ label,
+                            long long total, float inv_n, __nv_bfloat16 *__restrict__ g6,
+                            float *__restrict__ loss_sum) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f, gr = 0.f;
+  if (p < total) {
+    const float y = label[p];
+    if (isfinite(y)) {
+      const float e = z6[p * 16] - y;
+      const float ae = fabsf(e);
+      l = ae <= 1.f ? 0.5f * e * e : ae - 0.5f;
+      gr = (ae <= 1.f ? e : copysignf(1.f, e)) * inv_n;
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(g6 + p * 16);
+    dst[0] = make_uint4(pack_bf16(gr, 0.f), 0u, 0u, 0u);
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0 && loss_sum) atomicAdd(loss_sum, l * inv_n);
+}
+
+// Master weights (f32, real channels) -> padded bf16 forward weights
+// [coutP][9][cinP] and, for layers > 0, the transposed tap-flipped copies the
+// data gradient uses: [cinP][9][coutP] with wt_t[ci][t][co] = w[co][8-t][ci].
+__global__ void pack_weights_kernel(const float *__restrict__ master, __nv_bfloat16 *fwd,
+                                    __nv_bfloat16 *bwd, int layer_offset, int cin, int cout,
+                                    int cinP, int coutP) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = coutP * 9 * cinP;
+  if (i >= n) return;
+  const int co = i / (9 * cinP), rem = i - co * 9 * cinP, t = rem / cinP, ci = rem - t * cinP;
+  float v = 0.f;
+  if (co < cout && ci < cin) v = master[layer_offset + (co * 9 + t) * cin + ci];
+  fwd[i] = __float2bfloat16_rn(v);
+  if (bwd) bwd[(ci * 9 + (8 - t)) * coutP + co] = __float2bfloat16_rn(v);
+}
+
+__global__ void bias_pad_kernel(const float *__restrict__ master, float *bias, int off, int cout,
+                                int coutP) {
+  const int c = threadIdx.x;
+  if (c < coutP) bias[c] = c < cout ? master[off + c] : 0.f;
+}
+
+// Adam on the master weights; gradients are gathered from the padded
+// per-layer gradient buffers.
+__global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ grad, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gr = grad[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gr;
+  const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Padded per-layer gradients [coutP][9][cinP] + [coutP] -> master order.
+__global__ void gather_grad_kernel(const float *__restrict__ dWp, const float *__restrict__ dbp,
+                                   float *__restrict__ grad, int off, int cin, int cout,
+                                   int cinP) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nw = cout * 9 * cin;
+  if (i < nw) {
+    const int co = i / (9 * cin), rem = i - co * 9 * cin, t = rem / cin, ci = rem - t * cin;
+    grad[off + i] = dWp[(co * 9 + t) * cinP + ci];
+  } else if (i < nw + cout) {
+    grad[off + i] = dbp[i - nw];
+  }
+}
+
+// Level-3 net output (channel 0 of z6) -> plain map.
+__global__ void take_channel0_kernel(const float *__restrict__ z6, long long total, float *out) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < total) out[p] = z6[p * 16];
+}
+
+inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+struct bdis_net {
+  int device = 0;
+  // master weights and Adam state (f32, real channels, master order)
+  float *w = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+  // per-layer padded bf16 weights, transposed copies, padded biases, padded grads
+  __nv_bfloat16 *wf[kLayers] = {}, *wb[kLayers] = {};
+  float *bias[kLayers] = {}, *dW[kLayers] = {}, *db[kLayers] = {};
+  float *loss = nullptr;
+  long long step = 0;
+  // activations for `cap` pixels
+  long long cap = 0;
+  __nv_bfloat16 *x0 = nullptr, *a[5] = {}, *gbuf[2] = {}, *g6 = nullptr;
+  float *z6 = nullptr;
+};
+
+namespace {
+
+void net_free_acts(bdis_net *n) {
+  cudaFree(n->x0);
+  for (auto &p : n->a) cudaFree(p);
+  for (auto &p : n->gbuf) cudaFree(p);
+  cudaFree(n->g6);
+  cudaFree(n->z6);
+  n->x0 = nullptr;
+  for (auto &p : n->a) p = nullptr;
+  for (auto &p : n->gbuf) p = nullptr;
+  n->g6 = nullptr;
+  n->z6 = nullptr;
+  n->cap = 0;
+}
+
+bdis_status net_reserve(bdis_net *n, long long pixels) {
+  if (pixels <= n->cap) return BDIS_OK;
+  net_free_acts(n);
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  alloc((void **)&n->x0, pixels * 16 * 2);
+  for (auto &p : n->a) alloc((void **)&p, pixels * 32 * 2);
+  for (auto &p : n->gbuf) alloc((void **)&p, pixels * 32 * 2);
+  alloc((void **)&n->g6, pixels * 16 * 2);
+  alloc((void **)&n->z6, pixels * 16 * 4);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    net_free_acts(n);
+    return BDIS_E_NOMEM;
+  }
+  n->cap = pixels;
+  return BDIS_OK;
+}
+
+cudaError_t pack_all(bdis_net *n, cudaStream_t st) {
+  for (int l = 0; l < kLayers; ++l) {
+    const int cnt = kCoutP[l] * 9 * kCinP[l];
+    pack_weights_kernel<<<nblocks(cnt, 256), 256, 0, st>>>(n->w, n->wf[l], l > 0 ? n->wb[l] : nullptr,
+                                                           master_w_offset(l), kCin[l], kCout[l],
+                                                           kCinP[l], kCoutP[l]);
+    bias_pad_kernel<<<1, 32, 0, st>>>(n->w, n->bias[l],
+                                      master_w_offset(l) + kCout[l] * 9 * kCin[l], kCout[l],
+                                      kCoutP[l]);
+  }
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int MODE>
+void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, int dil, int H,
+          int W, long long total, const __nv_bfloat16 *mask, void *out, cudaStream_t st) {
+  conv_mma_kernel<CIN, COUT, MODE><<<nblocks(total, 64), 128, 0, st>>>(in, wt, bias, dil, H, W,
+                                                                      total, mask, out);
+}
+
+cudaError_t forward(bdis_net *n, const float *L3, const float *R3, int r_stride, int H, int W,
+                    long long total, cudaStream_t st) {
+  pack_input_kernel<<<nblocks(total, 256), 256, 0, st>>>(L3, R3, r_stride, total, n->x0);
+  conv<16, 32, kFwdRelu>(n->x0, n->wf[0], n->bias[0], kDil[0], H, W, total, nullptr, n->a[0], st);
+  for (int l = 1; l < 5; ++l)
+    conv<32, 32, kFwdRelu>(n->a[l - 1], n->wf[l], n->bias[l], kDil[l], H, W, total, nullptr,
+                           n->a[l], st);
+  conv<32, 16, kFwdLinearF32>(n->a[4], n->wf[5], n->bias[5], kDil[5], H, W, total, nullptr,
+                              n->z6, st);
+  return cudaGetLastError();
+}
+
+// Backward through all layers into the padded gradient buffers (zeroed here).
+cudaError_t backward(bdis_net *n, int H, int W, long long total, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < kLayers && e == cudaSuccess; ++l) {
+    e = cudaMemsetAsync(n->dW[l], 0, sizeof(float) * kCoutP[l] * 9 * kCinP[l], st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->db[l], 0, sizeof(float) * kCoutP[l], st);
+  }
+  if (e != cudaSuccess) return e;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, n->device);
+  const unsigned wblocks = (unsigned)std::min<long long>((total + 63) / 64, (long long)sms * 4);
+  // layer 6 (linear): gradient g6 of z6
+  conv_wgrad_kernel<32, 16><<<wblocks, 128, 0, st>>>(n->a[4], n->g6, kDil[5], H, W, total,
+                                                     n->dW[5], n->db[5]);
+  // g5 = (W6^T g6) * relu'(a5)
+  conv<16, 32, kBwdDataMasked>(n->g6, n->wb[5], nullptr, kDil[5], H, W, total, n->a[4],
+                               n->gbuf[0], st);
+  int cur = 0;
+  for (int l = 4; l >= 1; --l) {
+    // gradient of layer l (0-based) output is gbuf[cur]; its input is a[l-1]
+    conv_wgrad_kernel<32, 32><<<wblocks, 128, 0, st>>>(n->a[l - 1], n->gbuf[cur], kDil[l], H, W,
+                                                       total, n->dW[l], n->db[l]);
+    conv<32, 32, kBwdDataMasked>(n->gbuf[cur], n->wb[l], nullptr, kDil[l], H, W, total,
+                                 n->a[l - 1], n->gbuf[cur ^ 1], st);
+    cur ^= 1;
+  }
+  conv_wgrad_kernel<16, 32><<<wblocks, 128, 0, st>>>(n->x0, n->gbuf[cur], kDil[0], H, W, total,
+                                                     n->dW[0], n->db[0]);
+  for (int l = 0; l < kLayers; ++l) {
+    const int cnt = kCout[l] * 9 * kCin[l] + kCout[l];
+    gather_grad_kernel<<<nblocks(cnt, 256), 256, 0, st>>>(n->dW[l], n->db[l], n->grad,
+                                                          master_w_offset(l), kCin[l], kCout[l],
+                                                          kCinP[l]);
+  }
+  return cudaGetLastError();
+}
+
+void net_release(bdis_net *n) {
+  if (!n) return;
+  net_free_acts(n);
+  cudaFree(n->w);
+  cudaFree(n->m);
+  cudaFree(n->v);
+  cudaFree(n->grad);
+  cudaFree(n->loss);
+  for (int l = 0; l < kLayers; ++l) {
+    cudaFree(n->wf[l]);
+    cudaFree(n->wb[l]);
+    cudaFree(n->bias[l]);
+    cudaFree(n->dW[l]);
+    cudaFree(n->db[l]);
+  }
+  delete n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bdis_net_weight_count(void) { return kMasterCount; }
+
+bdis_status bdis_net_create(int device, const float *weights, bdis_net **out) {
+  if (!out || !weights) return BDIS_E_INVALID_ARG;
+  *out = nullptr;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return bdis::record_cuda(e);
+  bdis_net *n = new (std::nothrow) bdis_net();
+  if (!n) return BDIS_E_NOMEM;
+  n->device = device;
+  auto alloc = [&](void **p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+  };
+  const size_t wb = sizeof(float) * kMasterCount;
+  alloc((void **)&n->w, wb);
+  alloc((void **)&n->m, wb);
+  alloc((void **)&n->v, wb);
+  alloc((void **)&n->grad, wb);
+  alloc((void **)&n->loss, sizeof(float));
+  for (int l = 0; l < kLayers; ++l) {
+    alloc((void **)&n->wf[l], 2 * kCoutP[l] * 9 * kCinP[l]);
+    if (l > 0) alloc((void **)&n->wb[l], 2 * kCoutP[l] * 9 * kCinP[l]);
+    alloc((void **)&n->bias[l], sizeof(float) * kCoutP[l]);
+    alloc((void **)&n->dW[l], sizeof(float) * kCoutP[l] * 9 * kCinP[l]);
+    alloc((void **)&n->db[l], sizeof(float) * kCoutP[l]);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(n->w, weights, wb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(n->m, 0, wb);
+  if (e == cudaSuccess) e = cudaMemset(n->v, 0, wb);
+  if (e == cudaSuccess) e = pack_all(n, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    net_release(n);
+    return e == cudaErrorMemoryAllocation ? BDIS_E_NOMEM : bdis::record_cuda(e);
+  }
+  *out = n;
+  return BDIS_OK;
+}
+
+bdis_status bdis_net_forward(bdis_net *n, const float *L3, const float *R3, int r_stride,
+                             int width, int height, int count, float *disparity, void *stream) {
+  if (!n || !L3 || !R3 || !disparity || width < 1 || height < 1 || count < 1 ||
+      (r_stride != 1 && r_stride != 2))
+    return BDIS_E_INVALID_ARG;
+  const long long total = (long long)width * height * count;
+  bdis_status s = net_reserve(n, total);
+  if (s != BDIS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = forward(n, L3, R3, r_stride, height, width, total, st);
+  if (e == cudaSuccess) {
+    take_channel0_kernel<<<nblocks(total, 256), 256, 0, st>>>(n->z6, total, disparity);
+    e = cudaGetLastError();
+  }
+  return bdis::record_cuda(e);
+}
+
+bdis_status bdis_net_gradient(bdis_net *n, const float *L3, const float *R3, int r_stride,
+                              int width, int height, int count, const float *label,
+                              float *loss_out, float *grad_out, void *stream) {
+  if (!n || !L3 || !R3 || !label || width < 1 || height < 1 || count < 1 ||
+      (r_stride != 1 && r_stride != 2))
+    return BDIS_E_INVALID_ARG;
+  const long long total = (long long)width * height * count;
+  bdis_status s = net_reserve(n, total);
+  if (s != BDIS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = forward(n, L3, R3, r_stride, height, width, total, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->loss, 0, sizeof(float), st);
+  if (e == cudaSuccess) {
+    loss_kernel<<<nblocks(total, 256), 256, 0, st>>>(n->z6, label, total, 1.f / (float)total,
+                                                     n->g6, n->loss);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = backward(n, height, width, total, st);
+  if (e == cudaSuccess && loss_out)
+    e = cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && grad_out)
+    e = cudaMemcpyAsync(grad_out, n->grad, sizeof(float) * kMasterCount, cudaMemcpyDeviceToHost,
+                        st);
+  if (e == cudaSuccess && (loss_out || grad_out)) e = cudaStreamSynchronize(st);
+  return bdis::record_cuda(e);
+}
+
+bdis_status bdis_net_train_step(bdis_net *n, const float *L3, const float *R3, int r_stride,
+                                int width, int height, int count, const float *label, float lr,
+                                float *loss_out, void *stream) {
+  bdis_status s = bdis_net_gradient(n, L3, R3, r_stride, width, height, count, label, nullptr,
+                                    nullptr, stream);
+  if (s != BDIS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  n->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
+  adam_kernel<<<nblocks(kMasterCount, 256), 256, 0, st>>>(n->w, n->m, n->v, n->grad, kMasterCount,
+                                                          lr, b1, b2, 1e-8f, c1, c2);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = pack_all(n, st);
+  if (e == cudaSuccess && loss_out) {
+    e = cudaMemcpyAsync(loss_out, n->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  return bdis::record_cuda(e);
+}
+
+bdis_status bdis_net_get_weights(bdis_net *n, float *weights_out) {
+  if (!n || !weights_out) return BDIS_E_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(n->device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(weights_out, n->w, sizeof(float) * kMasterCount, cudaMemcpyDeviceToHost);
+  return bdis::record_cuda(e);
+}
+
+void bdis_net_destroy(bdis_net *n) {
+  if (!n) return;
+  cudaSetDevice(n->device);
+  cudaDeviceSynchronize();
+  net_release(n);
+}
+
+}  // extern "C"
