@@ -117,6 +117,7 @@ typedef struct {
 } bdis_patch_debug;
 
 typedef struct bdis_handle bdis_handle;
+typedef struct bdis_net bdis_net; /* the learned proposal network (see below) */
 
 /* Paper defaults (Sec. 3): patch 8, overlap 0.75, 12 iterations, scales 4..0,
  * sigma_r = sigma_s = 4, 5 samples 0.5 px apart, gamma 0.75, normalize 1,
@@ -194,6 +195,27 @@ bdis_status bdis_match(bdis_handle *h, const bdis_image *left, const bdis_image 
  * read before the output is written). prev NULL = bdis_match. */
 bdis_status bdis_match_warm(bdis_handle *h, const bdis_image *left, const bdis_image *right,
                             const bdis_params *p, const float *prev, float *disparity_out);
+
+/* Proposal start (R16): the coarsest level is seeded from `seed`, a disparity
+ * map at pyramid level seed_level (0..coarsest; count x ceil(H/2^l) x
+ * ceil(W/2^l) floats, values in that level's pixels, NaN allowed), reduced to
+ * level coarsest+1 by block means as at bdis_match_warm. With fallback = 0
+ * this is the warm start from that level. With fallback = 1 the coarsest
+ * level is searched twice, from the seed and from the plain start; a patch
+ * keeps the seeded result only if it is kept and the plain result is dropped
+ * or has no higher posterior, and pixels of that level that no kept patch
+ * covers carry the plain start: a proposal that every patch rejects gives
+ * exactly bdis_match. Not in the paper (its start is 0). */
+bdis_status bdis_match_seeded(bdis_handle *h, const bdis_image *left, const bdis_image *right,
+                              const bdis_params *p, const float *seed, int seed_level,
+                              int fallback, float *disparity_out);
+
+/* Learned start: the proposal network runs on pyramid level min(3,
+ * coarsest) of these pairs (inside the same launch sequence) and its output
+ * seeds the coarsest level as at bdis_match_seeded. */
+bdis_status bdis_match_learned(bdis_handle *h, bdis_net *net, const bdis_image *left,
+                               const bdis_image *right, const bdis_params *p, int fallback,
+                               float *disparity_out);
 
 /* Same, with HOST buffers: left/right are `count` dense width x height uint8
  * images in host memory, disparity_out a dense host float array. The call
@@ -327,8 +349,6 @@ void bdis_plan_destroy(bdis_plan *plan);
  * weights and activations, FP32 accumulation, on the tensor cores.
  * Master weights are FP32 in this order, layer by layer: W[co][ky*3+kx][ci]
  * (bdis_net_weight_count() floats in all), then b[co]. */
-typedef struct bdis_net bdis_net;
-
 int bdis_net_weight_count(void);
 
 /* weights: host, bdis_net_weight_count() floats (copied). */

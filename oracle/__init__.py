@@ -22,6 +22,7 @@ from .oracle import (  # noqa: F401
     densify_level,
     upsample,
     match,
+    match_seeded,
     match_stages,
     warm_map,
     FLAG_FLAT,

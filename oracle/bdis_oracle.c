@@ -512,6 +512,13 @@ void orc_upsample(const double *M, int mw, int mh, int f, int w, int h, double *
 
 /* ------------------------------------------------------------ the method */
 
+int orc_match_warm(const double *left, const double *right, int w, int h, const orc_params *p,
+                   const double *prev, double *out);
+int orc_match_seeded(const double *left, const double *right, int w, int h,
+                     const orc_params *p, const double *seed, int seed_level, int fallback,
+                     double *out);
+void orc_warm_map(const double *P, int w, int h, int level, double *out);
+
 /* Full BDIS on one pair (Sec. 2, Fig. 1). left/right: w x h gray levels in
  * [0, 255] as doubles (row-major). out: w x h, NaN where not estimated.
  * Returns 0 on success, a negative value on bad arguments or no memory. */
@@ -524,6 +531,13 @@ int orc_match(const double *left, const double *right, int w, int h, const orc_p
 int orc_match_warm(const double *left, const double *right, int w, int h, const orc_params *p,
                    const double *prev, double *out)
 {
+    return orc_match_seeded(left, right, w, h, p, prev, 0, 0, out);
+}
+
+int orc_match_seeded(const double *left, const double *right, int w, int h,
+                     const orc_params *p, const double *seed, int seed_level, int fallback,
+                     double *out)
+{
     const int ps = p->patch_size;
     const int top = p->coarsest_scale, fin = p->finest_scale;
     if (ps < 2 || ps > 32 || top < fin || fin < 0 || top > 15 || p->iterations < 0 ||
@@ -532,6 +546,7 @@ int orc_match_warm(const double *left, const double *right, int w, int h, const 
         (p->fusion != ORC_FUSION_BDIS && p->fusion != ORC_FUSION_DIS))
         return -1;
     if (orc_level_dim(w, top) < ps || orc_level_dim(h, top) < ps) return -1;
+    if (seed && (seed_level < 0 || seed_level > top)) return -1;
 
     int nl = top + 1;
     double **Lp = (double **)calloc(nl, sizeof(double *));
@@ -552,11 +567,12 @@ int orc_match_warm(const double *left, const double *right, int w, int h, const 
 
     double *coarse = NULL;
     int cw = 0, ch = 0;
-    if (prev) {
+    if (seed) {
         cw = orc_level_dim(w, top + 1);
         ch = orc_level_dim(h, top + 1);
         coarse = (double *)malloc(sizeof(double) * cw * ch);
-        orc_warm_map(prev, w, h, top + 1, coarse);
+        orc_warm_map(seed, orc_level_dim(w, seed_level), orc_level_dim(h, seed_level),
+                     top + 1 - seed_level, coarse);
     }
     for (int l = top; l >= fin; --l) {
         int W = lw[l], H = lh[l];
@@ -567,9 +583,40 @@ int orc_match_warm(const double *left, const double *right, int w, int h, const 
         double *wgt = (double *)malloc(sizeof(double) * np);
         double *dense = (double *)malloc(sizeof(double) * W * H);
         orc_sobel_x(Lp[l], W, H, G);
-        orc_search_level(Lp[l], Rp[l], G, W, H, coarse, cw, ch, p, NULL, dst, NULL, wgt, NULL,
-                         NULL, NULL);
-        orc_densify_level(W, H, p, dst, wgt, coarse, cw, ch, l == fin, Lp[l], Rp[l], dense);
+        const double *carry = coarse;
+        if (seed && fallback && l == top) {
+            /* R16: seeded and plain searches of the coarsest level, per-patch choice */
+            double *post_a = (double *)malloc(sizeof(double) * np);
+            double *dst_b = (double *)malloc(sizeof(double) * np);
+            double *wgt_b = (double *)malloc(sizeof(double) * np);
+            double *post_b = (double *)malloc(sizeof(double) * np);
+            int *fl_a = (int *)malloc(sizeof(int) * np), *fl_b = (int *)malloc(sizeof(int) * np);
+            orc_search_level(Lp[l], Rp[l], G, W, H, coarse, cw, ch, p, NULL, dst, post_a, wgt,
+                             fl_a, NULL, NULL);
+            orc_search_level(Lp[l], Rp[l], G, W, H, NULL, 0, 0, p, NULL, dst_b, post_b, wgt_b,
+                             fl_b, NULL, NULL);
+            const int drop = ORC_FLAG_DIVERGED | ORC_FLAG_SADDLE | ORC_FLAG_GAMMA |
+                             ORC_FLAG_EMPTY | ORC_FLAG_UNCONVERGED;
+            for (int k = 0; k < np; ++k) {
+                int use_seed = !(fl_a[k] & drop) && ((fl_b[k] & drop) || post_a[k] >= post_b[k]);
+                if (!use_seed) {
+                    dst[k] = dst_b[k];
+                    wgt[k] = wgt_b[k];
+                }
+            }
+            free(post_a);
+            free(dst_b);
+            free(wgt_b);
+            free(post_b);
+            free(fl_a);
+            free(fl_b);
+            carry = NULL; /* carried pixels keep the plain start */
+        } else {
+            orc_search_level(Lp[l], Rp[l], G, W, H, coarse, cw, ch, p, NULL, dst, NULL, wgt,
+                             NULL, NULL, NULL);
+        }
+        orc_densify_level(W, H, p, dst, wgt, carry, carry ? cw : 0, carry ? ch : 0, l == fin,
+                          Lp[l], Rp[l], dense);
         free(G);
         free(dst);
         free(wgt);
@@ -625,6 +672,19 @@ void orc_warm_map(const double *P, int w, int h, int level, double *out)
  * patches' initial values and its carried pixels). prev NULL = orc_match. */
 int orc_match_warm(const double *left, const double *right, int w, int h, const orc_params *p,
                    const double *prev, double *out);
+
+/* R16 proposal start: `seed` is a disparity map at pyramid level seed_level
+ * (values in that level's pixels, NaN allowed). Its block means seed the
+ * coarsest searched level as in R15 (blocks of 2^(coarsest + 1 - seed_level)
+ * pixels of the seed level). With fallback = 0 this is the warm start. With
+ * fallback = 1 the coarsest level is searched twice, from the seed and from
+ * the plain start (0); a patch keeps the seeded result only if it is kept and
+ * either the plain result is dropped or the seeded posterior is at least the
+ * plain one; pixels of that level that no kept patch covers carry the plain
+ * start, so a proposal that every patch rejects gives the plain method. */
+int orc_match_seeded(const double *left, const double *right, int w, int h,
+                     const orc_params *p, const double *seed, int seed_level, int fallback,
+                     double *out);
 
 /* uint8 entry: converts to gray levels as doubles (step 1 of the oracle). */
 int orc_match_u8(const uint8_t *left, const uint8_t *right, int w, int h, const orc_params *p,

@@ -103,6 +103,7 @@ def load():
         lib.orc_match_u8.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i, i, pp, dp]
         lib.orc_match_warm.argtypes = [dp, dp, i, i, pp, dp, dp]
         lib.orc_warm_map.argtypes = [dp, i, i, i, dp]
+        lib.orc_match_seeded.argtypes = [dp, dp, i, i, pp, dp, i, i, dp]
         _lib = lib
     return _lib
 
@@ -272,6 +273,20 @@ def match(left, right, params: OracleParams, prev=None) -> np.ndarray:
     else:
         lf, rf = _f64(left), _f64(right)
         rc_ = load().orc_match(_dp(lf), _dp(rf), w, h, ctypes.byref(params), _dp(out))
+    if rc_ != 0:
+        raise ValueError(f"oracle rejected the arguments (code {rc_})")
+    return out
+
+
+def match_seeded(left, right, params: OracleParams, seed, seed_level, fallback=True):
+    """R16: the method with the coarsest level seeded from `seed`, a disparity
+    map at pyramid level `seed_level`, with (or without) the per-patch
+    fallback to the plain start."""
+    h, w = left.shape
+    out = np.empty((h, w))
+    lf, rf, sf = _f64(left), _f64(right), _f64(seed)
+    rc_ = load().orc_match_seeded(_dp(lf), _dp(rf), w, h, ctypes.byref(params), _dp(sf),
+                                  int(seed_level), int(bool(fallback)), _dp(out))
     if rc_ != 0:
         raise ValueError(f"oracle rejected the arguments (code {rc_})")
     return out

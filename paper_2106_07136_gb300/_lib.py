@@ -23,7 +23,8 @@ EXPORTED = [
     "bdis_get_search_variant", "bdis_plan_create", "bdis_plan_run", "bdis_plan_info",
     "bdis_plan_workspace_bytes", "bdis_plan_destroy", "bdis_match_warm", "bdis_warm_map",
     "bdis_net_weight_count", "bdis_net_create", "bdis_net_forward", "bdis_net_gradient",
-    "bdis_net_train_step", "bdis_net_get_weights", "bdis_net_destroy",
+    "bdis_net_train_step", "bdis_net_get_weights", "bdis_net_destroy", "bdis_match_seeded",
+    "bdis_match_learned",
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
@@ -31,7 +32,7 @@ BDIS_PLAN_AUTOTUNE = 1
 STATIC_SCRATCH_BYTES = 24 << 20  # BDIS_STATIC_SCRATCH_BYTES
 
 TIMING_CLASSES = ["prepare_level0", "pyramid_level", "search", "densify", "upsample",
-                  "warm_map"]
+                  "warm_map", "proposal_net", "select_start"]
 
 
 class BdisParams(ctypes.Structure):
@@ -136,6 +137,8 @@ def load():
     lib.bdis_net_destroy.restype = None
     del fp
     lib.bdis_match_warm.argtypes = [c_void_p, ip, ip, pp, c_void_p, c_void_p]
+    lib.bdis_match_seeded.argtypes = [c_void_p, ip, ip, pp, c_void_p, c_int, c_int, c_void_p]
+    lib.bdis_match_learned.argtypes = [c_void_p, c_void_p, ip, ip, pp, c_int, c_void_p]
     lib.bdis_warm_map.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p]
     lib.bdis_plan_create.argtypes = [c_int, P(BdisGroup), c_int, pp, c_int, c_void_p,
                                      P(c_void_p)]

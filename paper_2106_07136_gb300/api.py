@@ -159,6 +159,42 @@ class Matcher:
               "bdis_match_warm")
         return out.view(b, h, w)[0] if squeeze else out
 
+    def _out(self, lb, out):
+        b, h, w = lb.shape
+        if out is None:
+            out = torch.empty((b, h, w), dtype=torch.float32, device=lb.device)
+        if not (out.is_contiguous() and out.dtype == torch.float32 and out.numel() == b * h * w):
+            raise ValueError("out must be a dense float32 tensor of B*H*W elements")
+        return out
+
+    def match_seeded(self, left, right, seed, seed_level, params: BdisParams = None,
+                     fallback: bool = True, out=None):
+        """Coarsest level seeded from `seed` (B, h_l, w_l) at pyramid level seed_level."""
+        params = params if params is not None else default_params()
+        squeeze = left.dim() == 2
+        lb, rb = _as_batch(left), _as_batch(right)
+        out = self._out(lb, out)
+        seed = _as_batch(seed).contiguous()
+        li, ri = image_desc(lb), image_desc(rb)
+        check(self._lib.bdis_match_seeded(self._h, ctypes.byref(li), ctypes.byref(ri),
+                                          ctypes.byref(params), seed.data_ptr(), int(seed_level),
+                                          int(bool(fallback)), out.data_ptr()),
+              "bdis_match_seeded")
+        return out.view(lb.shape)[0] if squeeze else out
+
+    def match_learned(self, net, left, right, params: BdisParams = None, fallback: bool = True,
+                      out=None):
+        """Coarsest level seeded by the proposal network (ProposalNet) run on level 3."""
+        params = params if params is not None else default_params()
+        squeeze = left.dim() == 2
+        lb, rb = _as_batch(left), _as_batch(right)
+        out = self._out(lb, out)
+        li, ri = image_desc(lb), image_desc(rb)
+        check(self._lib.bdis_match_learned(self._h, net._h, ctypes.byref(li), ctypes.byref(ri),
+                                           ctypes.byref(params), int(bool(fallback)),
+                                           out.data_ptr()), "bdis_match_learned")
+        return out.view(lb.shape)[0] if squeeze else out
+
     def match_host(self, left, right, params: BdisParams = None, out=None):
         """Host buffers in and out (numpy arrays or CPU tensors, pinned for DMA).
 

@@ -72,6 +72,20 @@ Layout plan_layout(int w, int h, int count, const bdis_params &p, bool host_stag
   lay.warm_w = level_dim(w, p.coarsest_scale + 1);
   lay.warm_h = level_dim(h, p.coarsest_scale + 1);
   lay.warm = take((size_t)lay.warm_w * lay.warm_h * count * sizeof(float));
+  {
+    const int top = p.coarsest_scale;
+    const size_t np_top = (size_t)grid_count(lay.lw[top], p.patch_size, stride) *
+                          grid_count(lay.lh[top], p.patch_size, stride) * count;
+    lay.d_star2 = take(np_top * sizeof(float));
+    lay.weight2 = take(np_top * sizeof(float));
+    lay.post1 = take(np_top * sizeof(float));
+    lay.post2 = take(np_top * sizeof(float));
+    lay.flags1 = take(np_top);
+    lay.flags2 = take(np_top);
+    lay.prop_level = top < 3 ? top : 3;
+    lay.prop = take((size_t)lay.lw[lay.prop_level] * lay.lh[lay.prop_level] * count *
+                    sizeof(float));
+  }
   if (host_staging) {
     lay.in_left = take((size_t)w * h * count);
     lay.in_right = take((size_t)w * h * count);
@@ -240,17 +254,20 @@ DensifyArgs level_densify_args(char *base, const Layout &lay, const bdis_params 
 // The whole method on device images already checked; `out` dense device.
 bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &right,
                       const bdis_params &p, float *out, const Layout &lay,
-                      const Tuning *tune = nullptr, const float *prev = nullptr) {
+                      const Tuning *tune = nullptr, const Seed *seed = nullptr) {
   char *base = static_cast<char *>(h->ws);
   auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
   auto F2 = [&](size_t off) { return reinterpret_cast<float2 *>(base + off); };
   const int count = left.count;
   cudaStream_t st = h->stream;
   cudaError_t e;
-  if (prev) {
-    // first, before the output (which may alias prev) is written
+  const int top = p.coarsest_scale;
+  const bool seeded = seed && (seed->map || seed->net);
+  if (seed && seed->map) {
+    // first, before the output (which may alias the seed) is written
     Timed tm(h, 5);
-    e = launch_warm_map(prev, left.width, left.height, p.coarsest_scale + 1, count,
+    e = launch_warm_map(seed->map, level_dim(left.width, seed->level),
+                        level_dim(left.height, seed->level), top + 1 - seed->level, count,
                         F(lay.warm), st);
     if (e != cudaSuccess) return record_cuda(e);
   }
@@ -267,15 +284,53 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
     }
     if (e != cudaSuccess) return record_cuda(e);
   }
+  if (seed && seed->net) {
+    // the proposal network on the level planes just built, then its seed map
+    const int nl = seed->level;
+    {
+      Timed tm(h, 6);
+      bdis_status s = net_forward_on(seed->net, F(lay.L[nl]), F(lay.R[nl]), 2, lay.lw[nl],
+                                     lay.lh[nl], count, F(lay.prop), st);
+      if (s != BDIS_OK) return s;
+    }
+    Timed tm(h, 5);
+    e = launch_warm_map(F(lay.prop), lay.lw[nl], lay.lh[nl], top + 1 - nl, count, F(lay.warm),
+                        st);
+    if (e != cudaSuccess) return record_cuda(e);
+  }
   for (int l = p.coarsest_scale; l >= p.finest_scale; --l) {
-    SearchArgs sa = level_search_args(base, lay, p, count, l, prev != nullptr);
+    const bool two = seeded && seed->fallback && l == top;
+    SearchArgs sa = level_search_args(base, lay, p, count, l, seeded);
     if (tune) apply_tuning(sa, tune->level[l]);
+    if (two) {
+      sa.posterior = F(lay.post1);
+      sa.flags = reinterpret_cast<uint8_t *>(base + lay.flags1);
+    }
     {
       Timed tm(h, 2);
       e = launch_search(sa, st);
     }
     if (e != cudaSuccess) return record_cuda(e);
-    DensifyArgs da = level_densify_args(base, lay, p, count, l, out, prev != nullptr);
+    if (two) {
+      // R16: the plain start of the same level, then the per-patch choice
+      SearchArgs sb = level_search_args(base, lay, p, count, l, false);
+      if (tune) apply_tuning(sb, tune->level[l]);
+      sb.d_star = F(lay.d_star2);
+      sb.weight = F(lay.weight2);
+      sb.posterior = F(lay.post2);
+      sb.flags = reinterpret_cast<uint8_t *>(base + lay.flags2);
+      {
+        Timed tm(h, 2);
+        e = launch_search(sb, st);
+      }
+      if (e != cudaSuccess) return record_cuda(e);
+      Timed tm(h, 7);
+      e = launch_select_start(sa.d_star, sa.weight, sa.posterior, sa.flags, sb.d_star, sb.weight,
+                              sb.posterior, sb.flags, sa.total, st);
+      if (e != cudaSuccess) return record_cuda(e);
+    }
+    // carried pixels of the coarsest level: the seed, unless the fallback applies
+    DensifyArgs da = level_densify_args(base, lay, p, count, l, out, seeded && !two);
     if (tune) apply_tuning(da, tune->level[l]);
     {
       Timed tm(h, 3);
@@ -330,7 +385,7 @@ bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right
 
 bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
                          const bdis_image &left, const bdis_image &right, const bdis_params &p,
-                         float *out, const Tuning *tune, const float *prev) {
+                         float *out, const Tuning *tune, const Seed *seed) {
   bdis_handle view;  // borrows the caller's scratch; owns nothing, times nothing
   view.stream = stream;
   view.ws = scratch;
@@ -338,7 +393,7 @@ bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t strea
   const Layout lay = plan_layout(left.width, left.height, left.count, p, false);
   if (lay.bytes > scratch_bytes) return BDIS_E_UNSUPPORTED;
   (void)0;
-  bdis_status s = run_match(&view, left, right, p, out, lay, tune, prev);
+  bdis_status s = run_match(&view, left, right, p, out, lay, tune, seed);
   view.ws = nullptr;
   return s;
 }
@@ -603,8 +658,9 @@ bdis_status bdis_match(bdis_handle *h, const bdis_image *left, const bdis_image 
   return run_match(h, *left, *right, *p, disparity_out, lay);
 }
 
-bdis_status bdis_match_warm(bdis_handle *h, const bdis_image *left, const bdis_image *right,
-                            const bdis_params *p, const float *prev, float *disparity_out) {
+static bdis_status match_with_seed(bdis_handle *h, const bdis_image *left,
+                                   const bdis_image *right, const bdis_params *p,
+                                   const Seed &seed, float *disparity_out) {
   if (!h || !disparity_out) return BDIS_E_INVALID_ARG;
   bdis_status s = check_pair(left, right);
   if (s != BDIS_OK) return s;
@@ -612,15 +668,49 @@ bdis_status bdis_match_warm(bdis_handle *h, const bdis_image *left, const bdis_i
   if (s != BDIS_OK) return s;
   s = check_geometry(left->width, left->height, *p);
   if (s != BDIS_OK) return s;
+  if ((seed.map || seed.net) && (seed.level < 0 || seed.level > p->coarsest_scale))
+    return BDIS_E_INVALID_ARG;
   s = bind_device(h);
   if (s != BDIS_OK) return s;
   if (check_device_ptr(left->data) != BDIS_OK || check_device_ptr(right->data) != BDIS_OK ||
-      check_device_ptr(disparity_out) != BDIS_OK || (prev && check_device_ptr(prev) != BDIS_OK))
+      check_device_ptr(disparity_out) != BDIS_OK ||
+      (seed.map && check_device_ptr(seed.map) != BDIS_OK))
     return BDIS_E_INVALID_ARG;
   const Layout lay = plan_layout(left->width, left->height, left->count, *p, false);
+  if (seed.net && seed.level != lay.prop_level) return BDIS_E_UNSUPPORTED;
   s = ensure_workspace(h, lay.bytes);
   if (s != BDIS_OK) return s;
-  return run_match(h, *left, *right, *p, disparity_out, lay, nullptr, prev);
+  return run_match(h, *left, *right, *p, disparity_out, lay, nullptr, &seed);
+}
+
+bdis_status bdis_match_warm(bdis_handle *h, const bdis_image *left, const bdis_image *right,
+                            const bdis_params *p, const float *prev, float *disparity_out) {
+  Seed seed;
+  seed.map = prev;
+  seed.level = 0;
+  return match_with_seed(h, left, right, p, seed, disparity_out);
+}
+
+bdis_status bdis_match_seeded(bdis_handle *h, const bdis_image *left, const bdis_image *right,
+                              const bdis_params *p, const float *seed_map, int seed_level,
+                              int fallback, float *disparity_out) {
+  if (!seed_map) return BDIS_E_INVALID_ARG;
+  Seed seed;
+  seed.map = seed_map;
+  seed.level = seed_level;
+  seed.fallback = fallback ? 1 : 0;
+  return match_with_seed(h, left, right, p, seed, disparity_out);
+}
+
+bdis_status bdis_match_learned(bdis_handle *h, bdis_net *net, const bdis_image *left,
+                               const bdis_image *right, const bdis_params *p, int fallback,
+                               float *disparity_out) {
+  if (!net || !p) return BDIS_E_INVALID_ARG;
+  Seed seed;
+  seed.net = net;
+  seed.level = p->coarsest_scale < 3 ? p->coarsest_scale : 3;
+  seed.fallback = fallback ? 1 : 0;
+  return match_with_seed(h, left, right, p, seed, disparity_out);
 }
 
 bdis_status bdis_warm_map(const float *prev, int width, int height, int level, int count,

@@ -83,6 +83,10 @@ struct Layout {
   size_t d_star = 0, weight = 0;
   size_t warm = 0;  // seed map of the coarsest level from a previous disparity
   int warm_w = 0, warm_h = 0;
+  // second search of the coarsest level (R16) and the posteriors / flags of both
+  size_t d_star2 = 0, weight2 = 0, post1 = 0, post2 = 0, flags1 = 0, flags2 = 0;
+  size_t prop = 0;  // network proposal at the proposal level
+  int prop_level = 3;
   size_t in_left = 0, in_right = 0, out = 0;  // host-path staging
   size_t bytes = 0;
 };
@@ -138,6 +142,21 @@ cudaError_t launch_pack_right(const float *R, int w, int h, int count, float2 *R
                               cudaStream_t st);
 cudaError_t launch_search(const SearchArgs &a, cudaStream_t st);
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st);
+cudaError_t launch_select_start(float *d_a, float *w_a, const float *p_a, const uint8_t *f_a,
+                                const float *d_b, const float *w_b, const float *p_b,
+                                const uint8_t *f_b, long long total, cudaStream_t st);
+// The network's forward pass on the caller's stream (net.cu).
+bdis_status net_forward_on(bdis_net *net, const float *L, const float *R, int r_stride, int w,
+                           int h, int count, float *out, cudaStream_t st);
+
+// How the coarsest searched level starts: 0 (plain), a given map, or the net.
+struct Seed {
+  const float *map = nullptr;  // a disparity map at pyramid level `level`
+  int level = 0;
+  bdis_net *net = nullptr;     // or: the proposal network run on pyramid level `level`
+  int fallback = 0;            // R16 per-patch choice against the plain start
+};
+
 cudaError_t launch_warm_map(const float *prev, int w, int h, int level, int count, float *out,
                             cudaStream_t st);
 cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, int h, int count,
@@ -164,8 +183,7 @@ bdis_status check_match_pointers(const bdis_image *left, const bdis_image *right
                                  const float *disparity_out);
 bdis_status run_match_in(void *scratch, size_t scratch_bytes, cudaStream_t stream,
                          const bdis_image &left, const bdis_image &right, const bdis_params &p,
-                         float *out, const Tuning *tune = nullptr,
-                         const float *prev = nullptr);
+                         float *out, const Tuning *tune = nullptr, const Seed *seed = nullptr);
 // Fill `tune` for every searched level by timing the candidate launches on
 // the given data (after one full run that fills the level planes).
 bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t stream,

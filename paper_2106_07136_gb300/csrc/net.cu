@@ -504,6 +504,23 @@ void net_release(bdis_net *n) {
 
 }  // namespace
 
+namespace bdis {
+
+bdis_status net_forward_on(bdis_net *n, const float *L, const float *R, int r_stride, int w,
+                           int h, int count, float *out, cudaStream_t st) {
+  const long long total = (long long)w * h * count;
+  bdis_status s = net_reserve(n, total);
+  if (s != BDIS_OK) return s;
+  cudaError_t e = forward(n, L, R, r_stride, h, w, total, st);
+  if (e == cudaSuccess) {
+    take_channel0_kernel<<<nblocks(total, 256), 256, 0, st>>>(n->z6, total, out);
+    e = cudaGetLastError();
+  }
+  return record_cuda(e);
+}
+
+}  // namespace bdis
+
 extern "C" {
 
 int bdis_net_weight_count(void) { return kMasterCount; }

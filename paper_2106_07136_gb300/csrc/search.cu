@@ -528,7 +528,32 @@ cudaError_t launch_groups(K kernel, int G, const SearchArgs &a, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// R16: keep the seeded result of a coarsest patch only if it is kept and the
+// plain result is dropped or has no higher posterior; otherwise take the plain.
+__global__ void select_start_kernel(float *__restrict__ d_a, float *__restrict__ w_a,
+                                    const float *__restrict__ p_a, const uint8_t *__restrict__ f_a,
+                                    const float *__restrict__ d_b, const float *__restrict__ w_b,
+                                    const float *__restrict__ p_b, const uint8_t *__restrict__ f_b,
+                                    long long total) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= total) return;
+  const bool keep_a = !(f_a[k] & kDropFlags) && ((f_b[k] & kDropFlags) || p_a[k] >= p_b[k]);
+  if (!keep_a) {
+    d_a[k] = d_b[k];
+    w_a[k] = w_b[k];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_select_start(float *d_a, float *w_a, const float *p_a, const uint8_t *f_a,
+                                const float *d_b, const float *w_b, const float *p_b,
+                                const uint8_t *f_b, long long total, cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  select_start_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d_a, w_a, p_a, f_a, d_b,
+                                                                      w_b, p_b, f_b, total);
+  return cudaGetLastError();
+}
 
 namespace {
 int g_cols_per_lane = 2;  // process-wide choice of the fast-path variant

@@ -551,3 +551,40 @@ def test_warm_start_reaches_beyond_the_cold_basin(orc):
     cold = orc.match(pair.left, pair.right, p)
     good_cold = np.isfinite(cold) & (np.abs(cold - k) < 1e-3)
     assert good_cold.sum() < 0.5 * est.sum()
+
+
+# ------------------------------------------- proposal start with fallback (R16)
+
+def test_seeded_without_fallback_is_the_warm_start(orc):
+    pair = synth.make_cfg1()
+    p = small_params(orc, overlap=0.5, iterations=8)
+    prev = orc.match(pair.left, pair.right, p)
+    a = orc.match(pair.left, pair.right, p, prev=prev)
+    b = orc.match_seeded(pair.left, pair.right, p, prev, 0, fallback=False)
+    assert np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(a[np.isfinite(a)],
+                                                                       b[np.isfinite(b)])
+
+
+def test_rejected_proposal_falls_back_to_the_plain_method(orc):
+    """A proposal far outside the image (every seeded coarsest patch has no
+    valid pixel and is dropped) gives exactly the plain result."""
+    pair = synth.make_cfg1()
+    p = small_params(orc, overlap=0.5, iterations=8)
+    plain = orc.match(pair.left, pair.right, p)
+    seed = np.full((orc.level_dim(120, 1), orc.level_dim(160, 1)), 500.0)
+    out = orc.match_seeded(pair.left, pair.right, p, seed, 1, fallback=True)
+    assert np.array_equal(np.isnan(out), np.isnan(plain))
+    assert np.array_equal(out[np.isfinite(out)], plain[np.isfinite(plain)])
+
+
+def test_good_proposal_is_kept_where_the_plain_start_fails(orc):
+    """A shift beyond the cold start's reach (as in the warm-start pin) is
+    recovered from a proposal given at level 1, and the fallback keeps it."""
+    k = 20
+    pair = synth.make_integer_shift_pair(48, 96, k)
+    p = small_params(orc, coarsest_scale=1, gamma=0.25)
+    seed = np.full((orc.level_dim(48, 1), orc.level_dim(96, 1)), (k - 0.7) / 2.0)
+    out = orc.match_seeded(pair.left, pair.right, p, seed, 1, fallback=True)
+    est = np.isfinite(out) & np.isfinite(pair.disp)
+    assert est.sum() > 0.9 * np.isfinite(pair.disp).sum()
+    assert np.median(np.abs(out[est] - k)) < 1e-3
