@@ -454,11 +454,87 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     U = Lh.shape[0]
     res["variants"]["mixed_batch_graph"] = measure_mixed_batch(args, bd, device, stream)
     res["serving"] = measure_serving(args, bd, device)
+    res["learned_vs_plain"] = measure_learned(args, bd, m, left, right, Lh, Rh, Dgt, device,
+                                              stream)
     res["variants"]["dis_fusion"] = {
         "value": B * kk / (ev0.elapsed_time(ev1) / 1e3), "unit": "pairs/s",
         "accuracy_vs_ground_truth": synth.error_stats(out[:U].cpu().numpy(), Dgt),
         "l2": "not flushed (back-to-back steps)"}
     return res
+
+
+def measure_learned(args, bd, m, left, right, Lh, Rh, Dgt, device, stream,
+                    iterations=(12, 8, 6, 5, 4)):
+    """Plain vs learned-init BDIS on the same batch: pairs/s and error against
+    the ground truth for several iteration counts, and the comparison at
+    matched error (bad-1 within 0.1 point of the plain method at the paper's
+    12 iterations)."""
+    import torch
+    import synth
+    path = os.path.join(ROOT, "paper_2106_07136_gb300", "weights", "proposal.bdisnet")
+    w, note = bd.load_net_weights(path)
+    net = bd.ProposalNet(w, device=device)
+    B, U = left.shape[0], Lh.shape[0]
+    out = torch.empty((B, H, W), dtype=torch.float32, device=device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(3, args.steps // 3)
+
+    def rate(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return B * k / (ev0.elapsed_time(ev1) / 1e3)
+
+    rows = []
+    for it in iterations:
+        p = bd.default_params(**dict(params_kw(args.patch), iterations=it))
+        rp = rate(lambda: m.match(left, right, p, out=out))
+        ep = synth.error_stats(out[:U].cpu().numpy(), Dgt)
+        rl = rate(lambda: m.match_learned(net, left, right, p, fallback=True, out=out))
+        el = synth.error_stats(out[:U].cpu().numpy(), Dgt)
+        rows.append({"iterations": it, "plain": {"pairs_per_s": rp, **ep},
+                     "learned": {"pairs_per_s": rl, **el}})
+    # single-pair latency of the learned form at the paper's settings
+    l1, r1 = left[0], right[0]
+    p12 = bd.default_params(**params_kw(args.patch))
+    o1 = torch.empty((H, W), dtype=torch.float32, device=device)
+    for _ in range(20):
+        m.match_learned(net, l1, r1, p12, fallback=True, out=o1)
+    torch.cuda.synchronize()
+    lat = []
+    for _ in range(args.latency_iters):
+        t0 = time.perf_counter()
+        m.match_learned(net, l1, r1, p12, fallback=True, out=o1)
+        stream.synchronize()
+        lat.append(1e3 * (time.perf_counter() - t0))
+    lat.sort()
+    net.close()
+    ref = next(r for r in rows if r["iterations"] == 12)["plain"]
+    bound = ref["bad1"] + 0.001
+
+    def fastest(kind):
+        ok = [r for r in rows if r[kind]["bad1"] <= bound]
+        best = max(ok, key=lambda r: r[kind]["pairs_per_s"]) if ok else None
+        return None if best is None else {"iterations": best["iterations"],
+                                          "pairs_per_s": best[kind]["pairs_per_s"],
+                                          "bad1": best[kind]["bad1"],
+                                          "mean_abs": best[kind]["mean_abs"]}
+    fp, fl = fastest("plain"), fastest("learned")
+    return {"weights": note, "rows": rows,
+            "matched_error": {
+                "bound": "bad-1 <= plain at 12 iterations + 0.1 point",
+                "plain_reference_12it": {"pairs_per_s": ref["pairs_per_s"], "bad1": ref["bad1"]},
+                "fastest_plain_within_bound": fp, "fastest_learned_within_bound": fl,
+                "learned_vs_plain_12it": (fl["pairs_per_s"] / ref["pairs_per_s"]) if fl else None,
+                "learned_vs_fastest_plain": (fl["pairs_per_s"] / fp["pairs_per_s"])
+                if (fl and fp) else None},
+            "latency_learned_12it": {"batch": 1, "p50_ms": lat[len(lat) // 2],
+                                     "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}}
 
 
 def measure_serving(args, bd, device, seconds=3.0, rate=2000.0, videos=4, frames=4):

@@ -11,6 +11,8 @@ from .api import (  # noqa: F401
     ProposalNet,
     net_init_weights,
     net_weight_count,
+    load_net_weights,
+    save_net_weights,
     default_params,
     densify_level,
     grid,

@@ -337,6 +337,43 @@ def net_init_weights(seed: int = 0) -> np.ndarray:
     return w
 
 
+WEIGHTS_MAGIC = b"BDISNET1"
+
+
+def save_net_weights(path, weights, note: str = ""):
+    """Versioned weights file: magic, version, count, note length, sha256 of the
+    float32 payload, note (utf-8), payload (little-endian float32)."""
+    import hashlib
+    import struct
+    w = np.ascontiguousarray(weights, dtype="<f4")
+    payload = w.tobytes()
+    nb = note.encode()
+    with open(path, "wb") as f:
+        f.write(WEIGHTS_MAGIC)
+        f.write(struct.pack("<III", 1, w.size, len(nb)))
+        f.write(hashlib.sha256(payload).digest())
+        f.write(nb)
+        f.write(payload)
+
+
+def load_net_weights(path):
+    """Read save_net_weights' format; checks magic, count and hash."""
+    import hashlib
+    import struct
+    data = open(path, "rb").read()
+    if data[:8] != WEIGHTS_MAGIC:
+        raise ValueError(f"{path}: not a proposal-network weights file")
+    version, count, nlen = struct.unpack("<III", data[8:20])
+    if version != 1 or count != net_weight_count():
+        raise ValueError(f"{path}: version {version}, {count} weights (need {net_weight_count()})")
+    digest = data[20:52]
+    note = data[52:52 + nlen].decode()
+    payload = data[52 + nlen:]
+    if len(payload) != 4 * count or hashlib.sha256(payload).digest() != digest:
+        raise ValueError(f"{path}: weights payload is corrupt")
+    return np.frombuffer(payload, dtype="<f4").astype(np.float32), note
+
+
 class ProposalNet:
     """The learned coarse proposal (bdis_net_*): forward, gradient, Adam steps."""
 

@@ -84,92 +84,112 @@ __global__ void pack_input_kernel(const float *__restrict__ L, const float *__re
 
 enum ConvMode { kFwdRelu = 0, kFwdLinearF32 = 1, kBwdDataMasked = 2 };
 
-// One warp computes 16 consecutive pixels x COUT channels; a block of 4 warps
-// 64 pixels. Weights (COUT x 9 x CIN bf16) live in shared memory.
-template <int CIN, int COUT, int MODE>
+// One warp computes MT x 16 consecutive pixels x COUT channels (MT m-tiles
+// share every weight fragment it loads); a block of 4 warps covers 64 MT
+// pixels per tile and loops over tiles (persistent), so the weights (COUT x 9
+// x CIN bf16) are staged in shared memory once per block.
+template <int CIN, int COUT, int MODE, int MT = 4>
 __global__ void __launch_bounds__(128) conv_mma_kernel(
     const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wt,
     const float *__restrict__ bias, int dil, int H, int W, long long total,
     const __nv_bfloat16 *__restrict__ mask, void *__restrict__ out) {
   static_assert(CIN % 16 == 0 && COUT % 8 == 0, "tile");
+  constexpr int NT = COUT / 8;
   __shared__ __align__(16) __nv_bfloat16 ws[COUT * 9 * CIN];
   for (int i = threadIdx.x * 8; i < COUT * 9 * CIN; i += blockDim.x * 8)
     *reinterpret_cast<uint4 *>(ws + i) = *reinterpret_cast<const uint4 *>(wt + i);
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long p0 = ((long long)blockIdx.x * 4 + warp) * 16;
   const int g = lane >> 2, q = lane & 3;
-  // the two pixel rows this thread feeds: p0 + g and p0 + g + 8
-  long long pr[2] = {p0 + g, p0 + g + 8};
-  int pb[2], py[2], px[2];
-  bool pv[2];
   const long long plane = (long long)H * W;
+  const long long per_tile = 64LL * MT;
+  for (long long tile = blockIdx.x; tile * per_tile < total; tile += gridDim.x) {
+    const long long p0 = tile * per_tile + (long long)warp * 16 * MT;
+    // pixel rows of this thread: m-tile m feeds rows p0 + 16 m + g and + 8
+    long long pr[MT][2];
+    int pb[MT][2], py[MT][2], px[MT][2];
+    bool pv[MT][2];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    pv[i] = pr[i] < total;
-    const long long pp = pv[i] ? pr[i] : 0;
-    pb[i] = (int)(pp / plane);
-    const int rem = (int)(pp - (long long)pb[i] * plane);
-    py[i] = rem / W;
-    px[i] = rem - py[i] * W;
-  }
-  float acc[COUT / 8][4];
+    for (int m = 0; m < MT; ++m)
 #pragma unroll
-  for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+      for (int i = 0; i < 2; ++i) {
+        pr[m][i] = p0 + 16 * m + g + 8 * i;
+        pv[m][i] = pr[m][i] < total;
+        const long long pp = pv[m][i] ? pr[m][i] : 0;
+        pb[m][i] = (int)(pp / plane);
+        const int rem = (int)(pp - (long long)pb[m][i] * plane);
+        py[m][i] = rem / W;
+        px[m][i] = rem - py[m][i] * W;
+      }
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int n = 0; n < NT; ++n) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
 #pragma unroll 1
-  for (int tap = 0; tap < 9; ++tap) {
-    const int dy = (tap / 3 - 1) * dil, dx = (tap % 3 - 1) * dil;
-    const __nv_bfloat16 *src[2];
+    for (int tap = 0; tap < 9; ++tap) {
+      const int dy = (tap / 3 - 1) * dil, dx = (tap % 3 - 1) * dil;
+      const __nv_bfloat16 *src[MT][2];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int yy = py[i] + dy, xx = px[i] + dx;
-      const bool ok = pv[i] && yy >= 0 && yy < H && xx >= 0 && xx < W;
-      src[i] = ok ? in + (((long long)pb[i] * H + yy) * W + xx) * CIN : nullptr;
-    }
+      for (int m = 0; m < MT; ++m)
 #pragma unroll
-    for (int kb = 0; kb < CIN / 16; ++kb) {
-      const int c0 = kb * 16 + q * 2;
-      uint32_t a[4];
-      a[0] = src[0] ? *reinterpret_cast<const uint32_t *>(src[0] + c0) : 0u;
-      a[1] = src[1] ? *reinterpret_cast<const uint32_t *>(src[1] + c0) : 0u;
-      a[2] = src[0] ? *reinterpret_cast<const uint32_t *>(src[0] + c0 + 8) : 0u;
-      a[3] = src[1] ? *reinterpret_cast<const uint32_t *>(src[1] + c0 + 8) : 0u;
+        for (int i = 0; i < 2; ++i) {
+          const int yy = py[m][i] + dy, xx = px[m][i] + dx;
+          const bool ok = pv[m][i] && yy >= 0 && yy < H && xx >= 0 && xx < W;
+          src[m][i] = ok ? in + (((long long)pb[m][i] * H + yy) * W + xx) * CIN : nullptr;
+        }
 #pragma unroll
-      for (int n = 0; n < COUT / 8; ++n) {
-        const __nv_bfloat16 *wr = ws + ((n * 8 + g) * 9 + tap) * CIN + c0;
-        uint32_t b[2];
-        b[0] = *reinterpret_cast<const uint32_t *>(wr);
-        b[1] = *reinterpret_cast<const uint32_t *>(wr + 8);
-        mma_bf16(acc[n], a, b);
+      for (int kb = 0; kb < CIN / 16; ++kb) {
+        const int c0 = kb * 16 + q * 2;
+        uint32_t b[NT][2];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          const __nv_bfloat16 *wr = ws + ((n * 8 + g) * 9 + tap) * CIN + c0;
+          b[n][0] = *reinterpret_cast<const uint32_t *>(wr);
+          b[n][1] = *reinterpret_cast<const uint32_t *>(wr + 8);
+        }
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+          uint32_t a[4];
+          a[0] = src[m][0] ? *reinterpret_cast<const uint32_t *>(src[m][0] + c0) : 0u;
+          a[1] = src[m][1] ? *reinterpret_cast<const uint32_t *>(src[m][1] + c0) : 0u;
+          a[2] = src[m][0] ? *reinterpret_cast<const uint32_t *>(src[m][0] + c0 + 8) : 0u;
+          a[3] = src[m][1] ? *reinterpret_cast<const uint32_t *>(src[m][1] + c0 + 8) : 0u;
+#pragma unroll
+          for (int n = 0; n < NT; ++n) mma_bf16(acc[m][n], a, b[n]);
+        }
       }
     }
-  }
-  // epilogue: acc[n][0..1] -> pixel row g, channels n*8 + 2q + {0,1}; [2..3] -> row g+8
+    // epilogue: acc[m][n][0..1] -> row 16m + g, channels 8n + 2q + {0,1}; [2..3] -> row + 8
 #pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    if (!pv[i]) continue;
-    const long long p = pr[i];
+    for (int m = 0; m < MT; ++m)
 #pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) {
-      const int c = n * 8 + q * 2;
-      float v0 = acc[n][2 * i], v1 = acc[n][2 * i + 1];
-      if (MODE == kFwdRelu) {
-        v0 = fmaxf(v0 + bias[c], 0.f);
-        v1 = fmaxf(v1 + bias[c + 1], 0.f);
-        *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(out) + p * COUT + c) =
-            pack_bf16(v0, v1);
-      } else if (MODE == kFwdLinearF32) {
-        float *o = reinterpret_cast<float *>(out) + p * COUT + c;
-        o[0] = v0 + bias[c];
-        o[1] = v1 + bias[c + 1];
-      } else {  // data gradient times the previous layer's ReLU derivative
-        const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162 *>(mask + p * COUT + c);
-        v0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
-        v1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
-        *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(out) + p * COUT + c) =
-            pack_bf16(v0, v1);
+      for (int i = 0; i < 2; ++i) {
+        if (!pv[m][i]) continue;
+        const long long p = pr[m][i];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          const int c = n * 8 + q * 2;
+          float v0 = acc[m][n][2 * i], v1 = acc[m][n][2 * i + 1];
+          if (MODE == kFwdRelu) {
+            v0 = fmaxf(v0 + bias[c], 0.f);
+            v1 = fmaxf(v1 + bias[c + 1], 0.f);
+            *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(out) + p * COUT + c) =
+                pack_bf16(v0, v1);
+          } else if (MODE == kFwdLinearF32) {
+            float *o = reinterpret_cast<float *>(out) + p * COUT + c;
+            o[0] = v0 + bias[c];
+            o[1] = v1 + bias[c + 1];
+          } else {  // data gradient times the previous layer's ReLU derivative
+            const __nv_bfloat162 mk =
+                *reinterpret_cast<const __nv_bfloat162 *>(mask + p * COUT + c);
+            v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+            v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+            *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_bfloat16 *>(out) + p * COUT + c) =
+                pack_bf16(v0, v1);
+          }
+        }
       }
-    }
   }
 }
 
@@ -428,11 +448,21 @@ cudaError_t pack_all(bdis_net *n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+int g_sms = 0;
+
 template <int CIN, int COUT, int MODE>
 void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, int dil, int H,
           int W, long long total, const __nv_bfloat16 *mask, void *out, cudaStream_t st) {
-  conv_mma_kernel<CIN, COUT, MODE><<<nblocks(total, 64), 128, 0, st>>>(in, wt, bias, dil, H, W,
-                                                                      total, mask, out);
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 152;
+  }
+  const long long tiles = (total + 255) / 256;  // 64 pixels x 4 m-tiles per block tile
+  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)g_sms * 3);
+  conv_mma_kernel<CIN, COUT, MODE><<<grid, 128, 0, st>>>(in, wt, bias, dil, H, W, total, mask,
+                                                         out);
 }
 
 cudaError_t forward(bdis_net *n, const float *L3, const float *R3, int r_stride, int H, int W,
