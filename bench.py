@@ -171,11 +171,30 @@ def whole_job_pairs_per_s(pairs_per_rank, steps, world, max_ms):
     return world * pairs_per_rank * steps / (max_ms / 1e3)
 
 
-def search_flops_per_pair(bd, ps, params):
+def search_flops_per_pair(bd, ps, params, left, right):
     """Algorithmic flops of the inverse search + window per pair: 8 flops per
-    pixel per patch evaluation, (iterations + window samples) evaluations."""
+    pixel per patch evaluation; a patch evaluates once per update it takes
+    (at most `iterations`: a converged patch stops early) and once per window
+    sample. The updates are counted by the kernels themselves (the per-patch
+    `steps` debug output) in one untimed stage-by-stage pass over `left`,
+    `right` (the distinct pairs of the batch). Returns (flops per pair,
+    patches per pair, mean updates per patch by level)."""
     n = bd.patch_count(W, H, params)
-    return n * ps * ps * 8 * (params.iterations + params.window_samples), n
+    L, R, G = bd.prepare_level0(left, right)
+    levels = {0: (L, R, G)}
+    for lvl in range(1, params.coarsest_scale + 1):
+        L, R, G = bd.pyramid_level(L, R)
+        levels[lvl] = (L, R, G)
+    coarse, steps, by_level = None, 0.0, {}
+    for lvl in range(params.coarsest_scale, params.finest_scale - 1, -1):
+        L, R, G = levels[lvl]
+        srch = bd.search_level(L, R, G, coarse, params)
+        st = srch["steps"].double()
+        by_level[lvl] = float(st.mean())
+        steps += float(st.sum()) / L.shape[0]
+        coarse = bd.densify_level(tuple(L.shape[1:]), params, srch["d_star"], srch["weight"],
+                                  coarse, lvl == params.finest_scale, L=L, R=R)
+    return ps * ps * 8 * (steps + n * params.window_samples), n, by_level
 
 
 def search_src_sha():
@@ -328,7 +347,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    flops, n_patches = search_flops_per_pair(bd, ps, params)
+    flops, n_patches, steps_by_level = search_flops_per_pair(bd, ps, params, left[:U], right[:U])
     s_ms, s_n = kt["search"]
     achieved = flops * B * args.steps / (s_ms / 1e3) / 1e12
     traffic = recorded_traffic(ps)
@@ -339,6 +358,8 @@ def main():
                 "kernel": "search (inverse search + posterior, all scales)",
                 "kernel_ms_per_launch": s_ms / s_n,
                 "algorithmic_flops_per_launch": flops * B / (s_n / args.steps),
+                "mean_updates_per_patch_by_level": steps_by_level,
+                "iterations_max": params.iterations,
                 "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
                 "peak_measured": probe,
                 "peak_measured_source": "FP32 FMA probe (bdis_probe_fp32_tflops) on this GPU",

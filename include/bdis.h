@@ -69,7 +69,8 @@ typedef struct {
  *   patch_size      side of the square patch in pixels (Sec. 1), 4..32;
  *   overlap         fraction shared by neighbouring patches, [0, 1); the
  *                   stride is round(patch_size * (1 - overlap)), at least 1;
- *   iterations      inverse-search steps per patch and scale (Eq. 1), >= 0;
+ *   iterations      maximum inverse-search steps per patch and scale (Eq. 1), >= 0;
+ *                   a patch stops early once its update falls below 1e-4 px;
  *   coarsest_scale  pyramid level where the search starts (level l has
  *                   ceil(W / 2^l) x ceil(H / 2^l) pixels), 0..15;
  *   finest_scale    level where it ends, 0..coarsest_scale; above 0 the map
@@ -114,6 +115,7 @@ typedef struct {
     float *energies;   /* window energies E_i, i = 0..s-1 */
     uint8_t *flags;    /* flag bits listed above */
     int32_t *n_valid;  /* pixels whose sample at D* is inside the image */
+    uint8_t *steps;    /* inverse-search updates applied to D, 0..iterations */
 } bdis_patch_debug;
 
 typedef struct bdis_handle bdis_handle;
@@ -202,8 +204,9 @@ bdis_status bdis_match_warm(bdis_handle *h, const bdis_image *left, const bdis_i
  * level coarsest+1 by block means as at bdis_match_warm. With fallback = 0
  * this is the warm start from that level. With fallback = 1 the coarsest
  * level is searched twice, from the seed and from the plain start; a patch
- * keeps the seeded result only if it is kept and the plain result is dropped
- * or has no higher posterior, and pixels of that level that no kept patch
+ * keeps the seeded result only if it is kept, lies more than 0.1 px from a
+ * kept plain result (closer, both found one solution and the plain result
+ * stands), and the plain result is dropped or has no higher posterior; pixels of that level that no kept patch
  * covers carry the plain start: a proposal that every patch rejects gives
  * exactly bdis_match. Not in the paper (its start is 0). */
 bdis_status bdis_match_seeded(bdis_handle *h, const bdis_image *left, const bdis_image *right,

@@ -78,6 +78,9 @@ enum {
 #define ORC_SADDLE_TAU 1e-6
 #define ORC_FLAT_EPS 1e-4
 #define ORC_CONVERGE_TOL 0.02
+/* A patch whose update falls below this (px) has converged: no more steps. */
+#define ORC_STEP_TOL 1e-4
+#define ORC_SAME_SOLUTION 0.1 /* px of the level searched twice (R16) */
 
 /* ---------------------------------------------------------------- geometry */
 
@@ -202,6 +205,7 @@ typedef struct {
     double weight;
     int flags;
     int n_valid;
+    int steps; /* updates applied to D (R12: at most `iterations`) */
 } orc_patch_result;
 
 /* Inverse-search Lucas-Kanade for one patch (Sec. 2.1, Eq. 1), then the
@@ -219,8 +223,9 @@ typedef struct {
  *     range and is abandoned there (no further steps, dropped); a patch
  *     whose last step is still above ORC_CONVERGE_TOL has not converged and
  *     is dropped (Sec. 3.2 discards the patches that do not converge).
- * R12: exactly `iterations` steps, no early exit other than flatness and
- *     leaving the search range.
+ * R12: at most `iterations` steps; a patch stops early when it is flat, when
+ *     it leaves its search range, or when its update falls below
+ *     ORC_STEP_TOL (further steps would move it by less than that).
  * energies[] receives s values (may be NULL). */
 void orc_search_patch(const double *L, const double *R, const double *G, int w, int h,
                       int x0, int y0, double u_init, const orc_params *p,
@@ -231,7 +236,7 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
     const int s = p->window_samples;
     double D = u_init;
     double last_step = 0.0;
-    int flags = 0;
+    int flags = 0, steps = 0;
 
     for (int it = 0; it < p->iterations; ++it) {
         /* means over the valid pixels at the current D */
@@ -273,8 +278,10 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
         }
         last_step = num / H;
         D += last_step;
+        ++steps;
         if (!isfinite(D)) break;
         if (fabs(D - u_init) > (double)ps) break; /* R8: left the search range */
+        if (fabs(last_step) < ORC_STEP_TOL) break; /* R12: converged */
     }
 
     /* R8: divergence and convergence */
@@ -376,6 +383,7 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
     }
     res->flags = flags;
     res->n_valid = n_valid;
+    res->steps = steps;
     if (energies)
         for (int i = 0; i < s; ++i) energies[i] = E[i];
 }
@@ -391,11 +399,12 @@ double orc_patch_init(const double *coarse, int cw, int ch, int x0, int y0, int 
 }
 
 /* Search every patch of one level. Outputs are per patch, row-major over the
- * patch grid (ny x nx). energies holds s values per patch (may be NULL). */
+ * patch grid (ny x nx); any may be NULL. energies holds s values per patch;
+ * steps the number of updates applied to each patch's D. */
 void orc_search_level(const double *L, const double *R, const double *G, int w, int h,
                       const double *coarse, int cw, int ch, const orc_params *p,
                       double *u_init, double *d_star, double *posterior, double *weight,
-                      int *flags, int *n_valid, double *energies)
+                      int *flags, int *n_valid, double *energies, int *steps)
 {
     const int ps = p->patch_size;
     const int stride = orc_grid_stride(ps, p->overlap);
@@ -415,6 +424,7 @@ void orc_search_level(const double *L, const double *R, const double *G, int w, 
             if (weight) weight[k] = res.weight;
             if (flags) flags[k] = res.flags;
             if (n_valid) n_valid[k] = res.n_valid;
+            if (steps) steps[k] = res.steps;
         }
 }
 
@@ -592,13 +602,17 @@ int orc_match_seeded(const double *left, const double *right, int w, int h,
             double *post_b = (double *)malloc(sizeof(double) * np);
             int *fl_a = (int *)malloc(sizeof(int) * np), *fl_b = (int *)malloc(sizeof(int) * np);
             orc_search_level(Lp[l], Rp[l], G, W, H, coarse, cw, ch, p, NULL, dst, post_a, wgt,
-                             fl_a, NULL, NULL);
+                             fl_a, NULL, NULL, NULL);
             orc_search_level(Lp[l], Rp[l], G, W, H, NULL, 0, 0, p, NULL, dst_b, post_b, wgt_b,
-                             fl_b, NULL, NULL);
+                             fl_b, NULL, NULL, NULL);
             const int drop = ORC_FLAG_DIVERGED | ORC_FLAG_SADDLE | ORC_FLAG_GAMMA |
                              ORC_FLAG_EMPTY | ORC_FLAG_UNCONVERGED;
             for (int k = 0; k < np; ++k) {
-                int use_seed = !(fl_a[k] & drop) && ((fl_b[k] & drop) || post_a[k] >= post_b[k]);
+                /* both kept and within ORC_SAME_SOLUTION px: one solution, the plain one */
+                int same = !(fl_a[k] & drop) && !(fl_b[k] & drop) &&
+                           fabs(dst[k] - dst_b[k]) <= ORC_SAME_SOLUTION;
+                int use_seed = !same && !(fl_a[k] & drop) &&
+                               ((fl_b[k] & drop) || post_a[k] >= post_b[k]);
                 if (!use_seed) {
                     dst[k] = dst_b[k];
                     wgt[k] = wgt_b[k];
@@ -613,7 +627,7 @@ int orc_match_seeded(const double *left, const double *right, int w, int h,
             carry = NULL; /* carried pixels keep the plain start */
         } else {
             orc_search_level(Lp[l], Rp[l], G, W, H, coarse, cw, ch, p, NULL, dst, NULL, wgt,
-                             NULL, NULL, NULL);
+                             NULL, NULL, NULL, NULL);
         }
         orc_densify_level(W, H, p, dst, wgt, carry, carry ? cw : 0, carry ? ch : 0, l == fin,
                           Lp[l], Rp[l], dense);
@@ -678,9 +692,11 @@ int orc_match_warm(const double *left, const double *right, int w, int h, const 
  * coarsest searched level as in R15 (blocks of 2^(coarsest + 1 - seed_level)
  * pixels of the seed level). With fallback = 0 this is the warm start. With
  * fallback = 1 the coarsest level is searched twice, from the seed and from
- * the plain start (0); a patch keeps the seeded result only if it is kept and
- * either the plain result is dropped or the seeded posterior is at least the
- * plain one; pixels of that level that no kept patch covers carry the plain
+ * the plain start (0); a patch keeps the seeded result only if it is kept,
+ * differs from a kept plain result by more than ORC_SAME_SOLUTION pixels
+ * (closer, the two searches found the same solution and the plain one
+ * stands), and either the plain result is dropped or the seeded posterior is
+ * at least the plain one; pixels of that level that no kept patch covers carry the plain
  * start, so a proposal that every patch rejects gives the plain method. */
 int orc_match_seeded(const double *left, const double *right, int w, int h,
                      const orc_params *p, const double *seed, int seed_level, int fallback,

@@ -96,7 +96,7 @@ def load():
         lib.orc_search_patch.argtypes = [dp, dp, dp, i, i, i, i, ctypes.c_double, pp,
                                          ctypes.c_void_p, dp]
         lib.orc_search_level.argtypes = [dp, dp, dp, i, i, dp, i, i, pp, dp, dp, dp, dp, ip, ip,
-                                         dp]
+                                         dp, ip]
         lib.orc_densify_level.argtypes = [i, i, pp, dp, dp, dp, i, i, i, dp, dp, dp]
         lib.orc_upsample.argtypes = [dp, i, i, i, i, i, dp]
         lib.orc_match.argtypes = [dp, dp, i, i, pp, dp]
@@ -169,7 +169,7 @@ def patch_init(coarse, x0, y0, ps):
 class _PatchResult(ctypes.Structure):
     _fields_ = [("u_init", ctypes.c_double), ("d_star", ctypes.c_double),
                 ("posterior", ctypes.c_double), ("weight", ctypes.c_double),
-                ("flags", ctypes.c_int), ("n_valid", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("n_valid", ctypes.c_int), ("steps", ctypes.c_int)]
 
 
 @dataclass
@@ -181,6 +181,7 @@ class PatchResult:
     flags: int
     n_valid: int
     energies: np.ndarray
+    steps: int = 0  # updates applied to D (R12: at most `iterations`)
 
 
 def search_patch(L, R, G, x0, y0, u_init, params: OracleParams) -> PatchResult:
@@ -190,7 +191,8 @@ def search_patch(L, R, G, x0, y0, u_init, params: OracleParams) -> PatchResult:
     e = np.zeros(params.window_samples)
     load().orc_search_patch(_dp(L), _dp(R), _dp(G), w, h, int(x0), int(y0), float(u_init),
                             ctypes.byref(params), ctypes.byref(res), _dp(e))
-    return PatchResult(res.u_init, res.d_star, res.posterior, res.weight, res.flags, res.n_valid, e)
+    return PatchResult(res.u_init, res.d_star, res.posterior, res.weight, res.flags, res.n_valid, e,
+                       res.steps)
 
 
 def search_level(L, R, G, coarse, params: OracleParams) -> dict:
@@ -202,6 +204,7 @@ def search_level(L, R, G, coarse, params: OracleParams) -> dict:
     out = {k: np.empty((ny, nx)) for k in ("u_init", "d_star", "posterior", "weight")}
     out["flags"] = np.empty((ny, nx), dtype=np.int32)
     out["n_valid"] = np.empty((ny, nx), dtype=np.int32)
+    out["steps"] = np.empty((ny, nx), dtype=np.int32)
     out["energies"] = np.empty((ny, nx, params.window_samples))
     if coarse is None:
         cp, cw, ch = None, 0, 0
@@ -211,7 +214,7 @@ def search_level(L, R, G, coarse, params: OracleParams) -> dict:
     load().orc_search_level(_dp(L), _dp(R), _dp(G), w, h, cp, cw, ch, ctypes.byref(params),
                             _dp(out["u_init"]), _dp(out["d_star"]), _dp(out["posterior"]),
                             _dp(out["weight"]), _ip(out["flags"]), _ip(out["n_valid"]),
-                            _dp(out["energies"]))
+                            _dp(out["energies"]), _ip(out["steps"]))
     return out
 
 

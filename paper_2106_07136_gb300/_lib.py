@@ -56,7 +56,7 @@ class BdisImage(ctypes.Structure):
 
 class BdisPatchDebug(ctypes.Structure):
     _fields_ = [("u_init", c_void_p), ("posterior", c_void_p), ("energies", c_void_p),
-                ("flags", c_void_p), ("n_valid", c_void_p)]
+                ("flags", c_void_p), ("n_valid", c_void_p), ("steps", c_void_p)]
 
 
 class BdisGroup(ctypes.Structure):

@@ -490,7 +490,8 @@ def search_level(L, R, G, coarse, params: BdisParams, debug: bool = True, stream
     """Inverse search + posterior of every patch of one level (R packed).
 
     Returns tensors shaped (B, ny, nx): d_star, weight and, with debug, u_init,
-    posterior, flags, n_valid and energies (B, ny, nx, s)."""
+    posterior, flags, n_valid, steps (updates applied to D, uint8) and energies
+    (B, ny, nx, s)."""
     L, G = (_as_batch(t).contiguous() for t in (L, G))
     R = _packed(R)
     b, h, w = L.shape
@@ -505,10 +506,11 @@ def search_level(L, R, G, coarse, params: BdisParams, debug: bool = True, stream
                    posterior=torch.empty((b, ny, nx), **f32),
                    energies=torch.empty((b, ny, nx, params.window_samples), **f32),
                    flags=torch.empty((b, ny, nx), dtype=torch.uint8, device=dev),
-                   n_valid=torch.empty((b, ny, nx), dtype=torch.int32, device=dev))
+                   n_valid=torch.empty((b, ny, nx), dtype=torch.int32, device=dev),
+                   steps=torch.empty((b, ny, nx), dtype=torch.uint8, device=dev))
         dbg = BdisPatchDebug(out["u_init"].data_ptr(), out["posterior"].data_ptr(),
                              out["energies"].data_ptr(), out["flags"].data_ptr(),
-                             out["n_valid"].data_ptr())
+                             out["n_valid"].data_ptr(), out["steps"].data_ptr())
     if coarse is not None:
         coarse = _as_batch(coarse).contiguous()
         cp, cw, ch = coarse.data_ptr(), coarse.shape[2], coarse.shape[1]

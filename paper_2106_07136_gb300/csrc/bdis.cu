@@ -600,7 +600,8 @@ void bdis_destroy(bdis_handle *h) {
 }
 
 bdis_status bdis_set_search_variant(int columns_per_lane) {
-  if (columns_per_lane != 1 && columns_per_lane != 2) return BDIS_E_INVALID_ARG;
+  if (columns_per_lane != 1 && columns_per_lane != 2 && columns_per_lane != 4)
+    return BDIS_E_INVALID_ARG;
   set_search_cols_per_lane(columns_per_lane);
   return BDIS_OK;
 }
@@ -811,6 +812,7 @@ bdis_status bdis_search_level(const float *L, const float *R, const float *G, in
     a.energies = dbg->energies;
     a.flags = dbg->flags;
     a.n_valid = dbg->n_valid;
+    a.steps = dbg->steps;
   }
   return record_cuda(launch_search(a, static_cast<cudaStream_t>(stream)));
 }

@@ -23,6 +23,11 @@ constexpr float kFlatEps = 1e-4f;
 // Largest final update (px) of a patch that counts as converged; patches whose
 // last step is larger are dropped (Sec. 3.2 discards non-converged patches).
 constexpr float kConvergeTol = 0.02f;
+// A patch whose update falls below this (px) has converged and stops stepping
+// (the step count is a maximum); a warp leaves the loop when all its patches have.
+constexpr float kStepTol = 1e-4f;
+// R16: seeded and plain results of one patch this close (px) are one solution
+constexpr float kSameSolution = 0.1f;
 // Largest window the search kernel keeps track of.
 constexpr int kMaxWindow = 15;
 // Largest patch side (one patch per group of at most 32 lanes).
@@ -106,13 +111,14 @@ struct SearchArgs {
   int iters, s;
   float step, kappa;
   int nmin_valid, normalize;
-  int cols_per_lane;  // fast path: columns of a patch per lane (1, or 2-3)
+  int cols_per_lane;  // fast path: columns of a patch per lane (1, 2, 3 or 4)
   int block_threads;  // 0 = 128
   int fusion;         // BDIS_FUSION_*
   float *d_star, *weight;
   float *u_init, *posterior, *energies;
   uint8_t *flags;
   int32_t *n_valid;
+  uint8_t *steps;
 };
 
 struct DensifyArgs {

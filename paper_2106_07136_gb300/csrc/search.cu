@@ -98,8 +98,8 @@ __device__ __forceinline__ PatchPos patch_pos(const SearchArgs &a, long long k) 
 // relative to the smallest energy) and the patch flags; writes the outputs.
 __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, bool write,
                                              float D, float u0, float last_step, bool flat,
-                                             int nvalid, int nc, float Ec, float Eo, float Emin,
-                                             float z, int ps) {
+                                             int steps, int nvalid, int nc, float Ec, float Eo,
+                                             float Emin, float z, int ps) {
   uint8_t flags = flat ? kFlagFlat : 0;
   if (!isfinite(D) || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
   if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
@@ -125,6 +125,7 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
     if (a.posterior) a.posterior[k] = post;
     if (a.flags) a.flags[k] = flags;
     if (a.n_valid) a.n_valid[k] = nvalid;
+    if (a.steps) a.steps[k] = (uint8_t)steps;
   }
 }
 
@@ -132,7 +133,7 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
 // iterations and the gamma count only.
 __device__ __forceinline__ void finish_patch_dis(const SearchArgs &a, long long k, bool write,
                                                  float D, float u0, float last_step, bool flat,
-                                                 int nvalid, int ps) {
+                                                 int steps, int nvalid, int ps) {
   uint8_t flags = flat ? kFlagFlat : 0;
   if (!isfinite(D) || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
   if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
@@ -144,6 +145,7 @@ __device__ __forceinline__ void finish_patch_dis(const SearchArgs &a, long long 
     if (a.posterior) a.posterior[k] = 0.f;
     if (a.flags) a.flags[k] = flags;
     if (a.n_valid) a.n_valid[k] = nvalid;
+    if (a.steps) a.steps[k] = (uint8_t)steps;
   }
 }
 
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   // ---- inverse-search iterations (Eq. 1)
   float D = u0, last_step = 0.f;
   bool frozen = false, flat = false, have = false;
+  int steps = 0;
   unsigned prev = 0u;
   float gc[CPL][PS];
 #pragma unroll
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   float H = 0.f, invH = 0.f, gcT = 0.f;
   int n = 0;
   for (int it = 0; it < a.iters; ++it) {
+    if (__all_sync(kFull, frozen)) break;  // every patch of the warp has stopped
     int kd;
     float t;
     split_disp(D, kd, t);
@@ -275,8 +279,10 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
     if (!frozen) {
       last_step = (Ssum - gcT) * invH;
       D += last_step;
-      // non-finite, or left the search range: no further steps (dropped below)
-      if (!isfinite(D) || fabsf(D - u0) > (float)PS) frozen = true;
+      ++steps;
+      // non-finite, or left the search range (dropped below), or converged
+      if (!isfinite(D) || fabsf(D - u0) > (float)PS || fabsf(last_step) < kStepTol)
+        frozen = true;
     }
   }
 
@@ -301,7 +307,7 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   }
   const int nvalid = PS * (int)group_sum<G>((float)nv_lane);
   if (a.fusion == BDIS_FUSION_DIS) {
-    finish_patch_dis(a, k, live && c == 0, D, u0, last_step, flat, nvalid, PS);
+    finish_patch_dis(a, k, live && c == 0, D, u0, last_step, flat, steps, nvalid, PS);
     return;
   }
   const int nc = PS * (int)group_sum<G>((float)nc_lane);
@@ -311,8 +317,11 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   // sums exactly: sum (d - md)^2 = S2 - 2 (md - cs) S1 + n (md - cs)^2.
   float cs[CPL];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j)
+  for (int j = 0; j < CPL; ++j) {
     cs[j] = vc[j] ? lerp_packed(__ldg(R2 + ib + j), t) - T[j][0] : 0.f;
+#pragma unroll
+    for (int r = 0; r < PS; ++r) T[j][r] += cs[j];  // the window works on T + shift
+  }
   const bool write = live && c == 0;
   float E[S];
 #pragma unroll
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
         const float2 *p = R2 + ib + j + off[i];
 #pragma unroll
         for (int r = 0; r < PS; ++r) {
-          const float d = lerp_packed(__ldg(p + (size_t)r * w), tt[i]) - (T[j][r] + cs[j]);
+          const float d = lerp_packed(__ldg(p + (size_t)r * w), tt[i]) - T[j][r];
           if (r & 1) {
             s1b += d;
             s2b = fmaf(d, d, s2b);
@@ -364,7 +373,8 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   float z = 0.f;
 #pragma unroll
   for (int i = 0; i < S; ++i) z += expf(-(E[i] - Emin) / a.kappa);
-  finish_patch(a, k, write, D, u0, last_step, flat, nvalid, nc, E[HALF], Eo, Emin, z, PS);
+  finish_patch(a, k, write, D, u0, last_step, flat, steps, nvalid, nc, E[HALF], Eo, Emin, z,
+               PS);
 }
 
 // ---------------------------------------------------------- generic path
@@ -393,6 +403,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
   const float u0 = pp.u0;
   float D = u0, last_step = 0.f;
   bool frozen = false, flat = false, have = false;
+  int steps = 0;
   unsigned prev = 0u;
   float gc[G];
 #pragma unroll
@@ -400,6 +411,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
   float H = 0.f, gcT = 0.f;
   int n = 0;
   for (int it = 0; it < a.iters; ++it) {
+    if (__all_sync(kFull, frozen)) break;
     int kd;
     float t;
     split_disp(D, kd, t);
@@ -447,7 +459,9 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
     if (!frozen) {
       last_step = (Ssum - gcT) / H;
       D += last_step;
-      if (!isfinite(D) || fabsf(D - u0) > (float)ps) frozen = true;
+      ++steps;
+      if (!isfinite(D) || fabsf(D - u0) > (float)ps || fabsf(last_step) < kStepTol)
+        frozen = true;
     }
   }
 
@@ -458,7 +472,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
   const bool v0 = act && fin && sample_ok(x + kd, t, w);
   const int nvalid = ps * __popc(__ballot_sync(kFull, v0) & gbits);
   if (a.fusion == BDIS_FUSION_DIS) {
-    finish_patch_dis(a, k, live && c == 0, D, u0, last_step, flat, nvalid, ps);
+    finish_patch_dis(a, k, live && c == 0, D, u0, last_step, flat, steps, nvalid, ps);
     return;
   }
   const int half = (a.s - 1) / 2;
@@ -506,7 +520,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
       z += expf(-(E - Emin) / a.kappa);
     }
   }
-  finish_patch(a, k, write, D, u0, last_step, flat, nvalid, nc, Ec, Eo, Emin, z, ps);
+  finish_patch(a, k, write, D, u0, last_step, flat, steps, nvalid, nc, Ec, Eo, Emin, z, ps);
 }
 
 template <int PS, int CPL, int MINB>
@@ -537,7 +551,10 @@ __global__ void select_start_kernel(float *__restrict__ d_a, float *__restrict__
                                     long long total) {
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= total) return;
-  const bool keep_a = !(f_a[k] & kDropFlags) && ((f_b[k] & kDropFlags) || p_a[k] >= p_b[k]);
+  const bool kept_a = !(f_a[k] & kDropFlags), kept_b = !(f_b[k] & kDropFlags);
+  // both kept and this close: the two searches found one solution; the plain one stands
+  const bool same = kept_a && kept_b && fabsf(d_a[k] - d_b[k]) <= kSameSolution;
+  const bool keep_a = !same && kept_a && (!kept_b || p_a[k] >= p_b[k]);
   if (!keep_a) {
     d_a[k] = d_b[k];
     w_a[k] = w_b[k];
@@ -587,7 +604,11 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
   const int count = (int)(a.total / a.np);
   if (a.s == 5 && a.step == 0.5f && count <= 65535) {
     const int cpl = a.cols_per_lane;
-    if (a.ps == 8) return cpl == 1 ? launch_fixed<8, 1, 8>(a, st) : launch_fixed<8, 2, 6>(a, st);
+    if (a.ps == 8) {
+      if (cpl == 1) return launch_fixed<8, 1, 8>(a, st);
+      if (cpl == 4) return launch_fixed<8, 4, 4>(a, st);
+      return launch_fixed<8, 2, 6>(a, st);
+    }
     if (a.ps == 12) return cpl == 1 ? launch_fixed<12, 1, 4>(a, st) : launch_fixed<12, 3, 3>(a, st);
     if (a.ps == 16) return cpl == 1 ? launch_fixed<16, 1, 4>(a, st) : launch_fixed<16, 2, 3>(a, st);
   }

@@ -11,7 +11,7 @@ import torch
 
 import paper_2106_07136_gb300 as bd
 import synth
-from gpu_helpers import assert_e2e, dev, host
+from gpu_helpers import WARM_STREAM, assert_e2e, dev, host
 from paper_2106_07136_gb300 import serve
 
 pytestmark = pytest.mark.gpu
@@ -67,7 +67,7 @@ def test_warm_start_gpu_matches_oracle(orc):
     """bdis_match_warm against the oracle's warm start on consecutive frames."""
     params = bd.default_params(**KW)
     op = orc.OracleParams.make(**KW)
-    v = synth.VideoStream(seed=synth.stereo.pair_seed(5, 99), h=240, w=320)
+    v = synth.VideoStream(seed=synth.stereo.pair_seed(*WARM_STREAM), h=240, w=320)
     f0, f1 = v.next(), v.next()
     m = bd.Matcher()
     d0 = host(m.match(dev(f0.left, torch.uint8), dev(f0.right, torch.uint8), params))
