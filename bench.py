@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--unique", type=int, default=16, help="distinct seeded pairs per rank")
     ap.add_argument("--patch", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0,
-                    help="search lane layout: 1 column per lane, 2 wide; 0 = library default")
+                    help="search lane layout: 1, 2 or 4 columns per lane; 0 = library default")
+    ap.add_argument("--tiling", type=int, default=0, choices=(0, 1),
+                    help="search kernel: 1 = warp-tiled shared-memory sampling (default 0)")
     ap.add_argument("--latency-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -294,6 +296,7 @@ def main():
     params = bd.default_params(**params_kw(ps))
     if args.variant:
         bd.set_search_variant(args.variant)
+    bd.set_search_tiling(bool(args.tiling))
     B, U = args.batch, min(args.unique, args.batch)
     first = rank_first_pair(rank, U)
     Lh, Rh, Dgt = make_pairs(first, U)
@@ -392,6 +395,7 @@ def main():
                    "pairs_per_step_per_gpu": B, "unique_pairs_per_gpu": U,
                    "patches_per_pair": n_patches,
                    "search_variant": bd.get_search_variant(),
+                   "search_tiling": int(bd.get_search_tiling()),
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
         "mpix_per_s": value * W * H / 1e6,

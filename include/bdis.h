@@ -28,7 +28,9 @@
  * no update), 2 diverged (moved more than the patch size from its start, or
  * non-finite), 4 saddle (another window sample has lower energy), 8 below
  * gamma, 16 no pixel valid at every window sample, 32 not converged (last
- * update above 0.02 px). Any bit but 1 drops the patch.
+ * update above 0.02 px). Any bit but 1 drops the patch. The window of a
+ * diverged patch is not evaluated: its posterior is 0 and bits 4 and 16 stay
+ * clear.
  */
 #ifndef BDIS_H
 #define BDIS_H
@@ -295,10 +297,30 @@ bdis_status bdis_upsample(const float *map, int map_width, int map_height, int l
 /* Tuning: lane layout of the inverse-search kernel for patch sizes 8, 12 and
  * 16 with the paper's 5-sample window. 1 = one patch column per lane (a
  * group of 8 or 16 lanes per patch); 2 = the wide layout (2 columns per lane
- * for sizes 8 and 16, 3 for size 12). Results are identical up to float
- * rounding; the choice only moves speed. Process-wide; default 2. */
+ * for sizes 8 and 16, 3 for size 12); 4 = 4 columns per lane (size 8 only;
+ * other sizes take 2). Results are identical up to float rounding; the
+ * choice only moves speed. Process-wide; default 2. Returns
+ * BDIS_E_INVALID_ARG for any other value. */
 bdis_status bdis_set_search_variant(int columns_per_lane);
 int bdis_get_search_variant(void);
+
+/* Tuning: how that kernel reads the right view. 0 (default) = every sample
+ * is read from global memory (through L1). 1 = warp-tiled: the patches of a
+ * warp lie on one patch-grid row, and the right-view rows they can sample
+ * while inside their search range are staged once in shared memory. A warp
+ * whose starts spread too far for its tile reads global memory instead.
+ * Results are bit-identical either way. Process-wide. */
+void bdis_set_search_tiling(int on);
+int bdis_get_search_tiling(void);
+
+/* Tuning: the densification kernel (Eq. 5 fusion, BDIS mode). 0 (default) =
+ * the strip kernel where the grid stride divides the patch size (overlap
+ * 0.75 at patch sizes 8, 12, 16), tiles of 32 rows otherwise; 8, 16 or 32 =
+ * the tiled kernel with that tile height. Results are identical whichever
+ * runs. Process-wide; BDIS_E_INVALID_ARG for any other value. A plan's
+ * autotuner makes its own per-level choice. */
+bdis_status bdis_set_densify_variant(int tile_height);
+int bdis_get_densify_variant(void);
 
 /* Measurement utility, not part of the method: FP32 FMA throughput of the
  * current device in TFLOP/s (the roofline denominator of the inverse search).
@@ -329,7 +351,8 @@ typedef struct {
 typedef struct {
     int search_columns_per_lane; /* 0 = default */
     int search_block_threads;    /* 0 = default (128) */
-    int densify_tile_height;     /* 0 = default (32) */
+    int densify_tile_height;     /* 0 = strip kernel (stride divides the patch
+                                    size), else tiles of 32; 8/16/32 = tiles */
     size_t workspace_bytes;      /* of the whole group */
 } bdis_plan_choice;
 

@@ -299,12 +299,15 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
             }
 
     /* R6: Bayesian window P' = {D* + (i - (s-1)/2) * step}, energies over the
-     * pixels valid at every sample so that they compare (Sec. 2.2). */
+     * pixels valid at every sample so that they compare (Sec. 2.2). R8: a
+     * patch that left its search range is dropped as diverged; its window is
+     * not evaluated (posterior 0, no window flags). */
+    const int diverged = (flags & ORC_FLAG_DIVERGED) != 0;
     double E[64];
     unsigned char common[32 * 32];
     int n_common = 0;
     for (int q = 0; q < ps * ps; ++q) common[q] = 0;
-    if (isfinite(D)) {
+    if (!diverged) {
         for (int r = 0; r < ps; ++r)
             for (int c = 0; c < ps; ++c) {
                 int all = 1;
@@ -320,7 +323,7 @@ void orc_search_patch(const double *L, const double *R, const double *G, int w, 
     }
     for (int i = 0; i < 64; ++i) E[i] = 0.0;
     if (n_common == 0) {
-        flags |= ORC_FLAG_EMPTY;
+        if (!diverged) flags |= ORC_FLAG_EMPTY;
     } else {
         for (int i = 0; i < s; ++i) {
             double di = D + (i - (s - 1) / 2) * p->window_step;

@@ -24,6 +24,10 @@ from .api import (  # noqa: F401
     probe_fp32_tflops,
     set_search_variant,
     get_search_variant,
+    set_search_tiling,
+    get_search_tiling,
+    set_densify_variant,
+    get_densify_variant,
     prepare_level0,
     pyramid_level,
     search_level,

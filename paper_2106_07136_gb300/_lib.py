@@ -20,7 +20,9 @@ EXPORTED = [
     "bdis_prepare_level0", "bdis_pyramid_level", "bdis_search_level", "bdis_densify_level",
     "bdis_upsample", "bdis_enable_timing", "bdis_read_timing", "bdis_pack_right",
     "bdis_match_static", "bdis_probe_fp32_tflops", "bdis_set_search_variant",
-    "bdis_get_search_variant", "bdis_plan_create", "bdis_plan_run", "bdis_plan_info",
+    "bdis_get_search_variant", "bdis_set_search_tiling", "bdis_get_search_tiling",
+    "bdis_set_densify_variant", "bdis_get_densify_variant",
+    "bdis_plan_create", "bdis_plan_run", "bdis_plan_info",
     "bdis_plan_workspace_bytes", "bdis_plan_destroy", "bdis_match_warm", "bdis_warm_map",
     "bdis_net_weight_count", "bdis_net_create", "bdis_net_forward", "bdis_net_gradient",
     "bdis_net_train_step", "bdis_net_get_weights", "bdis_net_destroy", "bdis_match_seeded",
@@ -150,6 +152,11 @@ def load():
     lib.bdis_plan_destroy.restype = None
     lib.bdis_set_search_variant.argtypes = [c_int]
     lib.bdis_get_search_variant.restype = c_int
+    lib.bdis_set_search_tiling.argtypes = [c_int]
+    lib.bdis_set_search_tiling.restype = None
+    lib.bdis_get_search_tiling.restype = c_int
+    lib.bdis_set_densify_variant.argtypes = [c_int]
+    lib.bdis_get_densify_variant.restype = c_int
     lib.bdis_probe_fp32_tflops.argtypes = [c_int, P(ctypes.c_double), c_void_p]
     lib.bdis_match_static.argtypes = [ip, ip, pp, c_void_p, c_void_p]
     lib.bdis_pack_right.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]

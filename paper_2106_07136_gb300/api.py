@@ -240,12 +240,30 @@ def match_static(left: torch.Tensor, right: torch.Tensor, params: BdisParams = N
 
 
 def set_search_variant(columns_per_lane: int):
-    """Lane layout of the fixed-size search kernel: 1 (column per lane) or 2 (wide)."""
+    """Lane layout of the fixed-size search kernel: 1, 2 (default) or 4 columns per lane."""
     check(_lib.load().bdis_set_search_variant(int(columns_per_lane)), "bdis_set_search_variant")
 
 
 def get_search_variant() -> int:
     return int(_lib.load().bdis_get_search_variant())
+
+
+def set_search_tiling(on: bool):
+    """Warp-tiled shared-memory sampling in the fixed-size search kernel (default off)."""
+    _lib.load().bdis_set_search_tiling(1 if on else 0)
+
+
+def get_search_tiling() -> bool:
+    return bool(_lib.load().bdis_get_search_tiling())
+
+
+def set_densify_variant(tile_height: int):
+    """Densify kernel: 0 = strips where they apply (default), 8/16/32 = tiles of that height."""
+    check(_lib.load().bdis_set_densify_variant(int(tile_height)), "bdis_set_densify_variant")
+
+
+def get_densify_variant() -> int:
+    return int(_lib.load().bdis_get_densify_variant())
 
 
 def probe_fp32_tflops(iterations: int = 1 << 16, stream=None) -> float:

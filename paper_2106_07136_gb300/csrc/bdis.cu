@@ -447,10 +447,11 @@ bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t st,
           tune->level[l].search_threads = bt;
         }
       }
-    // densify: tile height (the separable BDIS kernel only)
+    // densify (the separable BDIS kernels): 0 = the strip kernel where it
+    // applies, else a tile height of 8, 16 or 32
     if (p.fusion == BDIS_FUSION_BDIS) {
       best = 1e30f;
-      for (int ty = 8; ty <= 32 && e == cudaSuccess; ty *= 2) {
+      for (int ty = 0; ty <= 32 && e == cudaSuccess; ty = ty ? 2 * ty : 8) {
         DensifyArgs da = level_densify_args(base, lay, p, left.count, l, out);
         da.tile_y = ty;
         const float ms = time_launches(st, e0, e1, reps, [&] { return launch_densify(da, st); }, &e);
@@ -607,6 +608,19 @@ bdis_status bdis_set_search_variant(int columns_per_lane) {
 }
 
 int bdis_get_search_variant(void) { return search_cols_per_lane(); }
+
+void bdis_set_search_tiling(int on) { set_search_tiled(on); }
+
+int bdis_get_search_tiling(void) { return search_tiled(); }
+
+bdis_status bdis_set_densify_variant(int tile_height) {
+  if (tile_height != 0 && tile_height != 8 && tile_height != 16 && tile_height != 32)
+    return BDIS_E_INVALID_ARG;
+  set_densify_tile(tile_height);
+  return BDIS_OK;
+}
+
+int bdis_get_densify_variant(void) { return densify_tile(); }
 
 bdis_status bdis_enable_timing(bdis_handle *h, int on) {
   if (!h) return BDIS_E_INVALID_ARG;

@@ -74,7 +74,7 @@ inline int gamma_min_count(float gamma, int ps) {
 struct LevelTuning {
   int search_cpl = 0;      // fast search path: 1 column per lane, or 2 (wide)
   int search_threads = 0;  // search block size: 64 or 128
-  int densify_tile_y = 0;  // densify tile height: 8, 16 or 32
+  int densify_tile_y = 0;  // densify: 0 = strip kernel (or tiles of 32); 8, 16, 32 = tile height
 };
 struct Tuning {
   LevelTuning level[16];
@@ -113,6 +113,7 @@ struct SearchArgs {
   int nmin_valid, normalize;
   int cols_per_lane;  // fast path: columns of a patch per lane (1, 2, 3 or 4)
   int block_threads;  // 0 = 128
+  int tiled;          // fast path: 1 = warp-tiled shared-memory sampling
   int fusion;         // BDIS_FUSION_*
   float *d_star, *weight;
   float *u_init, *posterior, *energies;
@@ -133,7 +134,7 @@ struct DensifyArgs {
   long long cplane;
   int is_finest;
   int fusion;
-  int tile_y;         // 0 = 32
+  int tile_y;         // 0 = strip kernel where PS / stride is whole, else tiles of 32; > 0 tiles
   const float *L;     // DIS fusion: the level's left plane
   const float2 *R2;   // DIS fusion: the level's packed right plane
   float *out;
@@ -171,6 +172,10 @@ cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, 
 // Columns per lane of the fast search path (1 or the wide variant); tunable.
 int search_cols_per_lane();
 void set_search_cols_per_lane(int cpl);
+int search_tiled();
+void set_search_tiled(int on);
+int densify_tile();
+void set_densify_tile(int tile_height);
 
 // Fill SearchArgs / DensifyArgs geometry from parameters (host).
 void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p);

@@ -125,6 +125,129 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
   }
 }
 
+// Strip variant for patch grids whose stride S divides the patch size PS
+// (M = PS / S covering patch rows per pixel row; overlap 0.75 gives M = 4 for
+// PS 8, 12 and 16). A thread owns one column and a strip of K pixel rows. The
+// pixel rows of group g (rows gS .. gS + S - 1) are covered by the same M
+// regular patch rows g - M + 1 .. g (those in [0, ny - 2]) plus, near the
+// bottom, the last patch row (origin h - PS). Walking down the strip one group
+// at a time adds one regular patch row, so each thread computes the x-weighted
+// sums A_j, B_j of one new patch row per group and keeps the last M in
+// registers; the y-weighted sums then take them in ascending j, as the tiled
+// kernel does, with the same operations, so the two give identical results.
+// No shared memory and no block barriers: each warp's patch reads (19 patches
+// of a row for 32 columns) are L1 broadcasts.
+template <int PS, int S, int K>
+__global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a) {
+  constexpr int M = PS / S;
+  static_assert(M * S == PS && K % S == 0, "strip geometry");
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Y0 = blockIdx.y * K, b = blockIdx.z;
+  if (x >= a.w || Y0 >= a.h) return;
+  // Gaussian mask (Eq. 5) at an offset inside the patch; the same expression
+  // as the tiled kernel's table, so the same values
+  auto mask_at = [&](int q) {
+    const float m = (float)q - (PS - 1) * 0.5f;
+    return expf(-(m * m) / a.two_s2);
+  };
+  float mask[PS];  // indexed with compile-time offsets only (stays in registers)
+#pragma unroll
+  for (int q = 0; q < PS; ++q) mask[q] = mask_at(q);
+  // covering patches of column x: regular ilo .. ihi (<= nx - 2), then the last;
+  // their x weights are fixed for the thread
+  const int ilo = x - PS + 1 <= 0 ? 0 : (x - PS + 1 + S - 1) / S;
+  const int ihi = min(x / S, a.nx - 2);
+  const bool ilast = x >= a.w - PS;
+  float mxr[M + 1];
+#pragma unroll
+  for (int k = 0; k <= M; ++k) {
+    const int q = x - (ilo + k) * S;
+    mxr[k] = (q >= 0 && q < PS) ? mask_at(q) : 0.f;
+  }
+  const float mxl = ilast ? mask_at(x - (a.w - PS)) : 0.f;
+  const float *wp = a.weight + (long long)b * a.np;
+  const float *dp = a.d_star + (long long)b * a.np;
+  // x-weighted sums of patch row j (0 <= j < ny), same order as the tiled kernel
+  auto row_sums = [&](int j, float &A, float &B) {
+    A = 0.f;
+    B = 0.f;
+    const float *wr = wp + (long long)j * a.nx;
+    const float *dr = dp + (long long)j * a.nx;
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {  // at most M regular patches cover x, plus the last
+      const int ii = ilo + k;
+      const bool reg = ii <= ihi;
+      if (!reg && !(ilast && ii == ihi + 1)) continue;
+      const int i = reg ? ii : a.nx - 1;
+      const float wk = __ldg(wr + i);
+      if (wk > 0.f) {
+        const float q2 = wk * (reg ? mxr[k] : mxl);
+        A = fmaf(q2, __ldg(dr + i), A);
+        B += q2;
+      }
+    }
+  };
+  const int ylast = a.h - PS;  // first pixel row the last patch row covers
+  float lastA = 0.f, lastB = 0.f;
+  bool have_last = false;
+  // ring of the regular rows g - M + 1 .. g (slot k holds row g - M + 1 + k)
+  float rA[M], rB[M];
+  const int g0 = Y0 / S;
+#pragma unroll
+  for (int k = 0; k < M - 1; ++k) {
+    const int j = g0 - M + 1 + k;
+    rA[k + 1] = 0.f;
+    rB[k + 1] = 0.f;
+    if (j >= 0 && j <= a.ny - 2) row_sums(j, rA[k + 1], rB[k + 1]);
+  }
+  const long long obase = (long long)b * a.plane + x;
+  const int yend = min(Y0 + K, a.h);
+  for (int g = g0; g * S < yend; ++g) {
+#pragma unroll
+    for (int k = 0; k < M - 1; ++k) {
+      rA[k] = rA[k + 1];
+      rB[k] = rB[k + 1];
+    }
+    rA[M - 1] = 0.f;
+    rB[M - 1] = 0.f;
+    if (g <= a.ny - 2) row_sums(g, rA[M - 1], rB[M - 1]);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int y = g * S + t;
+      if (y >= yend) break;
+      float num = 0.f, den = 0.f;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        const int j = g - M + 1 + k;
+        if (j < 0 || j > a.ny - 2) continue;
+        const float my = mask[t + (M - 1 - k) * S];
+        num = fmaf(my, rA[k], num);
+        den = fmaf(my, rB[k], den);
+      }
+      if (y >= ylast) {
+        if (!have_last) {
+          row_sums(a.ny - 1, lastA, lastB);
+          have_last = true;
+        }
+        const float my = mask_at(y - ylast);
+        num = fmaf(my, lastA, num);
+        den = fmaf(my, lastB, den);
+      }
+      float out;
+      if (den > 0.f)
+        out = num / den;
+      else if (a.is_finest)
+        out = __int_as_float(0x7fc00000);  // NaN: not estimated
+      else if (a.coarse)
+        out = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, x * 0.5f,
+                                     y * 0.5f);
+      else
+        out = 0.f;
+      a.out[obase + (long long)y * a.w] = out;
+    }
+  }
+}
+
 // DIS fusion (Eq. 2): per pixel, every covering patch whose sample x - D*_k is
 // inside the right image, weighted by weight_k / max(r^2, 1) with r the
 // photometric residual R(x - D*_k) - L(x). The weights depend on the pixel
@@ -247,7 +370,15 @@ cudaError_t launch_warm_map(const float *prev, int w, int h, int level, int coun
   return cudaGetLastError();
 }
 
+namespace {
+int g_densify_tile = 0;  // process-wide densify kernel choice (0 = strips where they apply)
+}  // namespace
+
+int densify_tile() { return g_densify_tile; }
+void set_densify_tile(int tile_height) { g_densify_tile = tile_height; }
+
 void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_params &p) {
+  a.tile_y = g_densify_tile;
   a.w = w;
   a.h = h;
   a.plane = (long long)w * h;
@@ -269,6 +400,23 @@ cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
     return cudaGetLastError();
   }
   const int count = (int)(a.total / a.plane);
+  if (a.tile_y == 0 && a.nx > 0 && a.ny > 0) {  // default: strips where the geometry allows
+    constexpr int K = 32;
+    const dim3 sg((unsigned)((a.w + 127) / 128), (unsigned)((a.h + K - 1) / K), (unsigned)count);
+    if (a.ps == 8 && a.stride == 2) {
+      densify_strip_kernel<8, 2, K><<<sg, 128, 0, st>>>(a);
+      return cudaGetLastError();
+    }
+    if (a.ps == 12 && a.stride == 3) {
+      densify_strip_kernel<12, 3, K - 2><<<dim3(sg.x, (unsigned)((a.h + K - 3) / (K - 2)), sg.z),
+                                            128, 0, st>>>(a);
+      return cudaGetLastError();
+    }
+    if (a.ps == 16 && a.stride == 4) {
+      densify_strip_kernel<16, 4, K><<<sg, 128, 0, st>>>(a);
+      return cudaGetLastError();
+    }
+  }
   const int tile_y = a.tile_y > 0 ? a.tile_y : kTileY;
   const dim3 grid((unsigned)((a.w + kTileX - 1) / kTileX), (unsigned)((a.h + tile_y - 1) / tile_y),
                   (unsigned)count);

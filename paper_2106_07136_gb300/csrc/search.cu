@@ -105,7 +105,7 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
   if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
   float post = 0.f;
   if (nc == 0) {
-    flags |= kFlagEmpty;
+    if (!(flags & kFlagDiverged)) flags |= kFlagEmpty;  // a diverged patch reads no window
   } else {
     post = expf(-(Ec - Emin) / a.kappa) / z;
     if (a.s > 1 && Eo < Ec - kSaddleTau * fmaxf(Ec, 1.f)) flags |= kFlagSaddle;
@@ -156,31 +156,37 @@ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 
 // Patch size PS and a 5-sample window 0.5 px apart fixed at compile time.
 // Each lane owns CPL adjacent columns of its patch (G lanes per patch), so the
 // per-step work that does not scale with pixels (sample split, validity vote,
-// reductions, the update) is shared by CPL * PS pixels. Pairs are on
-// blockIdx.y, patches of a pair on blockIdx.x.
-template <int PS, int CPL, int MINB>
-__global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArgs a) {
+// reductions, the update) is shared by CPL * PS pixels.
+//
+// The right rows y0 .. y0 + PS - 1 are read through `Rows`: the packed plane
+// in global memory (runtime row pitch), or a warp's staged copy in shared
+// memory (row pitch fixed at compile time, so every sample is one shared load
+// at an immediate offset from its column).
+struct GlobalRows {
+  const float2 *row0;  // row y0 of the packed right plane
+  int w;
+  __device__ __forceinline__ const float2 *col(int x) const { return row0 + x; }
+  __device__ __forceinline__ float2 ld(const float2 *p, int r) const {
+    return __ldg(p + (size_t)r * w);
+  }
+};
+
+template <int TW>
+struct TileRows {
+  const float2 *tile;  // shared: PS rows of TW pairs, first column `lo`
+  int lo;
+  __device__ __forceinline__ const float2 *col(int x) const { return tile + (x - lo); }
+  __device__ __forceinline__ float2 ld(const float2 *p, int r) const { return p[r * TW]; }
+};
+
+template <int PS, int CPL, class Rows>
+__device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &rows, long long k,
+                                            bool live, int c, unsigned gbits, int b, int x0,
+                                            int y0, float u0) {
   constexpr int LANES = (PS + CPL - 1) / CPL;
   constexpr int G = pow2_at_least(LANES);
   constexpr int S = 5, HALF = 2;
-  static_assert(G <= 32, "group size");
-  const int lane = threadIdx.x & 31;
-  const int c = lane & (G - 1);
-  const unsigned gbits = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
-  const int kk = blockIdx.x * (blockDim.x / G) + (int)(threadIdx.x / G);
-  const bool live = kk < a.np;
-  const int kp = live ? kk : a.np - 1;  // past the end: redo the last patch, store nothing
-  const int b = blockIdx.y;
-  const long long k = (long long)b * a.np + kp;
-  const int pj = kp / a.nx, pi = kp - pj * a.nx;
-  const int w = a.w, x0 = grid_origin(pi, a.nx, w, PS, a.stride);
-  const int y0 = grid_origin(pj, a.ny, a.h, PS, a.stride);
-  float u0 = 0.f;
-  if (a.coarse) {
-    const float cx = (float)x0 + (PS - 1) * 0.5f, cy = (float)y0 + (PS - 1) * 0.5f;
-    u0 = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, cx * 0.5f,
-                                cy * 0.5f);
-  }
+  const int w = a.w;
   const int xl = x0 + c * CPL;  // first column of this lane
   bool act[CPL];
 #pragma unroll
@@ -188,13 +194,9 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   const long long poff = (long long)b * a.plane + (long long)y0 * w;
   const float *Lc = a.L + poff + xl;
   const float *Gc = a.G + poff + xl;
-  const float2 *R2 = a.R2 + poff;  // row y0 of the packed right plane
 
-  float T[CPL][PS];
-#pragma unroll
-  for (int j = 0; j < CPL; ++j)
-#pragma unroll
-    for (int r = 0; r < PS; ++r) T[j][r] = act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f;
+  // The template T (the lane's left columns) is read where it is used: in the
+  // sums of a new valid run and in the window, not held through the steps.
 
   // ---- inverse-search iterations (Eq. 1)
   float D = u0, last_step = 0.f;
@@ -245,7 +247,7 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
           const float q = v[j] ? g[j][r] - mg : 0.f;
           if (need) gc[j][r] = q;
           hh = fmaf(q, q, hh);
-          ct = fmaf(q, T[j][r], ct);
+          ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
         }
       hh = group_sum<G>(hh);
       ct = group_sum<G>(ct);
@@ -268,10 +270,10 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
         if (v[j]) {
-          const float2 *p = R2 + ib + j;
+          const auto p = rows.col(ib + j);
 #pragma unroll
           for (int r = 0; r < PS; ++r)
-            acc[r & 3] = fmaf(gc[j][r], lerp_packed(__ldg(p + (size_t)r * w), t), acc[r & 3]);
+            acc[r & 3] = fmaf(gc[j][r], lerp_packed(rows.ld(p, r), t), acc[r & 3]);
         }
       }
     }
@@ -288,6 +290,8 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
 
   // ---- Bayesian window (Eqs. 3-4): samples at D* + {-1, -0.5, 0, 0.5, 1}
   const bool fin = isfinite(D);
+  // a patch that left its search range is dropped (R8) and reads no window
+  const bool inr = fin && fabsf(D - u0) <= (float)PS;
   int kd;
   float t;
   split_disp(D, kd, t);
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
     nv_lane += (act[j] && fin && sample_ok(ib + j, t, w)) ? 1 : 0;
-    vc[j] = act[j] && fin && (ib + j >= 1) && sample_ok(ib + j + 1, t, w);
+    vc[j] = act[j] && inr && (ib + j >= 1) && sample_ok(ib + j + 1, t, w);
     nc_lane += vc[j] ? 1 : 0;
   }
   const int nvalid = PS * (int)group_sum<G>((float)nv_lane);
@@ -315,10 +319,15 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   // shift cs[j] (the column's first-row residual at D*), which removes the
   // brightness offset between the views; the group then merges the shifted
   // sums exactly: sum (d - md)^2 = S2 - 2 (md - cs) S1 + n (md - cs)^2.
+  float T[CPL][PS];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j)
+#pragma unroll
+    for (int r = 0; r < PS; ++r) T[j][r] = act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f;
   float cs[CPL];
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    cs[j] = vc[j] ? lerp_packed(__ldg(R2 + ib + j), t) - T[j][0] : 0.f;
+    cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) - T[j][0] : 0.f;
 #pragma unroll
     for (int r = 0; r < PS; ++r) T[j][r] += cs[j];  // the window works on T + shift
   }
@@ -332,10 +341,10 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
       // two partial sums per quantity (even / odd rows) shorten the chains
       float s1a = 0.f, s1b = 0.f, s2a = 0.f, s2b = 0.f;
       if (vc[j]) {
-        const float2 *p = R2 + ib + j + off[i];
+        const auto p = rows.col(ib + j + off[i]);
 #pragma unroll
         for (int r = 0; r < PS; ++r) {
-          const float d = lerp_packed(__ldg(p + (size_t)r * w), tt[i]) - T[j][r];
+          const float d = lerp_packed(rows.ld(p, r), tt[i]) - T[j][r];
           if (r & 1) {
             s1b += d;
             s2b = fmaf(d, d, s2b);
@@ -375,6 +384,104 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   for (int i = 0; i < S; ++i) z += expf(-(E[i] - Emin) / a.kappa);
   finish_patch(a, k, write, D, u0, last_step, flat, steps, nvalid, nc, E[HALF], Eo, Emin, z,
                PS);
+}
+
+// One patch per group, pairs on blockIdx.y, patches of a pair on blockIdx.x;
+// samples read from global memory (through L1).
+template <int PS, int CPL, int MINB>
+__global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArgs a) {
+  constexpr int LANES = (PS + CPL - 1) / CPL;
+  constexpr int G = pow2_at_least(LANES);
+  static_assert(G <= 32, "group size");
+  const int lane = threadIdx.x & 31;
+  const int c = lane & (G - 1);
+  const unsigned gbits = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int kk = blockIdx.x * (blockDim.x / G) + (int)(threadIdx.x / G);
+  const bool live = kk < a.np;
+  const int kp = live ? kk : a.np - 1;  // past the end: redo the last patch, store nothing
+  const int b = blockIdx.y;
+  const long long k = (long long)b * a.np + kp;
+  const int pj = kp / a.nx, pi = kp - pj * a.nx;
+  const int w = a.w, x0 = grid_origin(pi, a.nx, w, PS, a.stride);
+  const int y0 = grid_origin(pj, a.ny, a.h, PS, a.stride);
+  float u0 = 0.f;
+  if (a.coarse) {
+    const float cx = (float)x0 + (PS - 1) * 0.5f, cy = (float)y0 + (PS - 1) * 0.5f;
+    u0 = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, cx * 0.5f,
+                                cy * 0.5f);
+  }
+  fixed_patch<PS, CPL>(a, GlobalRows{a.R2 + (long long)b * a.plane + (long long)y0 * w, w}, k,
+                      live, c, gbits, b, x0, y0, u0);
+}
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// Warp-tiled variant: a warp takes 32 / G consecutive patches of one patch-grid
+// row, so they share rows y0 .. y0 + PS - 1. While a patch stays in its search
+// range (|D - u0| <= PS, window +-1 px) it reads columns
+// [x0 + floor(-u0 - PS) - 1, x0 + PS + floor(-u0 + PS)]; the warp stages the
+// union of its patches' ranges (with one more column each side for rounding
+// of the range test) into shared memory and samples from there. A warp whose
+// starts spread too far for TW columns reads global memory instead; results
+// are identical either way (same arithmetic in the same order). Measured on
+// GB300 it is the slower choice at patch size 8 (2 columns per lane: 6.2 vs
+// 5.4 ms of search per 128 pairs): the staging pass and its extra dependent
+// DRAM round trip cost more than the row-address arithmetic that the
+// immediate shared offsets save, so it is off by default.
+template <int PS, int CPL, int MINB, int TW>
+__global__ void __launch_bounds__(128, MINB) search_tiled_kernel(const SearchArgs a) {
+  constexpr int LANES = (PS + CPL - 1) / CPL;
+  constexpr int G = pow2_at_least(LANES);
+  constexpr int P = 32 / G;  // patches per warp
+  static_assert(G <= 32 && 32 % G == 0, "group size");
+  __shared__ float2 tiles[4][PS * TW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = lane & (G - 1);
+  const unsigned gbits = (G == 32) ? kFull : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int chunks = (a.nx + P - 1) / P;
+  const int wid = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (wid >= a.ny * chunks) return;  // whole warps only
+  const int pj = wid / chunks, q = wid - pj * chunks;
+  const int pi_raw = q * P + lane / G;
+  const bool live = pi_raw < a.nx;
+  const int pi = live ? pi_raw : a.nx - 1;  // past the row end: redo its last patch, store nothing
+  const int b = blockIdx.y;
+  const long long k = (long long)b * a.np + (long long)pj * a.nx + pi;
+  const int w = a.w, x0 = grid_origin(pi, a.nx, w, PS, a.stride);
+  const int y0 = grid_origin(pj, a.ny, a.h, PS, a.stride);
+  float u0 = 0.f;
+  if (a.coarse) {
+    const float cx = (float)x0 + (PS - 1) * 0.5f, cy = (float)y0 + (PS - 1) * 0.5f;
+    u0 = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, cx * 0.5f,
+                                cy * 0.5f);
+  }
+  const float2 *row0 = a.R2 + (long long)b * a.plane + (long long)y0 * w;
+  const bool bounded = fabsf(u0) < 1.0e6f;  // false for NaN
+  int lo = bounded ? x0 + (int)floorf(-u0 - (float)PS) - 3 : 0;
+  int hi = bounded ? x0 + PS + (int)floorf(-u0 + (float)PS) + 2 : 0;
+  lo = warp_min(lo);
+  hi = warp_max(hi);
+  if (__all_sync(kFull, bounded) && hi - lo < TW) {
+    float2 *tile = tiles[warp];
+    for (int i = lane; i < PS * TW; i += 32) {
+      const int r = i / TW, x = lo + (i - r * TW);
+      tile[i] = (x >= 0 && x < w) ? __ldg(row0 + (size_t)r * w + x) : make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    fixed_patch<PS, CPL>(a, TileRows<TW>{tile, lo}, k, live, c, gbits, b, x0, y0, u0);
+  } else {
+    fixed_patch<PS, CPL>(a, GlobalRows{row0, w}, k, live, c, gbits, b, x0, y0, u0);
+  }
 }
 
 // ---------------------------------------------------------- generic path
@@ -476,7 +583,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
     return;
   }
   const int half = (a.s - 1) / 2;
-  bool vc = act && fin;
+  bool vc = act && fin && fabsf(D - u0) <= (float)ps;  // a diverged patch reads no window
   for (int i = 0; i < a.s; ++i) {
     split_disp(D + (float)(i - half) * a.step, kd, t);
     vc = vc && sample_ok(x + kd, t, w);
@@ -533,6 +640,23 @@ cudaError_t launch_fixed(const SearchArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int PS, int CPL, int MINB>
+cudaError_t launch_tiled(const SearchArgs &a, cudaStream_t st) {
+  constexpr int G = pow2_at_least((PS + CPL - 1) / CPL), P = 32 / G;
+  constexpr int TW = (PS == 8 && CPL <= 2) ? 64 : 96;  // 4 warps x PS x TW x 8 B <= 48 KB
+  const int threads = a.block_threads == 64 ? 64 : 128, wpb = threads / 32;
+  const long long warps = (long long)a.ny * ((a.nx + P - 1) / P);
+  const int count = (int)(a.total / a.np);
+  const dim3 grid((unsigned)((warps + wpb - 1) / wpb), (unsigned)count);
+  search_tiled_kernel<PS, CPL, MINB, TW><<<grid, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int PS, int CPL, int MINB>
+cudaError_t launch_fast(const SearchArgs &a, cudaStream_t st) {
+  return a.tiled ? launch_tiled<PS, CPL, MINB>(a, st) : launch_fixed<PS, CPL, MINB>(a, st);
+}
+
 template <typename K>
 cudaError_t launch_groups(K kernel, int G, const SearchArgs &a, cudaStream_t st) {  // 1-D grid
   const int threads = 128;
@@ -574,10 +698,13 @@ cudaError_t launch_select_start(float *d_a, float *w_a, const float *p_a, const 
 
 namespace {
 int g_cols_per_lane = 2;  // process-wide choice of the fast-path variant
+int g_tiled = 0;          // fast path: warp-tiled shared-memory sampling (off: slower)
 }  // namespace
 
 int search_cols_per_lane() { return g_cols_per_lane; }
 void set_search_cols_per_lane(int cpl) { g_cols_per_lane = cpl; }
+int search_tiled() { return g_tiled; }
+void set_search_tiled(int on) { g_tiled = on ? 1 : 0; }
 
 void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p) {
   a.w = w;
@@ -596,6 +723,7 @@ void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params 
   a.nmin_valid = gamma_min_count(p.gamma, p.patch_size);
   a.normalize = p.normalize ? 1 : 0;
   a.cols_per_lane = search_cols_per_lane();
+  a.tiled = search_tiled();
   a.fusion = p.fusion;
 }
 
@@ -605,12 +733,12 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
   if (a.s == 5 && a.step == 0.5f && count <= 65535) {
     const int cpl = a.cols_per_lane;
     if (a.ps == 8) {
-      if (cpl == 1) return launch_fixed<8, 1, 8>(a, st);
-      if (cpl == 4) return launch_fixed<8, 4, 4>(a, st);
-      return launch_fixed<8, 2, 6>(a, st);
+      if (cpl == 1) return launch_fast<8, 1, 8>(a, st);
+      if (cpl == 4) return launch_fast<8, 4, 4>(a, st);
+      return launch_fast<8, 2, 8>(a, st);  // 64 registers: 8 blocks of 128 per SM
     }
-    if (a.ps == 12) return cpl == 1 ? launch_fixed<12, 1, 4>(a, st) : launch_fixed<12, 3, 3>(a, st);
-    if (a.ps == 16) return cpl == 1 ? launch_fixed<16, 1, 4>(a, st) : launch_fixed<16, 2, 3>(a, st);
+    if (a.ps == 12) return cpl == 1 ? launch_fast<12, 1, 4>(a, st) : launch_fast<12, 3, 3>(a, st);
+    if (a.ps == 16) return cpl == 1 ? launch_fast<16, 1, 4>(a, st) : launch_fast<16, 2, 3>(a, st);
   }
   if (a.ps <= 4) return launch_groups(search_generic_kernel<4>, 4, a, st);
   if (a.ps <= 8) return launch_groups(search_generic_kernel<8>, 8, a, st);

@@ -586,6 +586,23 @@ def test_update_count_and_early_stop(orc):
         assert abs(at_k1.d_star - at_k2.d_star) >= 1e-4
 
 
+def test_diverged_patch_reads_no_window(orc):
+    """R8: a patch that leaves its search range (|D - u0| > patch size) is
+    dropped as diverged; its window is not evaluated, so its posterior is 0
+    and it carries no saddle or empty bit. A start 12 px off the true shift
+    on a pair whose patches cannot lock on sends most patches away."""
+    pair = synth.make_integer_shift_pair(48, 96, 20)
+    p = small_params(orc, coarsest_scale=1, gamma=0.25)
+    L, R = np.asarray(pair.left, np.float64), np.asarray(pair.right, np.float64)
+    G = orc.sobel_x(L)
+    res = orc.search_level(L, R, G, np.full((24, 48), 16.0), p)
+    div = (res["flags"] & 2) != 0
+    assert div.sum() > 0
+    assert np.all(res["posterior"][div] == 0.0) and np.all(res["weight"][div] == 0.0)
+    assert np.all((res["flags"][div] & (4 | 16)) == 0)
+    assert np.all(res["energies"][div] == 0.0)
+
+
 def test_zero_iterations_take_no_update(orc):
     pair = synth.make_cfg1()
     p = small_params(orc, iterations=0)

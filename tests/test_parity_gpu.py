@@ -136,6 +136,13 @@ def search_variant(request):
     bd.set_search_variant(old)
 
 
+@pytest.fixture
+def search_variant_reset():
+    old = bd.get_search_variant()
+    yield
+    bd.set_search_variant(old)
+
+
 @pytest.mark.parametrize("search_variant", [1, 2, 4], indirect=True)
 @pytest.mark.parametrize("ps", [8, 12, 16])
 def test_search_stage_cfg2(orc, cfg2, ps, search_variant):
@@ -149,6 +156,40 @@ def test_search_stage_cfg2(orc, cfg2, ps, search_variant):
                                                                       coarsest_scale=1)])
 def test_search_stage_variants(orc, cfg1, kw):
     _search_stage(orc, cfg1, dict(CFG1, **kw), levels=[min(kw.get("coarsest_scale", 2), 1), 0])
+
+
+@pytest.fixture
+def tiling(request):
+    old = bd.get_search_tiling()
+    yield
+    bd.set_search_tiling(old)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 4])
+@pytest.mark.parametrize("ps", [8, 12, 16])
+@pytest.mark.parametrize("jumps", [False, True])
+def test_tiled_search_is_bit_identical(orc, cfg2, ps, variant, jumps, tiling, search_variant_reset):
+    """The warp-tiled kernel (right rows staged in shared memory) and the
+    untiled one give identical outputs, debug outputs included. With `jumps`
+    the start map gets +-30 px steps every 5 columns, so many warps' starts
+    spread beyond their tile and those warps read global memory instead."""
+    gp, op = params(orc, **dict(CFG2, patch_size=ps))
+    st = orc.match_stages(cfg2.left, cfg2.right, op)
+    bd.set_search_variant(variant)
+    for lvl in (2, 0):
+        o = st["levels"][lvl]
+        coarse = o["coarse"].copy()
+        if jumps:
+            coarse[:, ::5] += 30.0
+            coarse[:, 2::5] -= 30.0
+        args = (dev(o["L"]), bd.pack_right(dev(o["R"])), dev(o["G"]), dev(coarse), gp)
+        outs = []
+        for on in (True, False):
+            bd.set_search_tiling(on)
+            outs.append({k: host(v) for k, v in bd.search_level(*args).items()})
+        for key in outs[0]:
+            a, b = outs[0][key], outs[1][key]
+            assert np.array_equal(a, b, equal_nan=a.dtype.kind == "f"), (lvl, key)
 
 
 # ----------------------------------------------------------------- densify
@@ -167,6 +208,35 @@ def test_densify_stage(orc, cfg1, lvl, finest):
                                 finest))[0]
     assert np.array_equal(np.isnan(out), np.isnan(ref))
     np.testing.assert_allclose(out[~np.isnan(ref)], ref[~np.isnan(ref)], atol=DENSE_ATOL)
+
+
+@pytest.mark.parametrize("ps,overlap", [(8, 0.75), (12, 0.75), (16, 0.75), (5, 0.4)])
+@pytest.mark.parametrize("shape", [(480, 640), (61, 97), (97, 61)])
+@pytest.mark.parametrize("finest", [False, True])
+def test_densify_strip_matches_tiles(ps, overlap, shape, finest):
+    """The strip densify kernel (default where the stride divides the patch
+    size) and the tiled one give identical maps, carried pixels included."""
+    h, w = shape
+    kw = dict(patch_size=ps, overlap=overlap)
+    gp = bd.default_params(**kw)
+    s, nx = bd.grid(w, ps, overlap)
+    _, ny = bd.grid(h, ps, overlap)
+    rng = np.random.default_rng(ps * 1000 + h)
+    weight = rng.uniform(0, 1, (2, ny, nx)).astype(np.float32)
+    weight[rng.uniform(size=weight.shape) < 0.4] = 0.0
+    d_star = rng.uniform(-3, 40, (2, ny, nx)).astype(np.float32)
+    coarse = rng.uniform(0, 20, (2, (h + 1) // 2, (w + 1) // 2)).astype(np.float32)
+    outs = []
+    old = bd.get_densify_variant()
+    try:
+        for tile in (0, 32, 8):
+            bd.set_densify_variant(tile)
+            outs.append(host(bd.densify_level((h, w), gp, dev(d_star), dev(weight), dev(coarse),
+                                              finest)))
+    finally:
+        bd.set_densify_variant(old)
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o, equal_nan=True)
 
 
 def test_upsample_stage(orc):
