@@ -322,6 +322,13 @@ int bdis_get_search_tiling(void);
 bdis_status bdis_set_densify_variant(int tile_height);
 int bdis_get_densify_variant(void);
 
+/* Tuning: the pyramid step. 1 (default) = one fused kernel per level
+ * (downsample into shared memory, then L, packed R and the gradient written
+ * once); 0 = a downsample kernel, then a gradient-and-packing kernel over
+ * the new level. Results are identical. Process-wide. */
+void bdis_set_pyramid_variant(int fused);
+int bdis_get_pyramid_variant(void);
+
 /* Measurement utility, not part of the method: FP32 FMA throughput of the
  * current device in TFLOP/s (the roofline denominator of the inverse search).
  * Runs two launches of an FMA-chain kernel of `iterations` steps per chain on

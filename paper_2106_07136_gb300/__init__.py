@@ -28,6 +28,8 @@ from .api import (  # noqa: F401
     get_search_tiling,
     set_densify_variant,
     get_densify_variant,
+    set_pyramid_variant,
+    get_pyramid_variant,
     prepare_level0,
     pyramid_level,
     search_level,

@@ -266,6 +266,15 @@ def get_densify_variant() -> int:
     return int(_lib.load().bdis_get_densify_variant())
 
 
+def set_pyramid_variant(fused: bool):
+    """Pyramid step: one fused kernel per level (default) or downsample, then gradient."""
+    _lib.load().bdis_set_pyramid_variant(1 if fused else 0)
+
+
+def get_pyramid_variant() -> bool:
+    return bool(_lib.load().bdis_get_pyramid_variant())
+
+
 def probe_fp32_tflops(iterations: int = 1 << 16, stream=None) -> float:
     """Measured FP32 FMA throughput of the current GPU (TFLOP/s)."""
     t = ctypes.c_double()

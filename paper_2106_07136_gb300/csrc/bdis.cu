@@ -622,6 +622,10 @@ bdis_status bdis_set_densify_variant(int tile_height) {
 
 int bdis_get_densify_variant(void) { return densify_tile(); }
 
+void bdis_set_pyramid_variant(int fused) { set_pyramid_fused(fused); }
+
+int bdis_get_pyramid_variant(void) { return pyramid_fused(); }
+
 bdis_status bdis_enable_timing(bdis_handle *h, int on) {
   if (!h) return BDIS_E_INVALID_ARG;
   h->timing = on != 0;

@@ -176,6 +176,8 @@ int search_tiled();
 void set_search_tiled(int on);
 int densify_tile();
 void set_densify_tile(int tile_height);
+int pyramid_fused();
+void set_pyramid_fused(int on);
 
 // Fill SearchArgs / DensifyArgs geometry from parameters (host).
 void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p);

@@ -167,22 +167,29 @@ __global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a)
   const float mxl = ilast ? mask_at(x - (a.w - PS)) : 0.f;
   const float *wp = a.weight + (long long)b * a.np;
   const float *dp = a.d_star + (long long)b * a.np;
-  // x-weighted sums of patch row j (0 <= j < ny), same order as the tiled kernel
+  // x-weighted sums of patch row j (0 <= j < ny), same order as the tiled
+  // kernel; all of the row's loads are issued before any is used
   auto row_sums = [&](int j, float &A, float &B) {
-    A = 0.f;
-    B = 0.f;
     const float *wr = wp + (long long)j * a.nx;
     const float *dr = dp + (long long)j * a.nx;
+    float wv[M + 1], dv[M + 1];
+    bool use[M + 1];
 #pragma unroll
     for (int k = 0; k <= M; ++k) {  // at most M regular patches cover x, plus the last
       const int ii = ilo + k;
       const bool reg = ii <= ihi;
-      if (!reg && !(ilast && ii == ihi + 1)) continue;
+      use[k] = reg || (ilast && ii == ihi + 1);
       const int i = reg ? ii : a.nx - 1;
-      const float wk = __ldg(wr + i);
-      if (wk > 0.f) {
-        const float q2 = wk * (reg ? mxr[k] : mxl);
-        A = fmaf(q2, __ldg(dr + i), A);
+      wv[k] = use[k] ? __ldg(wr + i) : 0.f;
+      dv[k] = use[k] ? __ldg(dr + i) : 0.f;
+    }
+    A = 0.f;
+    B = 0.f;
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      if (use[k] && wv[k] > 0.f) {
+        const float q2 = wv[k] * (ilo + k <= ihi ? mxr[k] : mxl);
+        A = fmaf(q2, dv[k], A);
         B += q2;
       }
     }

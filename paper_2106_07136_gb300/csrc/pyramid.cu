@@ -110,6 +110,135 @@ __global__ void sobel_pack_kernel(const float *__restrict__ L, float2 *__restric
   Rb[x].y = x + 1 < w ? Rb[x + 1].x - Rb[x].x : 0.f;
 }
 
+// Level 0 from 8-bit views, four pixels per thread (width, pitch and image
+// stride multiples of 4): one 32-bit load per row segment plus the two
+// reflected neighbour bytes, float4 stores. Row and pair come from the grid,
+// so there is no per-pixel index division. Same values as the scalar kernel.
+__global__ void __launch_bounds__(128) prepare_level0_x4_kernel(
+    const uint8_t *__restrict__ left, const uint8_t *__restrict__ right, size_t pitch,
+    size_t stride, int w, int h, float *__restrict__ L0, float2 *__restrict__ R0,
+    float *__restrict__ G0) {
+  const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y, b = blockIdx.z;
+  if (x >= w) return;
+  const uint8_t *lb = left + (size_t)b * stride;
+  const uint8_t *rb = right + (size_t)b * stride;
+  const int xm = reflect101(x - 1, w), xq = reflect101(x + 4, w);
+  // v[0] = column x - 1 (reflected), v[1..4] = x .. x + 3, v[5] = x + 4 (reflected)
+  auto row6 = [&](const uint8_t *row, float v[6]) {
+    const uint32_t wd = __ldg(reinterpret_cast<const unsigned int *>(row + x));
+    v[0] = (float)__ldg(row + xm);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[1 + i] = (float)((wd >> (8 * i)) & 0xffu);
+    v[5] = (float)__ldg(row + xq);
+  };
+  float lm[6], l0[6], lp[6], r[6];
+  row6(lb + (size_t)reflect101(y - 1, h) * pitch, lm);
+  row6(lb + (size_t)y * pitch, l0);
+  row6(lb + (size_t)reflect101(y + 1, h) * pitch, lp);
+  row6(rb + (size_t)y * pitch, r);
+  const size_t o = (size_t)b * w * h + (size_t)y * w + x;
+  float g[4], rd[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float dm = lm[i + 2] - lm[i];
+    const float d0 = l0[i + 2] - l0[i];
+    const float dp = lp[i + 2] - lp[i];
+    g[i] = (dm + 2.f * d0 + dp) * 0.125f;
+    rd[i] = x + i + 1 < w ? r[i + 2] - r[i + 1] : 0.f;
+  }
+  *reinterpret_cast<float4 *>(L0 + o) = make_float4(l0[1], l0[2], l0[3], l0[4]);
+  *reinterpret_cast<float4 *>(G0 + o) = make_float4(g[0], g[1], g[2], g[3]);
+  float4 *r4 = reinterpret_cast<float4 *>(R0 + o);
+  r4[0] = make_float4(r[1], rd[0], r[2], rd[1]);
+  r4[1] = make_float4(r[3], rd[2], r[4], rd[3]);
+}
+
+// One pyramid step fused with the gradient and packing of the new level. A
+// block owns a 32 x 16 output tile and computes it plus a one-pixel halo. The
+// input rows and columns the tile needs are staged in shared memory once:
+// stage row r holds input row reflect101(2 Y0 - 4 + r), stage column c input
+// column reflect101(2 X0 - 4 + c). A horizontal 5-tap pass per stage row and
+// computed column, then a vertical 5-tap pass per computed output, give the
+// binomial downsample. A halo cell is evaluated at its reflected coordinate,
+// so it holds exactly the neighbour that reflect-101 asks for; every tap
+// reads the same input element, in the same order, as down_kernel. Then L1,
+// the packed R1 and Sobel-x / 8 of L1 are written once (as sobel_pack_kernel).
+constexpr int kPyrX = 32, kPyrY = 16;
+constexpr int kStX = 2 * kPyrX + 7, kStY = 2 * kPyrY + 7;  // staged input columns / rows
+
+__global__ void __launch_bounds__(256) pyramid_fused_kernel(
+    const float *__restrict__ L, const float2 *__restrict__ R, int w, int h, int dw, int dh,
+    float *__restrict__ L1, float2 *__restrict__ R1, float *__restrict__ G1) {
+  __shared__ float inL[kStY][kStX], inR[kStY][kStX];
+  __shared__ float hL[kStY][kPyrX + 2], hR[kStY][kPyrX + 2];
+  __shared__ float sL[kPyrY + 2][kPyrX + 2], sR[kPyrY + 2][kPyrX + 2];
+  const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
+  const int tid = threadIdx.x;
+  const float *Lb = L + (long long)b * w * h;
+  const float2 *Rb = R + (long long)b * w * h;
+  const float k[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
+  // stage rows needed: those of computed rows Y0 - 1 .. min(Y0 + kPyrY, dh)
+  // (reflected). Asynchronous 4-byte copies: every copy of the thread is in
+  // flight before the one wait (the value of R is the first word of its pair).
+  for (int q = tid; q < kStY * kStX; q += blockDim.x) {
+    const int r = q / kStX, c = q - r * kStX;
+    const int yi = 2 * Y0 - 4 + r, xi = 2 * X0 - 4 + c;
+    if (yi > h + 1 || xi > w + 1) continue;  // past the last reflected tap: never read
+    const size_t off = (size_t)reflect101(yi, h) * w + reflect101(xi, w);
+    const unsigned dl = (unsigned)__cvta_generic_to_shared(&inL[r][c]);
+    const unsigned dr = (unsigned)__cvta_generic_to_shared(&inR[r][c]);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dl), "l"(Lb + off));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr), "l"(Rb + off));
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  // horizontal taps of every stage row at every computed column
+  for (int q = tid; q < kStY * (kPyrX + 2); q += blockDim.x) {
+    const int r = q / (kPyrX + 2), cx = q - r * (kPyrX + 2);
+    const int Xr = X0 - 1 + cx;
+    if (Xr > dw || 2 * Y0 - 4 + r > h + 1) continue;
+    const int c0 = 2 * (reflect101(Xr, dw) - X0) + 2;  // stage column of tap 0
+    float hl = 0.f, hr = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      hl = fmaf(k[i], inL[r][c0 + i], hl);
+      hr = fmaf(k[i], inR[r][c0 + i], hr);
+    }
+    hL[r][cx] = hl;
+    hR[r][cx] = hr;
+  }
+  __syncthreads();
+  // vertical taps: the downsampled value of every computed cell
+  for (int q = tid; q < (kPyrY + 2) * (kPyrX + 2); q += blockDim.x) {
+    const int cy = q / (kPyrX + 2), cx = q - cy * (kPyrX + 2);
+    const int Xr = X0 - 1 + cx, Yr = Y0 - 1 + cy;
+    if (Xr > dw || Yr > dh) continue;
+    const int r0 = 2 * (reflect101(Yr, dh) - Y0) + 2;  // stage row of tap 0
+    float accL = 0.f, accR = 0.f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      accL = fmaf(k[j], hL[r0 + j][cx], accL);
+      accR = fmaf(k[j], hR[r0 + j][cx], accR);
+    }
+    sL[cy][cx] = accL;
+    sR[cy][cx] = accR;
+  }
+  __syncthreads();
+  const int cx = 1 + (tid & (kPyrX - 1));
+  for (int cy = 1 + tid / kPyrX; cy <= kPyrY; cy += blockDim.x / kPyrX) {
+    const int X = X0 + cx - 1, Y = Y0 + cy - 1;
+    if (X >= dw || Y >= dh) continue;
+    const float dm = sL[cy - 1][cx + 1] - sL[cy - 1][cx - 1];
+    const float d0 = sL[cy][cx + 1] - sL[cy][cx - 1];
+    const float dp = sL[cy + 1][cx + 1] - sL[cy + 1][cx - 1];
+    const size_t o = (size_t)b * dw * dh + (size_t)Y * dw + X;
+    L1[o] = sL[cy][cx];
+    G1[o] = (dm + 2.f * d0 + dp) * 0.125f;
+    R1[o] = make_float2(sR[cy][cx], X + 1 < dw ? sR[cy][cx + 1] - sR[cy][cx] : 0.f);
+  }
+}
+
 __global__ void pack_right_kernel(const float *__restrict__ R, int w, long long total,
                                   float2 *__restrict__ R2) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -119,11 +248,17 @@ __global__ void pack_right_kernel(const float *__restrict__ R, int w, long long 
   R2[idx] = make_float2(r, x + 1 < w ? R[idx + 1] - r : 0.f);
 }
 
+
 inline unsigned blocks_for(long long n, int threads) {
   return (unsigned)((n + threads - 1) / threads);
 }
 
+int g_pyramid_fused = 1;  // one fused kernel per pyramid level (0: downsample, then gradient)
+
 }  // namespace
+
+int pyramid_fused() { return g_pyramid_fused; }
+void set_pyramid_fused(int on) { g_pyramid_fused = on ? 1 : 0; }
 
 cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &right, float *L0,
                                   float2 *R0, float *G0, cudaStream_t st) {
@@ -131,6 +266,21 @@ cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &righ
   if (total == 0) return cudaSuccess;
   const int threads = 256;
   const size_t stride = left.count > 1 ? left.image_stride_bytes : 0;
+  const bool aligned4 = left.width % 4 == 0 && left.pitch_bytes % 4 == 0 && stride % 4 == 0 &&
+                        right.pitch_bytes == left.pitch_bytes &&
+                        (reinterpret_cast<uintptr_t>(left.data) & 3) == 0 &&
+                        (reinterpret_cast<uintptr_t>(right.data) & 3) == 0;
+  if (left.format == BDIS_U8 && aligned4 && left.height >= 2 &&
+      (reinterpret_cast<uintptr_t>(L0) & 15) == 0 && (reinterpret_cast<uintptr_t>(R0) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(G0) & 15) == 0) {
+    const int tpb = 128;
+    const dim3 grid((unsigned)((left.width / 4 + tpb - 1) / tpb), (unsigned)left.height,
+                    (unsigned)left.count);
+    prepare_level0_x4_kernel<<<grid, tpb, 0, st>>>(
+        static_cast<const uint8_t *>(left.data), static_cast<const uint8_t *>(right.data),
+        left.pitch_bytes, stride, left.width, left.height, L0, R0, G0);
+    return cudaGetLastError();
+  }
   if (left.format == BDIS_U8)
     prepare_level0_kernel<uint8_t><<<blocks_for(total, threads), threads, 0, st>>>(
         left.data, right.data, left.pitch_bytes, stride, left.width, left.height, total, L0, R0,
@@ -147,6 +297,12 @@ cudaError_t launch_pyramid_level(const float *L, const float2 *R, int w, int h, 
   const int dw = (w + 1) / 2, dh = (h + 1) / 2;
   const long long total = (long long)dw * dh * count;
   if (total == 0) return cudaSuccess;
+  if (g_pyramid_fused) {
+    const dim3 grid((unsigned)((dw + kPyrX - 1) / kPyrX), (unsigned)((dh + kPyrY - 1) / kPyrY),
+                    (unsigned)count);
+    pyramid_fused_kernel<<<grid, 256, 0, st>>>(L, R, w, h, dw, dh, L1, R1, G1);
+    return cudaGetLastError();
+  }
   const int threads = 256;
   down_kernel<<<blocks_for(total, threads), threads, 0, st>>>(L, R, w, h, dw, dh, total, L1, R1);
   cudaError_t e = cudaGetLastError();

@@ -74,6 +74,33 @@ def test_pyramid_and_gradient(orc, shape):
             np.testing.assert_allclose(host(G)[b], orc.sobel_x(oL[b]), atol=PYR_ATOL)
 
 
+@pytest.mark.parametrize("shape", [(120, 160), (61, 97), (5, 7), (33, 64), (480, 640)])
+def test_fused_pyramid_matches_two_pass(shape):
+    """The fused pyramid kernel (shared-memory tile with a reflected halo) and
+    the downsample-then-gradient pair write identical levels."""
+    h, w = shape
+    rng = np.random.default_rng(h + w)
+    left = rng.integers(0, 256, (2, h, w), dtype=np.uint8)
+    right = rng.integers(0, 256, (2, h, w), dtype=np.uint8)
+    old = bd.get_pyramid_variant()
+    try:
+        levels = []
+        for fused in (True, False):
+            bd.set_pyramid_variant(fused)
+            L, R, G = bd.prepare_level0(dev(left, torch.uint8), dev(right, torch.uint8))
+            out = []
+            while min(L.shape[1:]) >= 3:
+                L, R, G = bd.pyramid_level(L, R)
+                out.append([host(t) for t in (L, R, G)])
+            levels.append(out)
+    finally:
+        bd.set_pyramid_variant(old)
+    assert len(levels[0]) == len(levels[1]) > 0
+    for a, b in zip(*levels):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+
+
 def test_pitched_and_float_inputs(orc):
     pair = synth.make_cfg1()
     h, w = pair.shape
@@ -83,8 +110,10 @@ def test_pitched_and_float_inputs(orc):
     bigr[:, 3:3 + w] = dev(pair.right, torch.uint8)
     a = bd.prepare_level0(big[:, 3:3 + w], bigr[:, 3:3 + w])
     b = bd.prepare_level0(dev(pair.left, torch.float32), dev(pair.right, torch.float32))
-    for x, y in zip(a, b):
-        assert torch.equal(x, y)
+    # 4-byte aligned rows, width a multiple of 4: the four-pixels-per-thread kernel
+    c = bd.prepare_level0(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8))
+    for x, y, z in zip(a, b, c):
+        assert torch.equal(x, y) and torch.equal(x, z)
 
 
 # ------------------------------------------------------- search + posterior
