@@ -18,15 +18,18 @@
 //   - with mean normalisation, sum g_n (R~_n - T_n) = sum g_c R~ - sum g_c T
 //     where g_c is the gradient centred on the valid set, so an iteration is
 //     two FMAs and one load per pixel and one group reduction;
-//   - the window energies use two passes (mean, then squares) to keep the
-//     saddle decisions well conditioned.
+//   - the window energies are sums of residuals taken relative to a per-column
+//     shift (the column's first-row residual), merged exactly over the group,
+//     which keeps the saddle decisions well conditioned; per row a lane reads
+//     the CPL + 2 packed pairs that all five samples of its columns need once.
 //
 // Two instantiations: a fast path with the patch size and window length fixed
 // at compile time (fully unrolled, no per-row guards) for the common settings,
 // and a generic path for any patch size up to 32 and window up to 15.
 //
 // Roofline: instruction-issue / FP32 bound. Algorithmic work per patch
-// (patch evaluations x 8 flops per pixel): ps^2 * 8 * (iterations + s).
+// (patch evaluations x 8 flops per pixel): ps^2 * 8 * (updates + s), the
+// update count being at most `iterations` (a converged patch stops early).
 // DRAM bytes per patch level: the L, G and packed R planes read once
 // (16 B per pixel) plus 8 B written per patch.
 #include "bdis_internal.cuh"
@@ -99,7 +102,7 @@ __device__ __forceinline__ PatchPos patch_pos(const SearchArgs &a, long long k) 
 __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, bool write,
                                              float D, float u0, float last_step, bool flat,
                                              int steps, int nvalid, int nc, float Ec, float Eo,
-                                             float Emin, float z, int ps) {
+                                             float pc, float z, int ps) {
   uint8_t flags = flat ? kFlagFlat : 0;
   if (!isfinite(D) || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
   if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
   if (nc == 0) {
     if (!(flags & kFlagDiverged)) flags |= kFlagEmpty;  // a diverged patch reads no window
   } else {
-    post = expf(-(Ec - Emin) / a.kappa) / z;
+    post = pc / z;  // pc = exp(-(Ec - Emin) / kappa), the centre's term of z
     if (a.s > 1 && Eo < Ec - kSaddleTau * fmaxf(Ec, 1.f)) flags |= kFlagSaddle;
   }
   if (nvalid < a.nmin_valid) flags |= kFlagGamma;
@@ -166,17 +169,30 @@ struct GlobalRows {
   const float2 *row0;  // row y0 of the packed right plane
   int w;
   __device__ __forceinline__ const float2 *col(int x) const { return row0 + x; }
+  // a column that is always safe to read (for lanes whose sample is unused)
+  __device__ __forceinline__ const float2 *col_clamped(int x) const {
+    return row0 + min(max(x, 0), w - 1);
+  }
   __device__ __forceinline__ float2 ld(const float2 *p, int r) const {
     return __ldg(p + (size_t)r * w);
   }
+  __device__ __forceinline__ void ready() const {}
 };
 
 template <int TW>
 struct TileRows {
   const float2 *tile;  // shared: PS rows of TW pairs, first column `lo`
-  int lo;
+  int lo, width;       // columns lo .. lo + width - 1 are staged (the rest is never written)
   __device__ __forceinline__ const float2 *col(int x) const { return tile + (x - lo); }
+  __device__ __forceinline__ const float2 *col_clamped(int x) const {
+    return tile + min(max(x - lo, 0), width - 1);
+  }
   __device__ __forceinline__ float2 ld(const float2 *p, int r) const { return p[r * TW]; }
+  // the staging copies of this lane are complete and the warp's are visible
+  __device__ __forceinline__ void ready() const {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
+  }
 };
 
 template <int PS, int CPL, class Rows>
@@ -264,18 +280,17 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
       frozen = true;
       flat = true;
     }
-    // four partial sums break the FMA dependency chain
+    if (it == 0) rows.ready();  // staged rows (if any) arrive while the sums above load
+    // four partial sums break the FMA dependency chain. No branches: an invalid
+    // column has gc = 0 and reads a clamped (readable) column, so it adds
+    // exactly 0; a frozen patch's sum is not used.
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    if (!frozen) {
 #pragma unroll
-      for (int j = 0; j < CPL; ++j) {
-        if (v[j]) {
-          const auto p = rows.col(ib + j);
+    for (int j = 0; j < CPL; ++j) {
+      const auto p = rows.col_clamped(ib + j);
 #pragma unroll
-          for (int r = 0; r < PS; ++r)
-            acc[r & 3] = fmaf(gc[j][r], lerp_packed(rows.ld(p, r), t), acc[r & 3]);
-        }
-      }
+      for (int r = 0; r < PS; ++r)
+        acc[r & 3] = fmaf(gc[j][r], lerp_packed(rows.ld(p, r), t), acc[r & 3]);
     }
     const float Ssum = group_sum<G>((acc[0] + acc[1]) + (acc[2] + acc[3]));
     if (!frozen) {
@@ -288,6 +303,7 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     }
   }
 
+  rows.ready();
   // ---- Bayesian window (Eqs. 3-4): samples at D* + {-1, -0.5, 0, 0.5, 1}
   const bool fin = isfinite(D);
   // a patch that left its search range is dropped (R8) and reads no window
@@ -296,11 +312,10 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
   float t;
   split_disp(D, kd, t);
   const int ib = xl + kd;
-  // sample at D + delta sits at column base ib + off[delta] with fraction tt[delta]
+  // samples at D* + {-1, 0, 1} have fraction t; at D* +- 0.5 fraction th, with
+  // base column one further right when t >= 0.5
   const bool hi = t >= 0.5f;
   const float th = hi ? t - 0.5f : t + 0.5f;
-  const int off[S] = {1, hi ? 1 : 0, 0, hi ? 0 : -1, -1};
-  const float tt[S] = {t, th, t, th, t};
   bool vc[CPL];
   int nv_lane = 0, nc_lane = 0;
 #pragma unroll
@@ -315,59 +330,67 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     return;
   }
   const int nc = PS * (int)group_sum<G>((float)nc_lane);
-  // One pass over the rows: per column j, residuals are taken relative to a
-  // shift cs[j] (the column's first-row residual at D*), which removes the
+  // One pass over the rows. Every sample of the lane's columns lies in
+  // columns ib - 1 .. ib + CPL, so per row the lane reads those CPL + 2 packed
+  // pairs once and interpolates each at both fractions (t for D* and D* +- 1,
+  // th for D* +- 0.5). Per column j, residuals are taken relative to a shift
+  // cs[j] (the column's first-row residual at D*), which removes the
   // brightness offset between the views; the group then merges the shifted
   // sums exactly: sum (d - md)^2 = S2 - 2 (md - cs) S1 + n (md - cs)^2.
-  float T[CPL][PS];
+  // Pairs are read only where a valid column samples them (in bounds then).
+  bool need[CPL + 2];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j)
-#pragma unroll
-    for (int r = 0; r < PS; ++r) T[j][r] = act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f;
+  for (int m = 0; m < CPL + 2; ++m)
+    need[m] = (m < CPL && vc[m]) || (m >= 1 && m - 1 < CPL && vc[m - 1]) ||
+              (m >= 2 && m - 2 < CPL && vc[m - 2]);
   float cs[CPL];
 #pragma unroll
-  for (int j = 0; j < CPL; ++j) {
-    cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) - T[j][0] : 0.f;
+  for (int j = 0; j < CPL; ++j)
+    cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) - __ldg(Lc + j) : 0.f;
+  float S1[S][CPL], S2[S][CPL];
 #pragma unroll
-    for (int r = 0; r < PS; ++r) T[j][r] += cs[j];  // the window works on T + shift
+  for (int i = 0; i < S; ++i)
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) S1[i][j] = S2[i][j] = 0.f;
+#pragma unroll
+  for (int r = 0; r < PS; ++r) {
+    float Lt[CPL + 2], Lh[CPL + 2];
+#pragma unroll
+    for (int m = 0; m < CPL + 2; ++m) {
+      const float2 q = need[m] ? rows.ld(rows.col(ib - 1 + m), r) : make_float2(0.f, 0.f);
+      Lt[m] = lerp_packed(q, t);
+      Lh[m] = lerp_packed(q, th);
+    }
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const float Tj = (vc[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f) + cs[j];  // template + shift
+      // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1.
+      // An invalid column's sums (finite: its pairs read as 0) are not merged below.
+      const float d[S] = {Lt[j + 2] - Tj, (hi ? Lh[j + 2] : Lh[j + 1]) - Tj, Lt[j + 1] - Tj,
+                          (hi ? Lh[j + 1] : Lh[j]) - Tj, Lt[j] - Tj};
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        S1[i][j] += d[i];
+        S2[i][j] = fmaf(d[i], d[i], S2[i][j]);
+      }
+    }
   }
   const bool write = live && c == 0;
+  const float inv_nc = nc > 0 ? 1.f / (float)nc : 0.f;
   float E[S];
 #pragma unroll
   for (int i = 0; i < S; ++i) {
-    float S1[CPL], S2[CPL];
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      // two partial sums per quantity (even / odd rows) shorten the chains
-      float s1a = 0.f, s1b = 0.f, s2a = 0.f, s2b = 0.f;
-      if (vc[j]) {
-        const auto p = rows.col(ib + j + off[i]);
-#pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          const float d = lerp_packed(rows.ld(p, r), tt[i]) - T[j][r];
-          if (r & 1) {
-            s1b += d;
-            s2b = fmaf(d, d, s2b);
-          } else {
-            s1a += d;
-            s2a = fmaf(d, d, s2a);
-          }
-        }
-      }
-      S1[j] = s1a + s1b;
-      S2[j] = s2a + s2b;
-    }
     float s1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) s1 += S1[j] + (float)PS * cs[j];
+    for (int j = 0; j < CPL; ++j) s1 += vc[j] ? S1[i][j] + (float)PS * cs[j] : 0.f;
     s1 = group_sum<G>(s1);
-    const float md = (a.normalize && nc > 0) ? s1 / (float)nc : 0.f;
+    const float md = (a.normalize && nc > 0) ? s1 * inv_nc : 0.f;
     float e = 0.f;
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
       if (vc[j]) {
         const float u = md - cs[j];
-        e += fmaf(-2.f * u, S1[j], fmaf((float)PS * u, u, S2[j]));
+        e += fmaf(-2.f * u, S1[i][j], fmaf((float)PS * u, u, S2[i][j]));
       }
     }
     E[i] = group_sum<G>(e);
@@ -379,11 +402,15 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     Emin = fminf(Emin, E[i]);
     if (i != HALF) Eo = fminf(Eo, E[i]);
   }
-  float z = 0.f;
+  const float nik = -1.f / a.kappa;
+  float z = 0.f, pc = 0.f;
 #pragma unroll
-  for (int i = 0; i < S; ++i) z += expf(-(E[i] - Emin) / a.kappa);
-  finish_patch(a, k, write, D, u0, last_step, flat, steps, nvalid, nc, E[HALF], Eo, Emin, z,
-               PS);
+  for (int i = 0; i < S; ++i) {
+    const float ex = expf((E[i] - Emin) * nik);
+    z += ex;
+    if (i == HALF) pc = ex;
+  }
+  finish_patch(a, k, write, D, u0, last_step, flat, steps, nvalid, nc, E[HALF], Eo, pc, z, PS);
 }
 
 // One patch per group, pairs on blockIdx.y, patches of a pair on blockIdx.x;
@@ -433,11 +460,12 @@ __device__ __forceinline__ int warp_max(int v) {
 // union of its patches' ranges (with one more column each side for rounding
 // of the range test) into shared memory and samples from there. A warp whose
 // starts spread too far for TW columns reads global memory instead; results
-// are identical either way (same arithmetic in the same order). Measured on
-// GB300 it is the slower choice at patch size 8 (2 columns per lane: 6.2 vs
-// 5.4 ms of search per 128 pairs): the staging pass and its extra dependent
-// DRAM round trip cost more than the row-address arithmetic that the
-// immediate shared offsets save, so it is off by default.
+// are identical either way (same arithmetic in the same order). The copies
+// are asynchronous and the patch waits for them only before its first sample.
+// Measured on GB300 its steps run ~20% faster than the global-memory kernel's
+// (lower sample latency, about the same instruction count), but staging and
+// the second code path cost more per patch than that saves: 5.4 vs 4.6 ms of
+// search per 128 pairs at patch size 8, so it is off by default.
 template <int PS, int CPL, int MINB, int TW>
 __global__ void __launch_bounds__(128, MINB) search_tiled_kernel(const SearchArgs a) {
   constexpr int LANES = (PS + CPL - 1) / CPL;
@@ -472,13 +500,19 @@ __global__ void __launch_bounds__(128, MINB) search_tiled_kernel(const SearchArg
   lo = warp_min(lo);
   hi = warp_max(hi);
   if (__all_sync(kFull, bounded) && hi - lo < TW) {
+    // asynchronous copies of the needed columns lo .. hi of the PS rows (zero
+    // outside the image); fixed_patch waits for them just before the first
+    // sample, so they travel while the patch's first sums load
     float2 *tile = tiles[warp];
-    for (int i = lane; i < PS * TW; i += 32) {
-      const int r = i / TW, x = lo + (i - r * TW);
-      tile[i] = (x >= 0 && x < w) ? __ldg(row0 + (size_t)r * w + x) : make_float2(0.f, 0.f);
+    const int width = hi - lo + 1;
+    for (int i = lane; i < PS * width; i += 32) {
+      const int r = i / width, cc = i - r * width, x = lo + cc;
+      const bool in = x >= 0 && x < w;
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + r * TW + cc);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst),
+                   "l"(in ? row0 + (size_t)r * w + x : row0), "r"(in ? 8 : 0));
     }
-    __syncwarp();
-    fixed_patch<PS, CPL>(a, TileRows<TW>{tile, lo}, k, live, c, gbits, b, x0, y0, u0);
+    fixed_patch<PS, CPL>(a, TileRows<TW>{tile, lo, width}, k, live, c, gbits, b, x0, y0, u0);
   } else {
     fixed_patch<PS, CPL>(a, GlobalRows{row0, w}, k, live, c, gbits, b, x0, y0, u0);
   }
@@ -627,7 +661,8 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
       z += expf(-(E - Emin) / a.kappa);
     }
   }
-  finish_patch(a, k, write, D, u0, last_step, flat, steps, nvalid, nc, Ec, Eo, Emin, z, ps);
+  finish_patch(a, k, write, D, u0, last_step, flat, steps, nvalid, nc, Ec, Eo,
+               expf(-(Ec - Emin) / a.kappa), z, ps);
 }
 
 template <int PS, int CPL, int MINB>
