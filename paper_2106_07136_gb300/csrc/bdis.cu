@@ -29,6 +29,10 @@ struct bdis_handle {
   };
   std::vector<cudaEvent_t> event_pool;
   std::vector<Mark> marks;
+  // bdis_match_host pipeline: copy-in and copy-out streams beside `stream`,
+  // and per buffer slot the events "inputs copied", "matched", "output copied"
+  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {};
 };
 
 namespace bdis {
@@ -596,6 +600,17 @@ void bdis_destroy(bdis_handle *h) {
       cudaEventDestroy(m.stop);
     }
     for (auto e : h->event_pool) cudaEventDestroy(e);
+    if (h->copy_in) {
+      cudaStreamSynchronize(h->copy_in);
+      cudaStreamSynchronize(h->copy_out);
+      cudaStreamDestroy(h->copy_in);
+      cudaStreamDestroy(h->copy_out);
+      for (int i = 0; i < 2; ++i) {
+        cudaEventDestroy(h->ev_in[i]);
+        cudaEventDestroy(h->ev_done[i]);
+        cudaEventDestroy(h->ev_out[i]);
+      }
+    }
   }
   delete h;
 }
@@ -740,6 +755,23 @@ bdis_status bdis_warm_map(const float *prev, int width, int height, int level, i
                                      static_cast<cudaStream_t>(stream)));
 }
 
+namespace {
+
+// Copy streams and events of the host pipeline, created on first use.
+bdis_status ensure_pipeline(bdis_handle *h) {
+  if (h->copy_in) return BDIS_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming);
+  }
+  return record_cuda(e);
+}
+
+}  // namespace
+
 bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right, int width,
                             int height, int count, const bdis_params *p, float *disparity_out) {
   if (!h || !left || !right || !disparity_out || width < 1 || height < 1 || count < 1)
@@ -750,26 +782,76 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
   if (s != BDIS_OK) return s;
   s = bind_device(h);
   if (s != BDIS_OK) return s;
-  const Layout lay = plan_layout(width, height, count, *p, true);
-  s = ensure_workspace(h, lay.bytes);
+  const size_t wh = (size_t)width * height;
+  // The batch runs as chunks: chunk i's inputs are copied in (copy_in) while
+  // chunk i-1 is matched (stream) and chunk i-2's result is copied out
+  // (copy_out). Inputs and outputs on the device are double-buffered by slot
+  // (i & 1); a slot is refilled only after the match that read it (ev_done)
+  // and the copy-out that read its output (ev_out) have finished.
+  const int nchunk = count >= 8 ? 4 : (count >= 2 ? 2 : 1);
+  const int cs = (count + nchunk - 1) / nchunk;
+  const Layout lay = plan_layout(width, height, cs, *p, true);
+  const size_t in_b = wh * cs, out_b = wh * cs * sizeof(float);
+  size_t off = lay.bytes;
+  auto take = [&](size_t n) {
+    const size_t o = off;
+    off += (n + 255) / 256 * 256;
+    return o;
+  };
+  const size_t slot_l[2] = {lay.in_left, nchunk > 1 ? take(in_b) : 0};
+  const size_t slot_r[2] = {lay.in_right, nchunk > 1 ? take(in_b) : 0};
+  const size_t slot_o[2] = {lay.out, nchunk > 1 ? take(out_b) : 0};
+  s = ensure_workspace(h, off);
   if (s != BDIS_OK) return s;
+  if (nchunk > 1) {
+    s = ensure_pipeline(h);
+    if (s != BDIS_OK) return s;
+  }
   char *base = static_cast<char *>(h->ws);
-  const size_t in_bytes = (size_t)width * height * count;
-  cudaError_t e = cudaMemcpyAsync(base + lay.in_left, left, in_bytes, cudaMemcpyHostToDevice,
-                                  h->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + lay.in_right, right, in_bytes, cudaMemcpyHostToDevice, h->stream);
-  if (e != cudaSuccess) return record_cuda(e);
-  bdis_image L{base + lay.in_left, width, height, (size_t)width, (size_t)width * height, count,
-               BDIS_U8};
-  bdis_image R = L;
-  R.data = base + lay.in_right;
-  float *dout = reinterpret_cast<float *>(base + lay.out);
-  s = run_match(h, L, R, *p, dout, lay);
+  cudaStream_t sin = nchunk > 1 ? h->copy_in : h->stream;
+  cudaStream_t sout = nchunk > 1 ? h->copy_out : h->stream;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < nchunk && e == cudaSuccess; ++i) {
+    const int first = i * cs, n = count - first < cs ? count - first : cs;
+    if (n <= 0) break;
+    const int slot = i & 1;
+    const size_t ib = wh * n;
+    if (nchunk > 1 && i >= 2) e = cudaStreamWaitEvent(sin, h->ev_done[slot], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + slot_l[slot], left + wh * first, ib, cudaMemcpyHostToDevice, sin);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(base + slot_r[slot], right + wh * first, ib, cudaMemcpyHostToDevice,
+                          sin);
+    if (nchunk > 1) {
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[slot], sin);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_in[slot], 0);
+      if (e == cudaSuccess && i >= 2) e = cudaStreamWaitEvent(h->stream, h->ev_out[slot], 0);
+    }
+    if (e != cudaSuccess) break;
+    bdis_image L{base + slot_l[slot], width, height, (size_t)width, wh, n, BDIS_U8};
+    bdis_image R = L;
+    R.data = base + slot_r[slot];
+    float *dout = reinterpret_cast<float *>(base + slot_o[slot]);
+    s = run_match(h, L, R, *p, dout, lay);
+    if (s != BDIS_OK) break;
+    if (nchunk > 1) {
+      e = cudaEventRecord(h->ev_done[slot], h->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, h->ev_done[slot], 0);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(disparity_out + wh * first, dout, ib * sizeof(float),
+                          cudaMemcpyDeviceToHost, sout);
+    if (e == cudaSuccess && nchunk > 1) e = cudaEventRecord(h->ev_out[slot], sout);
+  }
+  // leave every stream idle: the next call may resize or reuse the workspace
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  if (nchunk > 1) {
+    cudaError_t e3 = cudaStreamSynchronize(h->copy_in);
+    cudaError_t e4 = cudaStreamSynchronize(h->copy_out);
+    if (e2 == cudaSuccess) e2 = e3 != cudaSuccess ? e3 : e4;
+  }
   if (s != BDIS_OK) return s;
-  e = cudaMemcpyAsync(disparity_out, dout, in_bytes * sizeof(float), cudaMemcpyDeviceToHost,
-                      h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = e2;
   return record_cuda(e);
 }
 

@@ -337,14 +337,23 @@ def test_batch_equals_single_pairs(orc, matcher):
         assert_e2e(outb[b], orc.match(L[b], R[b], op), f"pair {b}")
 
 
-def test_match_host_equals_device(matcher):
-    L, R, _ = synth.make_batch(1, 2)
+@pytest.mark.parametrize("count,pinned", [(1, True), (2, True), (3, True), (8, True), (13, True),
+                                          (13, False)])
+def test_match_host_equals_device(matcher, count, pinned):
+    """The host-buffer entry (chunked: copies of one chunk overlap the match
+    of the next, device buffers double-buffered) returns exactly what the
+    device entry returns, for every chunking: 1 pair, 2 and 4 chunks, a
+    short last chunk, and pageable host memory."""
+    L, R, _ = synth.make_batch(1, count)
     gp = bd.default_params(**CFG1)
     dv = host(matcher.match(dev(L, torch.uint8), dev(R, torch.uint8), gp))
-    out = matcher.match_host(torch.from_numpy(L).pin_memory(), torch.from_numpy(R).pin_memory(),
-                             gp).numpy()
-    assert np.array_equal(np.isnan(dv), np.isnan(out))
-    assert np.array_equal(dv[~np.isnan(dv)], out[~np.isnan(out)])
+    lt, rt = torch.from_numpy(L), torch.from_numpy(R)
+    if pinned:
+        lt, rt = lt.pin_memory(), rt.pin_memory()
+    for _ in range(2):  # the second call reuses the handle's pipeline
+        out = matcher.match_host(lt, rt, gp).numpy()
+        assert np.array_equal(np.isnan(dv), np.isnan(out))
+        assert np.array_equal(dv[~np.isnan(dv)], out[~np.isnan(out)])
 
 
 # ----------------------------------------------------- pins on the GPU path
