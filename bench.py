@@ -17,6 +17,7 @@ the FP64 CPU oracle on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import multiprocessing as mp
@@ -42,7 +43,7 @@ ALU_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
 def parse():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--batch", type=int, default=128, help="pairs per step and rank")
@@ -100,9 +101,13 @@ def run_oracle_sample(pairs, ps, pool):
 # ------------------------------------------------------------ clocks
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons every 50 ms, each sample
+    timestamped. Start it before the warm-up; `stop(t0, t1)` keeps the samples
+    taken within the timed region [t0, t1] (host clock, one interval of slack)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index):
         self.proc = None
@@ -110,12 +115,12 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
 
-    def stop(self):
+    def stop(self, t0, t1):
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -124,22 +129,27 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        slack = self.PERIOD_MS / 1e3
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in out.splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                clk, cmax = float(f[2]), float(f[3])
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
+            if not (t0 - slack <= ts <= t1 + slack):
+                continue
+            sm.append(clk)
+            smax.append(cmax)
+            for n, v in zip(names, f[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -272,10 +282,10 @@ def main():
         return run_reference(args)
 
     rank, world, local = dist_env()
-    # Start the CPU-oracle pool before any CUDA work (spawned workers).
+    # The CPU-oracle pool is spawned (fresh interpreters, no CUDA state) after
+    # all GPU measurements, so its workers never compete with them.
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     cores = host_cores()
-    pool = mp.get_context("spawn").Pool(cores) if want_cpu else None
 
     import torch
     import torch.distributed as dist
@@ -312,6 +322,7 @@ def main():
     m = bd.Matcher(device, stream)
     m.reserve(W, H, B, params)
 
+    clocks = ClockSampler(local)  # running through the warm-up, kept for the timed region
     for _ in range(args.warmup):
         flush.fill_(1.0)
         m.match(left, right, params, out=out)
@@ -321,17 +332,18 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     m.read_timing()
     m.enable_timing(True)
-    clocks = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
+    t_timed0 = time.time()
     for i in range(args.steps):
         flush.fill_(float(i))  # L2 flush between timed steps (not timed)
         starts[i].record(stream)
         m.match(left, right, params, out=out)
         ends[i].record(stream)
     torch.cuda.synchronize()
+    t_timed1 = time.time()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop(t_timed0, t_timed1)
     m.enable_timing(False)
     kt = m.read_timing()
     ms = reduce_max_ms(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device, world)
@@ -372,10 +384,12 @@ def main():
 
     acc = {"gpu_vs_ground_truth": synth.error_stats(gpu_maps, Dgt)}
     cpu = None
-    if pool is not None:
+    if want_cpu:
         n_cpu = min(cores, U)
-        wall, res = run_oracle_sample(list(zip(Lh[:n_cpu], Rh[:n_cpu])), ps, pool)
-        pool.close()
+        sample = list(zip(Lh[:n_cpu], Rh[:n_cpu]))
+        with mp.get_context("spawn").Pool(cores) as pool:
+            run_oracle_sample(sample, ps, pool)  # warm-up: workers start and load the oracle
+            wall, res = run_oracle_sample(sample, ps, pool)
         cpu = {"value": n_cpu / wall, "unit": "pairs/s", "cores": n_cpu, "kind": "oracle",
                "sample": f"{n_cpu} of the bench's 640x480 pairs, one per process "
                          f"(FP64 C oracle, single-threaded per pair)",
