@@ -770,7 +770,7 @@ cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
     if (a.ps == 8) {
       if (cpl == 1) return launch_fast<8, 1, 8>(a, st);
       if (cpl == 4) return launch_fast<8, 4, 4>(a, st);
-      return launch_fast<8, 2, 8>(a, st);  // 64 registers: 8 blocks of 128 per SM
+      return launch_fast<8, 2, 7>(a, st);  // 72 registers, no spill: 7 blocks of 128 per SM
     }
     if (a.ps == 12) return cpl == 1 ? launch_fast<12, 1, 4>(a, st) : launch_fast<12, 3, 3>(a, st);
     if (a.ps == 16) return cpl == 1 ? launch_fast<16, 1, 4>(a, st) : launch_fast<16, 2, 3>(a, st);
