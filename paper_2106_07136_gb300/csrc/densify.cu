@@ -138,21 +138,51 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
 // No shared memory and no block barriers: each warp's patch reads (19 patches
 // of a row for 32 columns) are L1 broadcasts.
 template <int PS, int S, int K>
-__global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a) {
+__global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(const DensifyArgs a) {
   constexpr int M = PS / S;
   static_assert(M * S == PS && K % S == 0, "strip geometry");
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  // patch columns / rows a block (128 columns x K rows) can need, plus one
+  // slot each for the last (irregular) patch column / row
+  constexpr int NCMAX = (128 + S - 1) / S + M + 2, NRMAX = K / S + M + 1;
+  // Whatever the image size, a block's regular patch columns number at most
+  // (126 + PS) / S + 1 (all of [ilo(X0), ihi(X0 + 127)]) and its regular rows
+  // at most K / S + M - 1 (rows g0 - M + 1 .. g0 + K / S - 1): with the last
+  // column / row slot they fit the tile.
+  static_assert((126 + PS) / S + 1 + 1 <= NCMAX && K / S + M - 1 + 1 <= NRMAX, "tile bounds");
+  __shared__ float sw[NRMAX][NCMAX], sd[NRMAX][NCMAX];
+  __shared__ float smask[PS];
+  const int X0 = blockIdx.x * 128, x = X0 + (int)threadIdx.x;
   const int Y0 = blockIdx.y * K, b = blockIdx.z;
-  if (x >= a.w || Y0 >= a.h) return;
-  // Gaussian mask (Eq. 5) at an offset inside the patch; the same expression
-  // as the tiled kernel's table, so the same values
-  auto mask_at = [&](int q) {
-    const float m = (float)q - (PS - 1) * 0.5f;
-    return expf(-(m * m) / a.two_s2);
-  };
-  float mask[PS];  // indexed with compile-time offsets only (stays in registers)
-#pragma unroll
-  for (int q = 0; q < PS; ++q) mask[q] = mask_at(q);
+  const bool active = x < a.w;
+  const float *wp = a.weight + (long long)b * a.np;
+  const float *dp = a.d_star + (long long)b * a.np;
+  // The block's patch rows and columns are staged into shared memory with
+  // asynchronous copies, all in flight at once (one round trip per block).
+  const int xlast_b = min(X0 + 127, a.w - 1);
+  const int g0 = Y0 / S, gend = (min(Y0 + K, a.h) - 1) / S;
+  const int ic0 = X0 - PS + 1 <= 0 ? 0 : (X0 - PS + 1 + S - 1) / S;
+  const int ic1 = min(xlast_b / S, a.nx - 2);
+  const int jr0 = max(0, g0 - M + 1), jr1 = min(gend, a.ny - 2);
+  const int NC = max(0, ic1 - ic0 + 1), NR = max(0, jr1 - jr0 + 1);
+  {
+    for (int q = threadIdx.x; q < (NR + 1) * (NC + 1); q += blockDim.x) {
+      const int rr = q / (NC + 1), cc = q - rr * (NC + 1);
+      const int j = rr < NR ? jr0 + rr : a.ny - 1, i = cc < NC ? ic0 + cc : a.nx - 1;
+      const long long o = (long long)j * a.nx + i;
+      const unsigned dw = (unsigned)__cvta_generic_to_shared(&sw[rr][cc]);
+      const unsigned dd = (unsigned)__cvta_generic_to_shared(&sd[rr][cc]);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dw), "l"(wp + o));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dd), "l"(dp + o));
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+  }
+  if (threadIdx.x < PS) {  // Gaussian mask (Eq. 5): the tiled kernel's expression and values
+    const float m = (float)threadIdx.x - (PS - 1) * 0.5f;
+    smask[threadIdx.x] = expf(-(m * m) / a.two_s2);
+  }
+  __syncthreads();
+  if (!active || Y0 >= a.h) return;
+  auto mask_at = [&](int q) { return smask[q]; };
   // covering patches of column x: regular ilo .. ihi (<= nx - 2), then the last;
   // their x weights are fixed for the thread
   const int ilo = x - PS + 1 <= 0 ? 0 : (x - PS + 1 + S - 1) / S;
@@ -165,24 +195,29 @@ __global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a)
     mxr[k] = (q >= 0 && q < PS) ? mask_at(q) : 0.f;
   }
   const float mxl = ilast ? mask_at(x - (a.w - PS)) : 0.f;
-  const float *wp = a.weight + (long long)b * a.np;
-  const float *dp = a.d_star + (long long)b * a.np;
-  // x-weighted sums of patch row j (0 <= j < ny), same order as the tiled
-  // kernel; all of the row's loads are issued before any is used
-  auto row_sums = [&](int j, float &A, float &B) {
-    const float *wr = wp + (long long)j * a.nx;
-    const float *dr = dp + (long long)j * a.nx;
-    float wv[M + 1], dv[M + 1];
-    bool use[M + 1];
+  // covering patch k of column x (k = 0..M: the regular ilo + k, then the last)
+  bool use[M + 1];
+  int pidx[M + 1];
 #pragma unroll
-    for (int k = 0; k <= M; ++k) {  // at most M regular patches cover x, plus the last
-      const int ii = ilo + k;
-      const bool reg = ii <= ihi;
-      use[k] = reg || (ilast && ii == ihi + 1);
-      const int i = reg ? ii : a.nx - 1;
-      wv[k] = use[k] ? __ldg(wr + i) : 0.f;
-      dv[k] = use[k] ? __ldg(dr + i) : 0.f;
+  for (int k = 0; k <= M; ++k) {
+    const int ii = ilo + k;
+    const bool reg = ii <= ihi;
+    use[k] = reg || (ilast && ii == ihi + 1);
+    pidx[k] = reg ? ii : a.nx - 1;
+  }
+  // a patch row's values (staged; read one row ahead of their use) and its
+  // x-weighted sums, in the same order and with the same operations as the
+  // tiled kernel
+  auto load_row = [&](int j, float *wv, float *dv) {
+    const int rr = j <= a.ny - 2 ? j - jr0 : NR;
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      const int cc = ilo + k <= ihi ? pidx[k] - ic0 : NC;
+      wv[k] = use[k] ? sw[rr][cc] : 0.f;
+      dv[k] = use[k] ? sd[rr][cc] : 0.f;
     }
+  };
+  auto sum_row = [&](const float *wv, const float *dv, float &A, float &B) {
     A = 0.f;
     B = 0.f;
 #pragma unroll
@@ -194,12 +229,16 @@ __global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a)
       }
     }
   };
+  auto row_sums = [&](int j, float &A, float &B) {
+    float wv[M + 1], dv[M + 1];
+    load_row(j, wv, dv);
+    sum_row(wv, dv, A, B);
+  };
   const int ylast = a.h - PS;  // first pixel row the last patch row covers
   float lastA = 0.f, lastB = 0.f;
   bool have_last = false;
   // ring of the regular rows g - M + 1 .. g (slot k holds row g - M + 1 + k)
   float rA[M], rB[M];
-  const int g0 = Y0 / S;
 #pragma unroll
   for (int k = 0; k < M - 1; ++k) {
     const int j = g0 - M + 1 + k;
@@ -209,7 +248,16 @@ __global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a)
   }
   const long long obase = (long long)b * a.plane + x;
   const int yend = min(Y0 + K, a.h);
+  float nw[M + 1], nd[M + 1];  // row g's loads, issued during group g - 1
+  if (g0 <= a.ny - 2) load_row(g0, nw, nd);
   for (int g = g0; g * S < yend; ++g) {
+    float cw[M + 1], cd[M + 1];
+#pragma unroll
+    for (int k = 0; k <= M; ++k) {
+      cw[k] = nw[k];
+      cd[k] = nd[k];
+    }
+    if (g + 1 <= a.ny - 2 && (g + 1) * S < yend) load_row(g + 1, nw, nd);
 #pragma unroll
     for (int k = 0; k < M - 1; ++k) {
       rA[k] = rA[k + 1];
@@ -217,7 +265,7 @@ __global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a)
     }
     rA[M - 1] = 0.f;
     rB[M - 1] = 0.f;
-    if (g <= a.ny - 2) row_sums(g, rA[M - 1], rB[M - 1]);
+    if (g <= a.ny - 2) sum_row(cw, cd, rA[M - 1], rB[M - 1]);
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       const int y = g * S + t;
@@ -227,7 +275,7 @@ __global__ void __launch_bounds__(256) densify_strip_kernel(const DensifyArgs a)
       for (int k = 0; k < M; ++k) {
         const int j = g - M + 1 + k;
         if (j < 0 || j > a.ny - 2) continue;
-        const float my = mask[t + (M - 1 - k) * S];
+        const float my = smask[t + (M - 1 - k) * S];
         num = fmaf(my, rA[k], num);
         den = fmaf(my, rB[k], den);
       }

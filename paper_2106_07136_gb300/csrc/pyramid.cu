@@ -166,67 +166,99 @@ __global__ void __launch_bounds__(128) prepare_level0_x4_kernel(
 // the packed R1 and Sobel-x / 8 of L1 are written once (as sobel_pack_kernel).
 constexpr int kPyrX = 32, kPyrY = 16;
 constexpr int kStX = 2 * kPyrX + 7, kStY = 2 * kPyrY + 7;  // staged input columns / rows
+constexpr int kStP = 72;                                     // staged row pitch (floats)
+constexpr int kCx = kPyrX + 2;                               // computed columns (with halo)
 
 __global__ void __launch_bounds__(256) pyramid_fused_kernel(
     const float *__restrict__ L, const float2 *__restrict__ R, int w, int h, int dw, int dh,
     float *__restrict__ L1, float2 *__restrict__ R1, float *__restrict__ G1) {
-  __shared__ float inL[kStY][kStX], inR[kStY][kStX];
-  __shared__ float hL[kStY][kPyrX + 2], hR[kStY][kPyrX + 2];
-  __shared__ float sL[kPyrY + 2][kPyrX + 2], sR[kPyrY + 2][kPyrX + 2];
+  __shared__ float inL[kStY][kStP], inR[kStY][kStP];
+  __shared__ float hL[kStY][kCx], hR[kStY][kCx];
+  __shared__ float sL[kPyrY + 2][kCx], sR[kPyrY + 2][kCx];
   const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
-  const int tid = threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const float *Lb = L + (long long)b * w * h;
   const float2 *Rb = R + (long long)b * w * h;
   const float k[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
-  // stage rows needed: those of computed rows Y0 - 1 .. min(Y0 + kPyrY, dh)
-  // (reflected). Asynchronous 4-byte copies: every copy of the thread is in
-  // flight before the one wait (the value of R is the first word of its pair).
-  for (int q = tid; q < kStY * kStX; q += blockDim.x) {
-    const int r = q / kStX, c = q - r * kStX;
-    const int yi = 2 * Y0 - 4 + r, xi = 2 * X0 - 4 + c;
-    if (yi > h + 1 || xi > w + 1) continue;  // past the last reflected tap: never read
-    const size_t off = (size_t)reflect101(yi, h) * w + reflect101(xi, w);
-    const unsigned dl = (unsigned)__cvta_generic_to_shared(&inL[r][c]);
-    const unsigned dr = (unsigned)__cvta_generic_to_shared(&inR[r][c]);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dl), "l"(Lb + off));
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr), "l"(Rb + off));
+  // Warps take stage rows, lanes take columns, so every reflected index is
+  // computed once per row (warp) or once per column (lane). Stage row r holds
+  // input row reflect101(2 Y0 - 4 + r), column c input column
+  // reflect101(2 X0 - 4 + c); anything past the last reflected tap is skipped.
+  int xsrc[3];
+  bool xok[3];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int c = lane + 32 * u, xi = 2 * X0 - 4 + c;
+    xok[u] = c < kStX && xi <= w + 1;
+    xsrc[u] = xok[u] ? reflect101(xi, w) : 0;
+  }
+  for (int r = warp; r < kStY; r += nwarp) {
+    const int yi = 2 * Y0 - 4 + r;
+    if (yi > h + 1) break;  // rows only grow from here
+    const size_t rowoff = (size_t)reflect101(yi, h) * w;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (!xok[u]) continue;
+      const int c = lane + 32 * u;
+      const unsigned dl = (unsigned)__cvta_generic_to_shared(&inL[r][c]);
+      const unsigned dr = (unsigned)__cvta_generic_to_shared(&inR[r][c]);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dl),
+                   "l"(Lb + rowoff + xsrc[u]));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr),
+                   "l"(Rb + rowoff + xsrc[u]));  // the value is the pair's first word
+    }
+  }
+  // per computed column of this lane (cx = lane, and lanes 0, 1 also take 32, 33):
+  // the stage column of tap 0, at the reflected output coordinate
+  int c0[2];
+  bool cok[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int cx = lane + 32 * u, Xr = X0 - 1 + cx;
+    cok[u] = cx < kCx && Xr <= dw;
+    c0[u] = cok[u] ? 2 * (reflect101(Xr, dw) - X0) + 2 : 0;
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   __syncthreads();
   // horizontal taps of every stage row at every computed column
-  for (int q = tid; q < kStY * (kPyrX + 2); q += blockDim.x) {
-    const int r = q / (kPyrX + 2), cx = q - r * (kPyrX + 2);
-    const int Xr = X0 - 1 + cx;
-    if (Xr > dw || 2 * Y0 - 4 + r > h + 1) continue;
-    const int c0 = 2 * (reflect101(Xr, dw) - X0) + 2;  // stage column of tap 0
-    float hl = 0.f, hr = 0.f;
+  for (int r = warp; r < kStY; r += nwarp) {
+    if (2 * Y0 - 4 + r > h + 1) break;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      hl = fmaf(k[i], inL[r][c0 + i], hl);
-      hr = fmaf(k[i], inR[r][c0 + i], hr);
+    for (int u = 0; u < 2; ++u) {
+      if (!cok[u]) continue;
+      float hl = 0.f, hr = 0.f;
+#pragma unroll
+      for (int i = 0; i < 5; ++i) {
+        hl = fmaf(k[i], inL[r][c0[u] + i], hl);
+        hr = fmaf(k[i], inR[r][c0[u] + i], hr);
+      }
+      hL[r][lane + 32 * u] = hl;
+      hR[r][lane + 32 * u] = hr;
     }
-    hL[r][cx] = hl;
-    hR[r][cx] = hr;
   }
   __syncthreads();
   // vertical taps: the downsampled value of every computed cell
-  for (int q = tid; q < (kPyrY + 2) * (kPyrX + 2); q += blockDim.x) {
-    const int cy = q / (kPyrX + 2), cx = q - cy * (kPyrX + 2);
-    const int Xr = X0 - 1 + cx, Yr = Y0 - 1 + cy;
-    if (Xr > dw || Yr > dh) continue;
+  for (int cy = warp; cy < kPyrY + 2; cy += nwarp) {
+    const int Yr = Y0 - 1 + cy;
+    if (Yr > dh) break;
     const int r0 = 2 * (reflect101(Yr, dh) - Y0) + 2;  // stage row of tap 0
-    float accL = 0.f, accR = 0.f;
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-      accL = fmaf(k[j], hL[r0 + j][cx], accL);
-      accR = fmaf(k[j], hR[r0 + j][cx], accR);
+    for (int u = 0; u < 2; ++u) {
+      if (!cok[u]) continue;
+      const int cx = lane + 32 * u;
+      float accL = 0.f, accR = 0.f;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        accL = fmaf(k[j], hL[r0 + j][cx], accL);
+        accR = fmaf(k[j], hR[r0 + j][cx], accR);
+      }
+      sL[cy][cx] = accL;
+      sR[cy][cx] = accR;
     }
-    sL[cy][cx] = accL;
-    sR[cy][cx] = accR;
   }
   __syncthreads();
-  const int cx = 1 + (tid & (kPyrX - 1));
-  for (int cy = 1 + tid / kPyrX; cy <= kPyrY; cy += blockDim.x / kPyrX) {
+  const int cx = 1 + lane;
+  for (int cy = 1 + warp; cy <= kPyrY; cy += nwarp) {
     const int X = X0 + cx - 1, Y = Y0 + cy - 1;
     if (X >= dw || Y >= dh) continue;
     const float dm = sL[cy - 1][cx + 1] - sL[cy - 1][cx - 1];
