@@ -388,6 +388,16 @@ void bdis_plan_destroy(bdis_plan *plan);
  * (bdis_net_weight_count() floats in all), then b[co]. */
 int bdis_net_weight_count(void);
 
+/* Tuning: the kernels of the network's forward convolutions. 1 (default) =
+ * 5th-generation tensor cores (tcgen05: a zero-padded slab of input pixels
+ * and the weights in shared memory, each tap's operand a shifted window of
+ * the slab, accumulator in tensor memory, 128-pixel tiles); 0 = implicit
+ * GEMM on mma.sync (warp-level BF16 MMA). Results agree up to FP32
+ * accumulation order. Inputs too wide for one slab, and the training
+ * kernels, use mma.sync. Process-wide. */
+void bdis_set_net_variant(int tensor_path);
+int bdis_get_net_variant(void);
+
 /* weights: host, bdis_net_weight_count() floats (copied). */
 bdis_status bdis_net_create(int device, const float *weights, bdis_net **out);
 

@@ -30,6 +30,8 @@ from .api import (  # noqa: F401
     get_densify_variant,
     set_pyramid_variant,
     get_pyramid_variant,
+    set_net_variant,
+    get_net_variant,
     prepare_level0,
     pyramid_level,
     search_level,

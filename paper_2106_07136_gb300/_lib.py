@@ -22,7 +22,7 @@ EXPORTED = [
     "bdis_match_static", "bdis_probe_fp32_tflops", "bdis_set_search_variant",
     "bdis_get_search_variant", "bdis_set_search_tiling", "bdis_get_search_tiling",
     "bdis_set_densify_variant", "bdis_get_densify_variant", "bdis_set_pyramid_variant",
-    "bdis_get_pyramid_variant",
+    "bdis_get_pyramid_variant", "bdis_set_net_variant", "bdis_get_net_variant",
     "bdis_plan_create", "bdis_plan_run", "bdis_plan_info",
     "bdis_plan_workspace_bytes", "bdis_plan_destroy", "bdis_match_warm", "bdis_warm_map",
     "bdis_net_weight_count", "bdis_net_create", "bdis_net_forward", "bdis_net_gradient",
@@ -161,6 +161,9 @@ def load():
     lib.bdis_set_pyramid_variant.argtypes = [c_int]
     lib.bdis_set_pyramid_variant.restype = None
     lib.bdis_get_pyramid_variant.restype = c_int
+    lib.bdis_set_net_variant.argtypes = [c_int]
+    lib.bdis_set_net_variant.restype = None
+    lib.bdis_get_net_variant.restype = c_int
     lib.bdis_probe_fp32_tflops.argtypes = [c_int, P(ctypes.c_double), c_void_p]
     lib.bdis_match_static.argtypes = [ip, ip, pp, c_void_p, c_void_p]
     lib.bdis_pack_right.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p]

@@ -275,6 +275,15 @@ def get_pyramid_variant() -> bool:
     return bool(_lib.load().bdis_get_pyramid_variant())
 
 
+def set_net_variant(tensor_path: int):
+    """Proposal network forward convolutions: 1 = tcgen05 kernel (default), 0 = mma.sync kernel."""
+    _lib.load().bdis_set_net_variant(int(tensor_path))
+
+
+def get_net_variant() -> int:
+    return int(_lib.load().bdis_get_net_variant())
+
+
 def probe_fp32_tflops(iterations: int = 1 << 16, stream=None) -> float:
     """Measured FP32 FMA throughput of the current GPU (TFLOP/s)."""
     t = ctypes.c_double()

@@ -12,9 +12,10 @@
 //   d = conv(a5) + b6                               1 channel (padded to 16), level-3 px
 // Activations are NHWC bf16 (channels innermost).
 //
-// Every convolution is an implicit GEMM on mma.sync.m16n8k16 (bf16 in, f32
-// accumulate): rows = pixels, columns = output channels, K = 9 taps x input
-// channels. The data-gradient of a layer is the same kernel run on the
+// Every convolution is an implicit GEMM (bf16 in, f32 accumulate): rows =
+// pixels, columns = output channels, K = 9 taps x input channels. The forward
+// convolutions run on the 5th-generation tensor cores (tcgen05, below) by
+// default, or on mma.sync.m16n8k16; training uses mma.sync. The data-gradient of a layer is the same kernel run on the
 // output gradient with transposed, tap-flipped weights and the previous
 // layer's ReLU mask fused into the store; the weight-gradient is a GEMM with
 // rows = output channels, columns = (tap, input channel), K = pixels,
@@ -191,6 +192,220 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(
         }
       }
   }
+}
+
+// ------------------------------------------------------- conv (tcgen05)
+
+// The same forward convolutions on the 5th-generation tensor cores, as an
+// implicit GEMM without an im2col copy. Pixels are numbered in a padded frame:
+// each image becomes (H + 2 dil) x (W + 2 dil) with zero borders, so a tap
+// (dy, dx) is the constant shift dy dil (W + 2 dil) + dx dil of that
+// numbering. A block (one warpgroup, 128 threads) owns a tile of 128
+// consecutive padded positions and stages, once, the slab of padded positions
+// [tile - s, tile + 127 + s] (s = the largest shift) in shared memory: for each
+// group of 8 channels a plane of slab rows, 16 bytes per row. In the
+// no-swizzle K-major layout that is a run of core matrices (8 rows x 16 bytes,
+// 128 B apart along M), so the A operand of tap t is the slab window starting
+// s + shift(t) rows in (a descriptor start 16 B per row), and the two channel
+// groups of one MMA (K = 16) are one plane apart (the leading offset). B (the
+// COUT x 9 CIN weights) is staged once per block. One thread issues the
+// 9 CIN / 16 MMAs (M 128, N COUT, K 16) into a tensor-memory accumulator and
+// commits them to an mbarrier; every thread then reads its row of D (warp w
+// owns tensor-memory lanes 32 w .. 32 w + 31) and, if its position is a real
+// pixel, writes the layer output. Waits are bounded by the global timer: on a
+// timeout the block writes NaN, frees its tensor memory and returns.
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);  // no swizzle
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait until the mbarrier's phase `parity` has completed, at most ~200 ms
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > 200000000ull) return false;
+  }
+}
+
+// slab rows of a tile: 128 positions plus the largest shift on either side
+__host__ __device__ __forceinline__ int tc_slab_rows(int dil, int W) {
+  return 128 + 2 * (dil * (W + 2 * dil) + dil);
+}
+
+template <int CIN, int COUT>
+int tc_smem_bytes(int dil, int W) {  // the slab and the weights
+  return (CIN / 8) * tc_slab_rows(dil, W) * 16 + (9 * CIN / 8) * (COUT / 8) * 128;
+}
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(128) conv_tc_kernel(
+    const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wt,
+    const float *__restrict__ bias, int dil, int H, int W, int count,
+    void *__restrict__ out) {
+  static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "tile");
+  static_assert(MODE == kFwdRelu || MODE == kFwdLinearF32, "forward only");
+  constexpr int KG = 9 * CIN / 8;  // 8-element k-groups of the weights
+  constexpr int NG = COUT / 8;
+  constexpr int CG = CIN / 8;      // channel groups (slab planes)
+  extern __shared__ __align__(128) uint8_t tc_smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int Wp = W + 2 * dil, Hp = H + 2 * dil;
+  const int NS = tc_slab_rows(dil, W), soff = dil * Wp + dil;
+  const long long planep = (long long)Hp * Wp, totalp = planep * count;
+  uint8_t *Ss = tc_smem, *Bs = tc_smem + CG * NS * 16;  // slab, weights
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // B: weight row co (K = 9 CIN contiguous) -> core (kg, co / 8), row co % 8
+  for (int i = tid; i < COUT * KG; i += 128) {
+    const int co = i / KG, kg = i - co * KG;
+    const uint4 v = *reinterpret_cast<const uint4 *>(wt + (size_t)co * 9 * CIN + kg * 8);
+    *reinterpret_cast<uint4 *>(Bs + ((kg * NG + co / 8) * 8 + co % 8) * 16) = v;
+  }
+  const uint32_t mbar_a = (uint32_t)__cvta_generic_to_shared(&mbar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar_a));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&tmem_slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(slot));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(Ss);
+  const uint32_t b_base = (uint32_t)__cvta_generic_to_shared(Bs);
+  constexpr uint32_t idesc = (1u << 4)                    // D: f32
+                             | (1u << 7) | (1u << 10)     // A, B: bf16, both K-major
+                             | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  // a padded position -> its real pixel index, or -1 on a border or past the end
+  auto real_pixel = [&](long long q) -> long long {
+    if (q < 0 || q >= totalp) return -1;
+    const int b = (int)(q / planep);
+    const int rem = (int)(q - (long long)b * planep);
+    const int y = rem / Wp - dil, x = rem - (rem / Wp) * Wp - dil;
+    if (y < 0 || y >= H || x < 0 || x >= W) return -1;
+    return ((long long)b * H + y) * W + x;
+  };
+  uint32_t parity = 0;
+  bool ok = true;
+  for (long long tile = blockIdx.x; tile * 128 < totalp && ok; tile += gridDim.x) {
+    const long long q0 = tile * 128 - soff;  // padded position of slab row 0
+    for (int i = tid; i < NS; i += 128) {
+      const long long pix = real_pixel(q0 + i);
+      const __nv_bfloat16 *src = pix >= 0 ? in + pix * CIN : in;
+#pragma unroll
+      for (int cg = 0; cg < CG; ++cg)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                         s_base + (cg * NS + i) * 16),
+                     "l"(src + cg * 8), "r"(pix >= 0 ? 16 : 0));
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    const uint32_t sb = s_base;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int row0 = soff + (tap / 3 - 1) * dil * Wp + (tap % 3 - 1) * dil;
+#pragma unroll
+        for (int kk = 0; kk < CIN / 16; ++kk) {
+          const uint64_t ad =
+              umma_smem_desc(sb + (2 * kk * NS + row0) * 16, (uint32_t)NS * 16, 128);
+          const uint64_t bd =
+              umma_smem_desc(b_base + (tap * CG + 2 * kk) * NG * 128, NG * 128, 128);
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(tap | kk));
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+              mbar_a));
+    }
+    ok = mbar_wait(mbar_a, parity);
+    parity ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    float d[COUT];
+    if (ok) {
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+      if constexpr (COUT == 32) {
+        uint32_t r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+              "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+              "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+              "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) d[c] = __uint_as_float(r[c]);
+      } else {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];\n"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) d[c] = __uint_as_float(r[c]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < COUT; ++c) d[c] = __int_as_float(0x7fc00000);
+    }
+    const long long p = real_pixel(tile * 128 + tid);
+    if (p >= 0) {
+      if constexpr (MODE == kFwdRelu) {
+        uint32_t pk[COUT / 2];
+#pragma unroll
+        for (int c = 0; c < COUT; c += 2)
+          pk[c / 2] = pack_bf16(fmaxf(d[c] + bias[c], 0.f), fmaxf(d[c + 1] + bias[c + 1], 0.f));
+        uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<__nv_bfloat16 *>(out) + p * COUT);
+#pragma unroll
+        for (int v = 0; v < COUT / 8; ++v)
+          o[v] = make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+      } else {
+        float *o = reinterpret_cast<float *>(out) + p * COUT;
+#pragma unroll
+        for (int c = 0; c < COUT; ++c) o[c] = d[c] + bias[c];
+      }
+    }
+    // every thread has read D and the MMAs are done: the slab and D may be rewritten
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");  // none left in flight (timeout exit)
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem));
 }
 
 // ------------------------------------------------------- weight gradient
@@ -449,6 +664,34 @@ cudaError_t pack_all(bdis_net *n, cudaStream_t st) {
 }
 
 int g_sms = 0;
+int g_net_tc = 1;  // forward convolutions: 1 = tcgen05 kernel (default), 0 = mma.sync kernel
+
+// Dynamic shared memory of the tcgen05 kernel is exactly its slab and the
+// weights (19 to 72 KB for 80-pixel-wide level-3 inputs), so up to four
+// blocks share an SM: some stage their slab while others multiply. (Double-
+// buffering the slab within a block measured slower: it halves the blocks per
+// SM.) Images too wide for one slab (over ~200 KB) take the mma.sync kernel.
+constexpr int kTcSmemMax = 200 * 1024;
+
+template <int CIN, int COUT, int MODE>
+bool conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, int dil,
+             int H, int W, long long total, void *out, cudaStream_t st) {
+  const int smem = tc_smem_bytes<CIN, COUT>(dil, W);
+  if (smem > kTcSmemMax) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, MODE>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax);
+    attr = true;
+  }
+  const int count = (int)(total / ((long long)H * W));
+  const long long totalp = (long long)(H + 2 * dil) * (W + 2 * dil) * count;
+  const long long tiles = (totalp + 127) / 128;
+  const int per_sm = std::max(1, std::min(4, (227 * 1024) / (smem + 1024)));
+  const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)per_sm * g_sms);
+  conv_tc_kernel<CIN, COUT, MODE><<<grid, 128, smem, st>>>(in, wt, bias, dil, H, W, count, out);
+  return true;
+}
 
 template <int CIN, int COUT, int MODE>
 void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, int dil, int H,
@@ -458,6 +701,9 @@ void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, i
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_sms <= 0) g_sms = 152;
+  }
+  if constexpr (MODE == kFwdRelu || MODE == kFwdLinearF32) {
+    if (g_net_tc && conv_tc<CIN, COUT, MODE>(in, wt, bias, dil, H, W, total, out, st)) return;
   }
   const long long tiles = (total + 255) / 256;  // 64 pixels x 4 m-tiles per block tile
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)g_sms * 3);
@@ -554,6 +800,10 @@ bdis_status net_forward_on(bdis_net *n, const float *L, const float *R, int r_st
 extern "C" {
 
 int bdis_net_weight_count(void) { return kMasterCount; }
+
+void bdis_set_net_variant(int tensor_path) { g_net_tc = tensor_path ? 1 : 0; }
+
+int bdis_get_net_variant(void) { return g_net_tc; }
 
 bdis_status bdis_net_create(int device, const float *weights, bdis_net **out) {
   if (!out || !weights) return BDIS_E_INVALID_ARG;

@@ -52,6 +52,31 @@ def test_forward_matches_oracle(data):
     net.close()
 
 
+def test_forward_on_tcgen05_matches_mma_and_oracle(data):
+    """The tcgen05 forward kernels (operands in shared memory, accumulator in
+    tensor memory) against the mma.sync kernels and the FP64 oracle. The batch
+    is tiled 8x so that each block runs several 128-pixel tiles (alternating
+    mbarrier phases); 24 x 60 x 80 pixels end in a partial tile."""
+    Lp, Rp, _ = data
+    w = bd.net_init_weights(seed=3)
+    net = bd.ProposalNet(w)
+    L8, R8 = Lp.repeat(8, 1, 1).contiguous(), Rp.repeat(8, 1, 1, 1).contiguous()
+    old = bd.get_net_variant()
+    try:
+        bd.set_net_variant(0)
+        ref_mma = host(net.forward(L8, R8))
+        bd.set_net_variant(1)
+        out = host(net.forward(L8, R8))
+    finally:
+        bd.set_net_variant(old)
+    assert np.all(np.isfinite(out))
+    ref = no.forward(host(Lp), host(Rp)[..., 0], w)
+    for k in range(8):
+        assert rel(out[3 * k:3 * k + 3], ref) < 3e-2, (k, rel(out[3 * k:3 * k + 3], ref))
+    assert rel(out, ref_mma) < 1e-2, rel(out, ref_mma)
+    net.close()
+
+
 def test_gradient_matches_oracle(data):
     Lp, Rp, gt = data
     w = bd.net_init_weights(seed=4)
