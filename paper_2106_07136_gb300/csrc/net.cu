@@ -678,11 +678,18 @@ bool conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias
              int H, int W, long long total, void *out, cudaStream_t st) {
   const int smem = tc_smem_bytes<CIN, COUT>(dil, W);
   if (smem > kTcSmemMax) return false;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, MODE>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemMax);
-    attr = true;
+  // the shared-memory limit is a per-device attribute of the kernel
+  static uint64_t attr_set = 0;  // bit d: set on device d
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !(attr_set >> dev & 1u)) {
+    if (cudaFuncSetAttribute(conv_tc_kernel<CIN, COUT, MODE>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kTcSmemMax) != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it, the mma.sync kernel runs instead
+      return false;
+    }
+    if (dev < 64) attr_set |= 1ull << dev;
   }
   const int count = (int)(total / ((long long)H * W));
   const long long totalp = (long long)(H + 2 * dil) * (W + 2 * dil) * count;

@@ -77,6 +77,30 @@ def test_forward_on_tcgen05_matches_mma_and_oracle(data):
     net.close()
 
 
+@pytest.mark.parametrize("shape", [(2, 135, 240), (1, 40, 400)])
+def test_forward_on_tcgen05_wide_inputs(shape):
+    """Level-3 inputs as wide as a 1920x1080 pair's (240 px: the largest
+    slabs, 154 KB of shared memory at dilation 4), and wider still (400 px:
+    the dilation-4 layers exceed the slab limit and run on mma.sync while the
+    others run on tcgen05). Both agree with the all-mma.sync forward."""
+    b, h, w = shape
+    rng = np.random.default_rng(w)
+    L = dev(rng.uniform(0, 255, shape).astype(np.float32))
+    R = dev(rng.uniform(0, 255, shape).astype(np.float32))
+    net = bd.ProposalNet(bd.net_init_weights(seed=7))
+    old = bd.get_net_variant()
+    try:
+        bd.set_net_variant(0)
+        ref = host(net.forward(L, R))
+        bd.set_net_variant(1)
+        out = host(net.forward(L, R))
+    finally:
+        bd.set_net_variant(old)
+    assert np.all(np.isfinite(out))
+    assert rel(out, ref) < 1e-2, rel(out, ref)
+    net.close()
+
+
 def test_gradient_matches_oracle(data):
     Lp, Rp, gt = data
     w = bd.net_init_weights(seed=4)
