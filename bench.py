@@ -462,7 +462,24 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     lat.sort()
     res["latency"] = {"batch": 1, "p50_ms": lat[len(lat) // 2],
                       "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                      "iters": len(lat)}
+                      "iters": len(lat), "path": "bdis_match"}
+    # the same single pair replayed as one CUDA graph (bdis_plan_run)
+    plan = bd.Plan([(l1.unsqueeze(0), r1.unsqueeze(0), o1.unsqueeze(0))], params,
+                   autotune=False, device=device)
+    for _ in range(20):
+        plan.run(stream)
+    stream.synchronize()
+    glat = []
+    for _ in range(args.latency_iters):
+        t0 = time.perf_counter()
+        plan.run(stream)
+        stream.synchronize()
+        glat.append(1e3 * (time.perf_counter() - t0))
+    plan.close()
+    glat.sort()
+    res["latency_graph"] = {"batch": 1, "p50_ms": glat[len(glat) // 2],
+                            "p99_ms": glat[min(len(glat) - 1, int(0.99 * len(glat)))],
+                            "iters": len(glat), "path": "bdis_plan_run (one CUDA graph)"}
     # patch 12 variant of the same workload
     p12 = bd.default_params(**params_kw(12))
     out = torch.empty((B, H, W), dtype=torch.float32, device=device)
