@@ -1,6 +1,6 @@
 """Train the learned coarse proposal on the GPU with the library's kernels.
 
-  python -m paper_2106_07136_gb300.train_proposal [--pairs 50000] [--batch 64]
+  python -m paper_2106_07136_gb300.train_proposal [--pairs 50000] [--batch 64] [--epochs 4]
          [--out paper_2106_07136_gb300/weights/proposal.bdisnet]
 
 Each step draws a batch of seeded surgical-like 640x480 pairs on the device
@@ -38,14 +38,17 @@ def level3(L, R):
     return Lp, Rp
 
 
-def train(pairs=50000, batch=64, lr=2e-3, lr_end=1e-4, seed=0, log_every=100, device="cuda"):
+def train(pairs=50000, batch=64, lr=2e-3, lr_end=1e-4, seed=0, log_every=100, device="cuda",
+          epochs=1):
+    """`epochs` passes over the same `pairs` seeded pairs, one cosine schedule."""
     gen = TorchCfg2Generator(device=device)
     net = bd.ProposalNet(bd.net_init_weights(seed=seed))
-    steps = max(1, pairs // batch)
+    per_epoch = max(1, pairs // batch)
+    steps = per_epoch * max(1, epochs)
     hist = []
     t0 = time.perf_counter()
     for s in range(steps):
-        L, R, gt = gen.batch(TRAIN_SEED + s, batch)
+        L, R, gt = gen.batch(TRAIN_SEED + s % per_epoch, batch)
         L3, R3 = level3(L, R)
         label = (gt[:, ::8, ::8] / 8.0).contiguous()
         f = s / max(steps - 1, 1)
@@ -65,12 +68,14 @@ def main():
     ap.add_argument("--pairs", type=int, default=50000)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--out", default=DEFAULT_OUT)
     a = ap.parse_args()
-    w, hist, secs = train(a.pairs, a.batch, a.lr)
+    w, hist, secs = train(a.pairs, a.batch, a.lr, epochs=a.epochs)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     note = (f"trained on {a.pairs} seeded 640x480 surgical-like pairs (seeds from {TRAIN_SEED}), "
-            f"batch {a.batch}, Adam lr {a.lr} cosine to 1e-4, Huber loss on level-3 ground truth; "
+            f"{a.epochs} epoch(s), batch {a.batch}, Adam lr {a.lr} cosine to 1e-4, Huber loss on "
+            f"level-3 ground truth; "
             f"final loss {hist[-1]:.4f}, {secs:.1f}s")
     bd.save_net_weights(a.out, w, note)
     print(note)
