@@ -226,6 +226,10 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     for (int r = 0; r < PS; ++r) gc[j][r] = 0.f;
   float H = 0.f, invH = 0.f, gcT = 0.f;
   int n = 0;
+  // Within one integer base the interpolated sum is linear in the fraction:
+  // sum gc (R + t dR) = A + t B, A = sum gc R, B = sum gc dR at base kc.
+  float A = 0.f, B = 0.f;
+  int kc = INT_MIN;
   for (int it = 0; it < a.iters; ++it) {
     if (__all_sync(kFull, frozen)) break;  // every patch of the warp has stopped
     int kd;
@@ -281,18 +285,29 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
       flat = true;
     }
     if (it == 0) rows.ready();  // staged rows (if any) arrive while the sums above load
-    // four partial sums break the FMA dependency chain. No branches: an invalid
-    // column has gc = 0 and reads a clamped (readable) column, so it adds
-    // exactly 0; a frozen patch's sum is not used.
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    // A and B change only with the base or the centred gradient. When some
+    // patch of the warp needs them anew the whole warp recomputes (a patch
+    // whose base and gradient did not change gets the same sums again, so the
+    // result does not depend on its neighbours). No branches inside: an
+    // invalid column has gc = 0 and reads a clamped (readable) column, so it
+    // adds exactly 0; a frozen patch's sums are not used.
+    if (__any_sync(kFull, !frozen && (need || kd != kc))) {
+      float sa[2] = {0.f, 0.f}, sb[2] = {0.f, 0.f};
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      const auto p = rows.col_clamped(ib + j);
+      for (int j = 0; j < CPL; ++j) {
+        const auto p = rows.col_clamped(ib + j);
 #pragma unroll
-      for (int r = 0; r < PS; ++r)
-        acc[r & 3] = fmaf(gc[j][r], lerp_packed(rows.ld(p, r), t), acc[r & 3]);
+        for (int r = 0; r < PS; ++r) {
+          const float2 q = rows.ld(p, r);
+          sa[r & 1] = fmaf(gc[j][r], q.x, sa[r & 1]);
+          sb[r & 1] = fmaf(gc[j][r], q.y, sb[r & 1]);
+        }
+      }
+      A = group_sum<G>(sa[0] + sa[1]);
+      B = group_sum<G>(sb[0] + sb[1]);
+      kc = kd;
     }
-    const float Ssum = group_sum<G>((acc[0] + acc[1]) + (acc[2] + acc[3]));
+    const float Ssum = fmaf(t, B, A);
     if (!frozen) {
       last_step = (Ssum - gcT) * invH;
       D += last_step;
@@ -348,30 +363,83 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
   for (int j = 0; j < CPL; ++j)
     cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) - __ldg(Lc + j) : 0.f;
   float S1[S][CPL], S2[S][CPL];
+  if constexpr (CPL % 2 == 0) {
+    // Columns j and j + 1 take the same operations, so each pair runs as one
+    // packed f32x2 instruction (per component the same rounding as the scalar
+    // fadd / fma): half the issue slots for the residuals and both sums.
+    float2 P1[S][CPL / 2], P2[S][CPL / 2];
 #pragma unroll
-  for (int i = 0; i < S; ++i)
+    for (int i = 0; i < S; ++i)
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) S1[i][j] = S2[i][j] = 0.f;
+      for (int jp = 0; jp < CPL / 2; ++jp) P1[i][jp] = P2[i][jp] = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int r = 0; r < PS; ++r) {
-    float Lt[CPL + 2], Lh[CPL + 2];
+    for (int r = 0; r < PS; ++r) {
+      float Lt[CPL + 2], Lh[CPL + 2];
 #pragma unroll
-    for (int m = 0; m < CPL + 2; ++m) {
-      const float2 q = need[m] ? rows.ld(rows.col(ib - 1 + m), r) : make_float2(0.f, 0.f);
-      Lt[m] = lerp_packed(q, t);
-      Lh[m] = lerp_packed(q, th);
+      for (int m = 0; m < CPL + 2; ++m) {
+        const float2 q = need[m] ? rows.ld(rows.col(ib - 1 + m), r) : make_float2(0.f, 0.f);
+        Lt[m] = lerp_packed(q, t);
+        Lh[m] = lerp_packed(q, th);
+      }
+#pragma unroll
+      for (int jp = 0; jp < CPL / 2; ++jp) {
+        const int j = 2 * jp;
+        // minus (template + shift): -(T + cs) rounds to exactly -fl(T + cs)
+        float tn[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          tn[e] = -(vc[j + e] ? __ldg(Lc + (size_t)r * w + j + e) : 0.f) - cs[j + e];
+        const float2 Tn = make_float2(tn[0], tn[1]);
+        // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1
+        const float2 d[S] = {
+            __fadd2_rn(make_float2(Lt[j + 2], Lt[j + 3]), Tn),
+            __fadd2_rn(hi ? make_float2(Lh[j + 2], Lh[j + 3]) : make_float2(Lh[j + 1], Lh[j + 2]),
+                       Tn),
+            __fadd2_rn(make_float2(Lt[j + 1], Lt[j + 2]), Tn),
+            __fadd2_rn(hi ? make_float2(Lh[j + 1], Lh[j + 2]) : make_float2(Lh[j], Lh[j + 1]), Tn),
+            __fadd2_rn(make_float2(Lt[j], Lt[j + 1]), Tn)};
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          P1[i][jp] = __fadd2_rn(P1[i][jp], d[i]);
+          P2[i][jp] = __ffma2_rn(d[i], d[i], P2[i][jp]);
+        }
+      }
     }
 #pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      const float Tj = (vc[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f) + cs[j];  // template + shift
-      // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1.
-      // An invalid column's sums (finite: its pairs read as 0) are not merged below.
-      const float d[S] = {Lt[j + 2] - Tj, (hi ? Lh[j + 2] : Lh[j + 1]) - Tj, Lt[j + 1] - Tj,
-                          (hi ? Lh[j + 1] : Lh[j]) - Tj, Lt[j] - Tj};
+    for (int i = 0; i < S; ++i)
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
-        S1[i][j] += d[i];
-        S2[i][j] = fmaf(d[i], d[i], S2[i][j]);
+      for (int jp = 0; jp < CPL / 2; ++jp) {
+        S1[i][2 * jp] = P1[i][jp].x;
+        S1[i][2 * jp + 1] = P1[i][jp].y;
+        S2[i][2 * jp] = P2[i][jp].x;
+        S2[i][2 * jp + 1] = P2[i][jp].y;
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) S1[i][j] = S2[i][j] = 0.f;
+#pragma unroll
+    for (int r = 0; r < PS; ++r) {
+      float Lt[CPL + 2], Lh[CPL + 2];
+#pragma unroll
+      for (int m = 0; m < CPL + 2; ++m) {
+        const float2 q = need[m] ? rows.ld(rows.col(ib - 1 + m), r) : make_float2(0.f, 0.f);
+        Lt[m] = lerp_packed(q, t);
+        Lh[m] = lerp_packed(q, th);
+      }
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        const float Tj = (vc[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f) + cs[j];  // template + shift
+        // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1.
+        // An invalid column's sums (finite: its pairs read as 0) are not merged below.
+        const float d[S] = {Lt[j + 2] - Tj, (hi ? Lh[j + 2] : Lh[j + 1]) - Tj, Lt[j + 1] - Tj,
+                            (hi ? Lh[j + 1] : Lh[j]) - Tj, Lt[j] - Tj};
+#pragma unroll
+        for (int i = 0; i < S; ++i) {
+          S1[i][j] += d[i];
+          S2[i][j] = fmaf(d[i], d[i], S2[i][j]);
+        }
       }
     }
   }

@@ -68,13 +68,19 @@ def decision_margins(o, ps):
     return saddle, div, edge
 
 
-def oracle_unstable(orc, o, params, eps=1e-6, runs=2):
+def oracle_unstable(orc, o, params, eps=1e-6, runs=2, with_steps=False):
     """Patches whose oracle result is itself ill-conditioned: the keep/drop
     decision changes, or D* moves by more than 1e-4 px, when the level's
     planes get eps gray levels of noise and its coarse disparities a relative
-    perturbation of 1e-6 (one float32 rounding)."""
+    perturbation of 1e-6 (one float32 rounding).
+
+    with_steps: also return the patches whose update count (R12) moves by more
+    than one under the same perturbation. Where the updates hover at the
+    1e-4 px stop for several steps, when the patch stops is not fixed at
+    float32 resolution even though D* is."""
     dropped = (o["flags"] & DROP) != 0
     bad = np.zeros(dropped.shape, dtype=bool)
+    step_bad = np.zeros(dropped.shape, dtype=bool)
     for seed in range(runs):
         rng = np.random.default_rng(100 + seed)
         L = o["L"] + rng.normal(0, eps, o["L"].shape)
@@ -86,7 +92,8 @@ def oracle_unstable(orc, o, params, eps=1e-6, runs=2):
         d2 = (p2["flags"] & DROP) != 0
         bad |= d2 != dropped
         bad |= ~dropped & ~d2 & (np.abs(p2["d_star"] - o["d_star"]) > 1e-4)
-    return bad
+        step_bad |= np.abs(p2["steps"].astype(np.int64) - o["steps"]) > 1
+    return (bad, step_bad) if with_steps else bad
 
 
 def explained_flag_mismatch(o, g_flags, ps, unstable, tol=1e-4):

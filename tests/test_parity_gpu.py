@@ -127,8 +127,9 @@ def _search_stage(orc, pair, kw, levels):
         g = bd.search_level(dev(o["L"]), bd.pack_right(dev(o["R"])), dev(o["G"]), coarse, gp)
         g = {k: host(v)[0] for k, v in g.items()}
         np.testing.assert_allclose(g["u_init"], o["u_init"], atol=1e-4)
-        unstable = oracle_unstable(orc, o, op)
+        unstable, step_unstable = oracle_unstable(orc, o, op, with_steps=True)
         assert unstable.mean() < 2e-3, (lvl, int(unstable.sum()))
+        assert step_unstable.mean() < 1e-3, (lvl, int(step_unstable.sum()))
         diff, explained = explained_flag_mismatch(o, g["flags"], gp.patch_size, unstable)
         assert explained.all(), (lvl, np.argwhere(~explained)[:5])
         assert diff.mean() < 2e-3, (lvl, int(diff.sum()))
@@ -145,8 +146,9 @@ def _search_stage(orc, pair, kw, levels):
         dropped = ~diff & ((o["flags"] & DROP) != 0)
         assert np.all(g["weight"][dropped] == 0.0)
         # updates taken (R12): equal except where an update lands within
-        # rounding of the 1e-4 px stop, and then by one step
-        both = ~diff & ~unstable
+        # rounding of the 1e-4 px stop, and then by one step; patches whose
+        # oracle update count is itself ill-conditioned are left out
+        both = ~diff & ~unstable & ~step_unstable
         dsteps = g["steps"][both].astype(int) - o["steps"][both]
         assert np.abs(dsteps).max() <= 1, (lvl, int(np.abs(dsteps).max()))
         assert (dsteps == 0).mean() >= 0.97, (lvl, float((dsteps == 0).mean()))
