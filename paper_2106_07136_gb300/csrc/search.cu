@@ -110,7 +110,7 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
   if (nc == 0) {
     if (!(flags & kFlagDiverged)) flags |= kFlagEmpty;  // a diverged patch reads no window
   } else {
-    post = pc / z;  // pc = exp(-(Ec - Emin) / kappa), the centre's term of z
+    post = __fdividef(pc, z);  // pc = exp(-(Ec - Emin) / kappa), the centre's term of z; z in [1, s]
     if (a.s > 1 && Eo < Ec - kSaddleTau * fmaxf(Ec, 1.f)) flags |= kFlagSaddle;
   }
   if (nvalid < a.nmin_valid) flags |= kFlagGamma;
@@ -244,45 +244,90 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
       code |= (unsigned)v[j] << j;
     }
     const bool need_lane = !frozen && (!have || code != prev);
-    const bool need = (__ballot_sync(kFull, need_lane) & gbits) != 0u;  // whole group recomputes
-    if (__any_sync(kFull, need)) {
+    const unsigned need_bits = __ballot_sync(kFull, need_lane);
+    const bool need = (need_bits & gbits) != 0u;  // whole group recomputes
+    if (need_bits != 0u) {
       // sums of the new valid set: centred gradient, Hessian, template term
-      float g[CPL][PS];
-      float sg = 0.f;
+      float hh, ct;
+      int nn;
+      if constexpr (CPL % 2 == 0) {
+        // column pairs as packed f32x2; an invalid column's term is (g - mg) * 0
+        float2 g2[CPL / 2][PS], s2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < CPL; ++j)
+        for (int jp = 0; jp < CPL / 2; ++jp)
 #pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
-          sg += g[j][r];
+          for (int r = 0; r < PS; ++r) {
+            float ge[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+              ge[e] = v[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
+            g2[jp][r] = make_float2(ge[0], ge[1]);
+            s2 = __fadd2_rn(s2, g2[jp][r]);
+          }
+        const float sg = group_sum<G>(s2.x + s2.y);
+        nn = PS * (int)group_sum<G>((float)__popc(code));
+        const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
+        const float2 nmg = make_float2(-mg, -mg);
+        float2 h2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int jp = 0; jp < CPL / 2; ++jp) {
+          const float2 m2 = make_float2(v[2 * jp] ? 1.f : 0.f, v[2 * jp + 1] ? 1.f : 0.f);
+#pragma unroll
+          for (int r = 0; r < PS; ++r) {
+            const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2);
+            if (need) {
+              gc[2 * jp][r] = q.x;
+              gc[2 * jp + 1][r] = q.y;
+            }
+            float te[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+              te[e] = act[2 * jp + e] ? __ldg(Lc + (size_t)r * w + 2 * jp + e) : 0.f;
+            h2 = __ffma2_rn(q, q, h2);
+            c2 = __ffma2_rn(q, make_float2(te[0], te[1]), c2);
+          }
         }
-      sg = group_sum<G>(sg);
-      const int nn = PS * (int)group_sum<G>((float)__popc(code));
-      const float mg = (a.normalize && nn > 0) ? sg / (float)nn : 0.f;
-      float hh = 0.f, ct = 0.f;
+        hh = h2.x + h2.y;
+        ct = c2.x + c2.y;
+      } else {
+        float g[CPL][PS];
+        float sg = 0.f;
 #pragma unroll
-      for (int j = 0; j < CPL; ++j)
+        for (int j = 0; j < CPL; ++j)
 #pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          const float q = v[j] ? g[j][r] - mg : 0.f;
-          if (need) gc[j][r] = q;
-          hh = fmaf(q, q, hh);
-          ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
-        }
+          for (int r = 0; r < PS; ++r) {
+            g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
+            sg += g[j][r];
+          }
+        sg = group_sum<G>(sg);
+        nn = PS * (int)group_sum<G>((float)__popc(code));
+        const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
+        hh = 0.f;
+        ct = 0.f;
+#pragma unroll
+        for (int j = 0; j < CPL; ++j)
+#pragma unroll
+          for (int r = 0; r < PS; ++r) {
+            const float q = v[j] ? g[j][r] - mg : 0.f;
+            if (need) gc[j][r] = q;
+            hh = fmaf(q, q, hh);
+            ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
+          }
+      }
       hh = group_sum<G>(hh);
       ct = group_sum<G>(ct);
-      if (need) {
+      if (need) {  // implies not frozen (frozen is the same in every lane of a group)
         H = hh;
-        invH = hh > 0.f ? 1.f / hh : 0.f;
+        invH = hh > 0.f ? __fdividef(1.f, hh) : 0.f;  // hh is far below 2^126
         gcT = ct;
         n = nn;
         prev = code;
         have = true;
+        if (n == 0 || H <= kFlatEps * (float)n) {  // H and n change only here
+          frozen = true;
+          flat = true;
+        }
       }
-    }
-    if (!frozen && (n == 0 || H <= kFlatEps * (float)n)) {
-      frozen = true;
-      flat = true;
     }
     if (it == 0) rows.ready();  // staged rows (if any) arrive while the sums above load
     // A and B change only with the base or the centred gradient. When some
@@ -444,7 +489,7 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     }
   }
   const bool write = live && c == 0;
-  const float inv_nc = nc > 0 ? 1.f / (float)nc : 0.f;
+  const float inv_nc = nc > 0 ? __fdividef(1.f, (float)nc) : 0.f;
   float E[S];
 #pragma unroll
   for (int i = 0; i < S; ++i) {
@@ -470,11 +515,11 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     Emin = fminf(Emin, E[i]);
     if (i != HALF) Eo = fminf(Eo, E[i]);
   }
-  const float nik = -1.f / a.kappa;
+  const float nik = -1.4426950408889634f / a.kappa;  // exp(x / -kappa) = 2^(x log2(e) / -kappa)
   float z = 0.f, pc = 0.f;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
-    const float ex = expf((E[i] - Emin) * nik);
+    const float ex = exp2f((E[i] - Emin) * nik);
     z += ex;
     if (i == HALF) pc = ex;
   }
