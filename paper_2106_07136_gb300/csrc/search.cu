@@ -195,6 +195,165 @@ struct TileRows {
   }
 };
 
+// Inverse-search state of one patch (the group's lanes hold the same scalars;
+// gc is the lane's columns of the centred gradient).
+template <int PS, int CPL>
+struct PatchState {
+  float D, last_step;
+  bool frozen, flat;
+  int steps;
+  unsigned prev;  // valid-column code the sums below were taken over
+  float gc[CPL][PS];
+  float H, invH, gcT;
+  int n;
+  // Within one integer base the interpolated sum is linear in the fraction:
+  // sum gc (R + t dR) = A + t B, A = sum gc R, B = sum gc dR at base kc.
+  float A, B;
+  int kc;
+};
+
+// One update of Eq. 1 for every patch of the warp. FIRST: the first update,
+// where every patch computes its sums (no votes, no predicated stores).
+template <int PS, int CPL, bool FIRST, class Rows>
+__device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &rows,
+                                            PatchState<PS, CPL> &st, const bool (&act)[CPL],
+                                            int xl, const float *Lc, const float *Gc,
+                                            unsigned gbits, float u0) {
+  constexpr int LANES = (PS + CPL - 1) / CPL;
+  constexpr int G = pow2_at_least(LANES);
+  const int w = a.w;
+  int kd;
+  float t;
+  split_disp(st.D, kd, t);
+  const int ib = xl + kd;
+  bool v[CPL];
+  unsigned code = 0u;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    v[j] = act[j] && sample_ok(ib + j, t, w);
+    code |= (unsigned)v[j] << j;
+  }
+  // the first step computes every patch's sums; later ones only where the
+  // valid run changed (the whole group recomputes)
+  unsigned need_bits = kFull;
+  if constexpr (!FIRST) need_bits = __ballot_sync(kFull, !st.frozen && code != st.prev);
+  const bool need = FIRST || (need_bits & gbits) != 0u;
+  if (FIRST || need_bits != 0u) {
+    // sums of the new valid set: centred gradient, Hessian, template term
+    float hh, ct;
+    int nn;
+    if constexpr (CPL % 2 == 0) {
+      // column pairs as packed f32x2; an invalid column's term is (g - mg) * 0
+      float2 g2[CPL / 2][PS], s2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jp = 0; jp < CPL / 2; ++jp)
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+          float ge[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e)
+            ge[e] = v[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
+          g2[jp][r] = make_float2(ge[0], ge[1]);
+          s2 = __fadd2_rn(s2, g2[jp][r]);
+        }
+      const float sg = group_sum<G>(s2.x + s2.y);
+      nn = PS * (int)group_sum<G>((float)__popc(code));
+      const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
+      const float2 nmg = make_float2(-mg, -mg);
+      float2 h2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jp = 0; jp < CPL / 2; ++jp) {
+        const float2 m2 = make_float2(v[2 * jp] ? 1.f : 0.f, v[2 * jp + 1] ? 1.f : 0.f);
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+          const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2);
+          if (need) {
+            st.gc[2 * jp][r] = q.x;
+            st.gc[2 * jp + 1][r] = q.y;
+          }
+          float te[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e)
+            te[e] = act[2 * jp + e] ? __ldg(Lc + (size_t)r * w + 2 * jp + e) : 0.f;
+          h2 = __ffma2_rn(q, q, h2);
+          c2 = __ffma2_rn(q, make_float2(te[0], te[1]), c2);
+        }
+      }
+      hh = h2.x + h2.y;
+      ct = c2.x + c2.y;
+    } else {
+      float g[CPL][PS];
+      float sg = 0.f;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j)
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+          g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
+          sg += g[j][r];
+        }
+      sg = group_sum<G>(sg);
+      nn = PS * (int)group_sum<G>((float)__popc(code));
+      const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
+      hh = 0.f;
+      ct = 0.f;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j)
+#pragma unroll
+        for (int r = 0; r < PS; ++r) {
+          const float q = v[j] ? g[j][r] - mg : 0.f;
+          if (need) st.gc[j][r] = q;
+          hh = fmaf(q, q, hh);
+          ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
+        }
+    }
+    hh = group_sum<G>(hh);
+    ct = group_sum<G>(ct);
+    if (need) {  // implies not st.frozen (st.frozen is the same in every lane of a group)
+      st.H = hh;
+      st.invH = hh > 0.f ? __fdividef(1.f, hh) : 0.f;  // hh is far below 2^126
+      st.gcT = ct;
+      st.n = nn;
+      st.prev = code;
+      if (st.n == 0 || st.H <= kFlatEps * (float)st.n) {  // st.H and st.n change only here
+        st.frozen = true;
+        st.flat = true;
+      }
+    }
+  }
+  if constexpr (FIRST) rows.ready();  // staged rows (if any) arrive while the sums above load
+  // st.A and st.B change only with the base or the centred gradient. When some
+  // patch of the warp needs them anew the whole warp recomputes (a patch
+  // whose base and gradient did not change gets the same sums again, so the
+  // result does not depend on its neighbours). No branches inside: an
+  // invalid column has st.gc = 0 and reads a clamped (readable) column, so it
+  // adds exactly 0; a st.frozen patch's sums are not used.
+  if (FIRST || __any_sync(kFull, !st.frozen && (need || kd != st.kc))) {
+    float sa[2] = {0.f, 0.f}, sb[2] = {0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const auto p = rows.col_clamped(ib + j);
+#pragma unroll
+      for (int r = 0; r < PS; ++r) {
+        const float2 q = rows.ld(p, r);
+        sa[r & 1] = fmaf(st.gc[j][r], q.x, sa[r & 1]);
+        sb[r & 1] = fmaf(st.gc[j][r], q.y, sb[r & 1]);
+      }
+    }
+    st.A = group_sum<G>(sa[0] + sa[1]);
+    st.B = group_sum<G>(sb[0] + sb[1]);
+    st.kc = kd;
+  }
+  const float Ssum = fmaf(t, st.B, st.A);
+  if (!st.frozen) {
+    st.last_step = (Ssum - st.gcT) * st.invH;
+    st.D += st.last_step;
+    ++st.steps;
+    // non-finite, or left the search range (dropped below), or converged
+    if (!isfinite(st.D) || fabsf(st.D - u0) > (float)PS || fabsf(st.last_step) < kStepTol)
+      st.frozen = true;
+  }
+}
+
 template <int PS, int CPL, class Rows>
 __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &rows, long long k,
                                             bool live, int c, unsigned gbits, int b, int x0,
@@ -215,153 +374,21 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
   // sums of a new valid run and in the window, not held through the steps.
 
   // ---- inverse-search iterations (Eq. 1)
-  float D = u0, last_step = 0.f;
-  bool frozen = false, flat = false, have = false;
-  int steps = 0;
-  unsigned prev = 0u;
-  float gc[CPL][PS];
-#pragma unroll
-  for (int j = 0; j < CPL; ++j)
-#pragma unroll
-    for (int r = 0; r < PS; ++r) gc[j][r] = 0.f;
-  float H = 0.f, invH = 0.f, gcT = 0.f;
-  int n = 0;
-  // Within one integer base the interpolated sum is linear in the fraction:
-  // sum gc (R + t dR) = A + t B, A = sum gc R, B = sum gc dR at base kc.
-  float A = 0.f, B = 0.f;
-  int kc = INT_MIN;
-  for (int it = 0; it < a.iters; ++it) {
-    if (__all_sync(kFull, frozen)) break;  // every patch of the warp has stopped
-    int kd;
-    float t;
-    split_disp(D, kd, t);
-    const int ib = xl + kd;
-    bool v[CPL];
-    unsigned code = 0u;
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      v[j] = act[j] && sample_ok(ib + j, t, w);
-      code |= (unsigned)v[j] << j;
-    }
-    const bool need_lane = !frozen && (!have || code != prev);
-    const unsigned need_bits = __ballot_sync(kFull, need_lane);
-    const bool need = (need_bits & gbits) != 0u;  // whole group recomputes
-    if (need_bits != 0u) {
-      // sums of the new valid set: centred gradient, Hessian, template term
-      float hh, ct;
-      int nn;
-      if constexpr (CPL % 2 == 0) {
-        // column pairs as packed f32x2; an invalid column's term is (g - mg) * 0
-        float2 g2[CPL / 2][PS], s2 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int jp = 0; jp < CPL / 2; ++jp)
-#pragma unroll
-          for (int r = 0; r < PS; ++r) {
-            float ge[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e)
-              ge[e] = v[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
-            g2[jp][r] = make_float2(ge[0], ge[1]);
-            s2 = __fadd2_rn(s2, g2[jp][r]);
-          }
-        const float sg = group_sum<G>(s2.x + s2.y);
-        nn = PS * (int)group_sum<G>((float)__popc(code));
-        const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
-        const float2 nmg = make_float2(-mg, -mg);
-        float2 h2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int jp = 0; jp < CPL / 2; ++jp) {
-          const float2 m2 = make_float2(v[2 * jp] ? 1.f : 0.f, v[2 * jp + 1] ? 1.f : 0.f);
-#pragma unroll
-          for (int r = 0; r < PS; ++r) {
-            const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2);
-            if (need) {
-              gc[2 * jp][r] = q.x;
-              gc[2 * jp + 1][r] = q.y;
-            }
-            float te[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e)
-              te[e] = act[2 * jp + e] ? __ldg(Lc + (size_t)r * w + 2 * jp + e) : 0.f;
-            h2 = __ffma2_rn(q, q, h2);
-            c2 = __ffma2_rn(q, make_float2(te[0], te[1]), c2);
-          }
-        }
-        hh = h2.x + h2.y;
-        ct = c2.x + c2.y;
-      } else {
-        float g[CPL][PS];
-        float sg = 0.f;
-#pragma unroll
-        for (int j = 0; j < CPL; ++j)
-#pragma unroll
-          for (int r = 0; r < PS; ++r) {
-            g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
-            sg += g[j][r];
-          }
-        sg = group_sum<G>(sg);
-        nn = PS * (int)group_sum<G>((float)__popc(code));
-        const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
-        hh = 0.f;
-        ct = 0.f;
-#pragma unroll
-        for (int j = 0; j < CPL; ++j)
-#pragma unroll
-          for (int r = 0; r < PS; ++r) {
-            const float q = v[j] ? g[j][r] - mg : 0.f;
-            if (need) gc[j][r] = q;
-            hh = fmaf(q, q, hh);
-            ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
-          }
-      }
-      hh = group_sum<G>(hh);
-      ct = group_sum<G>(ct);
-      if (need) {  // implies not frozen (frozen is the same in every lane of a group)
-        H = hh;
-        invH = hh > 0.f ? __fdividef(1.f, hh) : 0.f;  // hh is far below 2^126
-        gcT = ct;
-        n = nn;
-        prev = code;
-        have = true;
-        if (n == 0 || H <= kFlatEps * (float)n) {  // H and n change only here
-          frozen = true;
-          flat = true;
-        }
-      }
-    }
-    if (it == 0) rows.ready();  // staged rows (if any) arrive while the sums above load
-    // A and B change only with the base or the centred gradient. When some
-    // patch of the warp needs them anew the whole warp recomputes (a patch
-    // whose base and gradient did not change gets the same sums again, so the
-    // result does not depend on its neighbours). No branches inside: an
-    // invalid column has gc = 0 and reads a clamped (readable) column, so it
-    // adds exactly 0; a frozen patch's sums are not used.
-    if (__any_sync(kFull, !frozen && (need || kd != kc))) {
-      float sa[2] = {0.f, 0.f}, sb[2] = {0.f, 0.f};
-#pragma unroll
-      for (int j = 0; j < CPL; ++j) {
-        const auto p = rows.col_clamped(ib + j);
-#pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          const float2 q = rows.ld(p, r);
-          sa[r & 1] = fmaf(gc[j][r], q.x, sa[r & 1]);
-          sb[r & 1] = fmaf(gc[j][r], q.y, sb[r & 1]);
-        }
-      }
-      A = group_sum<G>(sa[0] + sa[1]);
-      B = group_sum<G>(sb[0] + sb[1]);
-      kc = kd;
-    }
-    const float Ssum = fmaf(t, B, A);
-    if (!frozen) {
-      last_step = (Ssum - gcT) * invH;
-      D += last_step;
-      ++steps;
-      // non-finite, or left the search range (dropped below), or converged
-      if (!isfinite(D) || fabsf(D - u0) > (float)PS || fabsf(last_step) < kStepTol)
-        frozen = true;
+  PatchState<PS, CPL> st;
+  st.D = u0;
+  st.last_step = 0.f;
+  st.frozen = st.flat = false;
+  st.steps = 0;
+  if (a.iters > 0) {
+    search_step<PS, CPL, true>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
+    for (int it = 1; it < a.iters; ++it) {
+      if (__all_sync(kFull, st.frozen)) break;  // every patch of the warp has stopped
+      search_step<PS, CPL, false>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
     }
   }
+  const float D = st.D, last_step = st.last_step;
+  const bool flat = st.flat;
+  const int steps = st.steps;
 
   rows.ready();
   // ---- Bayesian window (Eqs. 3-4): samples at D* + {-1, -0.5, 0, 0.5, 1}
