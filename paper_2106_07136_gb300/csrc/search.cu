@@ -60,6 +60,9 @@ __device__ __forceinline__ bool sample_ok(int i0, float t, int w) {
   return i0 >= 0 && (i0 < w - 1 || (i0 == w - 1 && t == 0.f));
 }
 
+// The same test for several columns at one fraction: i0 in [0, last_base(t, w)].
+__device__ __forceinline__ int last_base(float t, int w) { return t == 0.f ? w - 1 : w - 2; }
+
 __device__ __forceinline__ float lerp_packed(float2 q, float t) { return fmaf(t, q.y, q.x); }
 
 __device__ __forceinline__ float bilinear_clamped(const float *M, int w, int h, float x,
@@ -204,8 +207,7 @@ struct PatchState {
   int steps;
   unsigned prev;  // valid-column code the sums below were taken over
   float gc[CPL][PS];
-  float H, invH, gcT;
-  int n;
+  float invH, gcT;  // 1 / Hessian, template term of the sums
   // Within one integer base the interpolated sum is linear in the fraction:
   // sum gc (R + t dR) = A + t B, A = sum gc R, B = sum gc dR at base kc.
   float A, B;
@@ -226,11 +228,12 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
   float t;
   split_disp(st.D, kd, t);
   const int ib = xl + kd;
+  const int lb = last_base(t, w);
   bool v[CPL];
   unsigned code = 0u;
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    v[j] = act[j] && sample_ok(ib + j, t, w);
+    v[j] = act[j] && ib + j >= 0 && ib + j <= lb;
     code |= (unsigned)v[j] << j;
   }
   // the first step computes every patch's sums; later ones only where the
@@ -243,8 +246,12 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
     float hh, ct;
     int nn;
     if constexpr (CPL % 2 == 0) {
-      // column pairs as packed f32x2; an invalid column's term is (g - mg) * 0
-      float2 g2[CPL / 2][PS], s2 = make_float2(0.f, 0.f);
+      // column pairs as packed f32x2; the lane's own columns are always
+      // readable, and an invalid column's terms are multiplied by 0
+      float2 g2[CPL / 2][PS], m2[CPL / 2], s2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int jp = 0; jp < CPL / 2; ++jp)
+        m2[jp] = make_float2(v[2 * jp] ? 1.f : 0.f, v[2 * jp + 1] ? 1.f : 0.f);
 #pragma unroll
       for (int jp = 0; jp < CPL / 2; ++jp)
 #pragma unroll
@@ -252,9 +259,9 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
           float ge[2];
 #pragma unroll
           for (int e = 0; e < 2; ++e)
-            ge[e] = v[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
+            ge[e] = act[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
           g2[jp][r] = make_float2(ge[0], ge[1]);
-          s2 = __fadd2_rn(s2, g2[jp][r]);
+          s2 = __ffma2_rn(g2[jp][r], m2[jp], s2);  // adds g where valid, exactly
         }
       const float sg = group_sum<G>(s2.x + s2.y);
       nn = PS * (int)group_sum<G>((float)__popc(code));
@@ -263,10 +270,9 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
       float2 h2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int jp = 0; jp < CPL / 2; ++jp) {
-        const float2 m2 = make_float2(v[2 * jp] ? 1.f : 0.f, v[2 * jp + 1] ? 1.f : 0.f);
 #pragma unroll
         for (int r = 0; r < PS; ++r) {
-          const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2);
+          const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2[jp]);
           if (need) {
             st.gc[2 * jp][r] = q.x;
             st.gc[2 * jp + 1][r] = q.y;
@@ -308,25 +314,23 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
     }
     hh = group_sum<G>(hh);
     ct = group_sum<G>(ct);
-    if (need) {  // implies not st.frozen (st.frozen is the same in every lane of a group)
-      st.H = hh;
+    if (need) {  // implies not frozen (frozen is the same in every lane of a group)
       st.invH = hh > 0.f ? __fdividef(1.f, hh) : 0.f;  // hh is far below 2^126
       st.gcT = ct;
-      st.n = nn;
       st.prev = code;
-      if (st.n == 0 || st.H <= kFlatEps * (float)st.n) {  // st.H and st.n change only here
+      if (nn == 0 || hh <= kFlatEps * (float)nn) {  // the Hessian and count change only here
         st.frozen = true;
         st.flat = true;
       }
     }
   }
   if constexpr (FIRST) rows.ready();  // staged rows (if any) arrive while the sums above load
-  // st.A and st.B change only with the base or the centred gradient. When some
+  // A and B change only with the base or the centred gradient. When some
   // patch of the warp needs them anew the whole warp recomputes (a patch
   // whose base and gradient did not change gets the same sums again, so the
   // result does not depend on its neighbours). No branches inside: an
-  // invalid column has st.gc = 0 and reads a clamped (readable) column, so it
-  // adds exactly 0; a st.frozen patch's sums are not used.
+  // invalid column has gc = 0 and reads a clamped (readable) column, so it
+  // adds exactly 0; a frozen patch's sums are not used.
   if (FIRST || __any_sync(kFull, !st.frozen && (need || kd != st.kc))) {
     float sa[2] = {0.f, 0.f}, sb[2] = {0.f, 0.f};
 #pragma unroll
@@ -351,6 +355,56 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
     // non-finite, or left the search range (dropped below), or converged
     if (!isfinite(st.D) || fabsf(st.D - u0) > (float)PS || fabsf(st.last_step) < kStepTol)
       st.frozen = true;
+  }
+}
+
+// The window's row pass for column pairs (packed f32x2). Each of the CPL + 2
+// packed pairs of a row is read once and interpolated at both fractions.
+// GUARD: read only the pairs a valid column samples (the others may lie
+// outside the image or the staged tile); without it every pair is in both.
+// An invalid column's sums are finite and are multiplied by 0 in the merge.
+template <int PS, int CPL, bool GUARD, class Rows>
+__device__ __forceinline__ void window_rows_pairs(const Rows &rows, int ib, float t, float th,
+                                                  bool hi, const float *Lc, int w,
+                                                  const bool (&act)[CPL],
+                                                  const bool (&need)[CPL + 2],
+                                                  const float (&cs)[CPL],
+                                                  float2 (&P1)[5][CPL / 2],
+                                                  float2 (&P2)[5][CPL / 2]) {
+  constexpr int S = 5;
+#pragma unroll
+  for (int r = 0; r < PS; ++r) {
+    float Lt[CPL + 2], Lh[CPL + 2];
+#pragma unroll
+    for (int m = 0; m < CPL + 2; ++m) {
+      const float2 q = (!GUARD || need[m]) ? rows.ld(rows.col(ib - 1 + m), r)
+                                            : make_float2(0.f, 0.f);
+      Lt[m] = lerp_packed(q, t);
+      Lh[m] = lerp_packed(q, th);
+    }
+#pragma unroll
+    for (int jp = 0; jp < CPL / 2; ++jp) {
+      const int j = 2 * jp;
+      // minus (template + shift): -(T + cs) rounds to exactly -fl(T + cs)
+      float tn[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+        tn[e] = -(act[j + e] ? __ldg(Lc + (size_t)r * w + j + e) : 0.f) - cs[j + e];
+      const float2 Tn = make_float2(tn[0], tn[1]);
+      // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1
+      const float2 d[S] = {
+          __fadd2_rn(make_float2(Lt[j + 2], Lt[j + 3]), Tn),
+          __fadd2_rn(hi ? make_float2(Lh[j + 2], Lh[j + 3]) : make_float2(Lh[j + 1], Lh[j + 2]),
+                     Tn),
+          __fadd2_rn(make_float2(Lt[j + 1], Lt[j + 2]), Tn),
+          __fadd2_rn(hi ? make_float2(Lh[j + 1], Lh[j + 2]) : make_float2(Lh[j], Lh[j + 1]), Tn),
+          __fadd2_rn(make_float2(Lt[j], Lt[j + 1]), Tn)};
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        P1[i][jp] = __fadd2_rn(P1[i][jp], d[i]);
+        P2[i][jp] = __ffma2_rn(d[i], d[i], P2[i][jp]);
+      }
+    }
   }
 }
 
@@ -403,12 +457,13 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
   // base column one further right when t >= 0.5
   const bool hi = t >= 0.5f;
   const float th = hi ? t - 0.5f : t + 0.5f;
+  const int lb = last_base(t, w);
   bool vc[CPL];
   int nv_lane = 0, nc_lane = 0;
 #pragma unroll
   for (int j = 0; j < CPL; ++j) {
-    nv_lane += (act[j] && fin && sample_ok(ib + j, t, w)) ? 1 : 0;
-    vc[j] = act[j] && inr && (ib + j >= 1) && sample_ok(ib + j + 1, t, w);
+    nv_lane += (act[j] && fin && ib + j >= 0 && ib + j <= lb) ? 1 : 0;
+    vc[j] = act[j] && inr && ib + j >= 1 && ib + j + 1 <= lb;
     nc_lane += vc[j] ? 1 : 0;
   }
   const int nvalid = PS * (int)group_sum<G>((float)nv_lane);
@@ -434,7 +489,10 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
 #pragma unroll
   for (int j = 0; j < CPL; ++j)
     cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) - __ldg(Lc + j) : 0.f;
-  float S1[S][CPL], S2[S][CPL];
+  // Merge per sample: s1 = sum of the residuals, md their mean, and
+  // E = sum (d - md)^2 = S2 - 2 (md - cs) S1 + n (md - cs)^2 per column.
+  const float inv_nc = nc > 0 ? __fdividef(1.f, (float)nc) : 0.f;
+  float E[S];
   if constexpr (CPL % 2 == 0) {
     // Columns j and j + 1 take the same operations, so each pair runs as one
     // packed f32x2 instruction (per component the same rounding as the scalar
@@ -444,49 +502,45 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     for (int i = 0; i < S; ++i)
 #pragma unroll
       for (int jp = 0; jp < CPL / 2; ++jp) P1[i][jp] = P2[i][jp] = make_float2(0.f, 0.f);
+    // A warp whose patches are all in range (so their pairs lie in a staged
+    // tile, if any) with all pairs in the image reads them unconditionally.
+    if (__all_sync(kFull, inr && ib >= 1 && ib + CPL <= w - 1))
+      window_rows_pairs<PS, CPL, false>(rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
+    else
+      window_rows_pairs<PS, CPL, true>(rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
+    // the merge below, per column pair; an invalid column's term is x * 0
+    // (every term is finite)
+    const float2 kPS = make_float2((float)PS, (float)PS), kM2 = make_float2(-2.f, -2.f);
+    float2 cs2[CPL / 2], ncs2[CPL / 2], vm[CPL / 2];
 #pragma unroll
-    for (int r = 0; r < PS; ++r) {
-      float Lt[CPL + 2], Lh[CPL + 2];
-#pragma unroll
-      for (int m = 0; m < CPL + 2; ++m) {
-        const float2 q = need[m] ? rows.ld(rows.col(ib - 1 + m), r) : make_float2(0.f, 0.f);
-        Lt[m] = lerp_packed(q, t);
-        Lh[m] = lerp_packed(q, th);
-      }
-#pragma unroll
-      for (int jp = 0; jp < CPL / 2; ++jp) {
-        const int j = 2 * jp;
-        // minus (template + shift): -(T + cs) rounds to exactly -fl(T + cs)
-        float tn[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e)
-          tn[e] = -(vc[j + e] ? __ldg(Lc + (size_t)r * w + j + e) : 0.f) - cs[j + e];
-        const float2 Tn = make_float2(tn[0], tn[1]);
-        // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1
-        const float2 d[S] = {
-            __fadd2_rn(make_float2(Lt[j + 2], Lt[j + 3]), Tn),
-            __fadd2_rn(hi ? make_float2(Lh[j + 2], Lh[j + 3]) : make_float2(Lh[j + 1], Lh[j + 2]),
-                       Tn),
-            __fadd2_rn(make_float2(Lt[j + 1], Lt[j + 2]), Tn),
-            __fadd2_rn(hi ? make_float2(Lh[j + 1], Lh[j + 2]) : make_float2(Lh[j], Lh[j + 1]), Tn),
-            __fadd2_rn(make_float2(Lt[j], Lt[j + 1]), Tn)};
-#pragma unroll
-        for (int i = 0; i < S; ++i) {
-          P1[i][jp] = __fadd2_rn(P1[i][jp], d[i]);
-          P2[i][jp] = __ffma2_rn(d[i], d[i], P2[i][jp]);
-        }
-      }
+    for (int jp = 0; jp < CPL / 2; ++jp) {
+      cs2[jp] = make_float2(cs[2 * jp], cs[2 * jp + 1]);
+      ncs2[jp] = make_float2(-cs[2 * jp], -cs[2 * jp + 1]);
+      vm[jp] = make_float2(vc[2 * jp] ? 1.f : 0.f, vc[2 * jp + 1] ? 1.f : 0.f);
     }
 #pragma unroll
-    for (int i = 0; i < S; ++i)
+    for (int i = 0; i < S; ++i) {
+      float s1 = 0.f;
 #pragma unroll
       for (int jp = 0; jp < CPL / 2; ++jp) {
-        S1[i][2 * jp] = P1[i][jp].x;
-        S1[i][2 * jp + 1] = P1[i][jp].y;
-        S2[i][2 * jp] = P2[i][jp].x;
-        S2[i][2 * jp + 1] = P2[i][jp].y;
+        const float2 x = __fmul2_rn(__ffma2_rn(kPS, cs2[jp], P1[i][jp]), vm[jp]);
+        s1 += x.x + x.y;
       }
+      s1 = group_sum<G>(s1);
+      const float md = (a.normalize && nc > 0) ? s1 * inv_nc : 0.f;
+      const float2 md2 = make_float2(md, md);
+      float e = 0.f;
+#pragma unroll
+      for (int jp = 0; jp < CPL / 2; ++jp) {
+        const float2 u = __fadd2_rn(md2, ncs2[jp]);
+        const float2 in = __ffma2_rn(__fmul2_rn(kPS, u), u, P2[i][jp]);
+        const float2 x = __fmul2_rn(__ffma2_rn(__fmul2_rn(kM2, u), P1[i][jp], in), vm[jp]);
+        e += x.x + x.y;
+      }
+      E[i] = group_sum<G>(e);
+    }
   } else {
+    float S1[S][CPL], S2[S][CPL];
 #pragma unroll
     for (int i = 0; i < S; ++i)
 #pragma unroll
@@ -514,27 +568,28 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
         }
       }
     }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      float s1 = 0.f;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) s1 += vc[j] ? S1[i][j] + (float)PS * cs[j] : 0.f;
+      s1 = group_sum<G>(s1);
+      const float md = (a.normalize && nc > 0) ? s1 * inv_nc : 0.f;
+      float e = 0.f;
+#pragma unroll
+      for (int j = 0; j < CPL; ++j) {
+        if (vc[j]) {
+          const float u = md - cs[j];
+          e += fmaf(-2.f * u, S1[i][j], fmaf((float)PS * u, u, S2[i][j]));
+        }
+      }
+      E[i] = group_sum<G>(e);
+    }
   }
   const bool write = live && c == 0;
-  const float inv_nc = nc > 0 ? __fdividef(1.f, (float)nc) : 0.f;
-  float E[S];
+  if (write && a.energies) {
 #pragma unroll
-  for (int i = 0; i < S; ++i) {
-    float s1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) s1 += vc[j] ? S1[i][j] + (float)PS * cs[j] : 0.f;
-    s1 = group_sum<G>(s1);
-    const float md = (a.normalize && nc > 0) ? s1 * inv_nc : 0.f;
-    float e = 0.f;
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      if (vc[j]) {
-        const float u = md - cs[j];
-        e += fmaf(-2.f * u, S1[i][j], fmaf((float)PS * u, u, S2[i][j]));
-      }
-    }
-    E[i] = group_sum<G>(e);
-    if (write && a.energies) a.energies[k * S + i] = E[i];
+    for (int i = 0; i < S; ++i) a.energies[k * S + i] = E[i];
   }
   float Emin = E[0], Eo = INFINITY;
 #pragma unroll
