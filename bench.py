@@ -444,9 +444,45 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     for _ in range(k):
         m.match_host(Lp, Rp, params, out=Op)
     dt = time.perf_counter() - t0
+    blocking = {"value": B * k / dt, "unit": "pairs/s", "h2d_bytes_per_step": 2 * B * W * H,
+                "d2h_bytes_per_step": 4 * B * W * H,
+                "path": "bdis_match_host (returns with the result): pinned host uint8 in, "
+                        "float32 disparity out, 4 chunks overlapping copies and match"}
+    # the same steps as a stream of batches: step i is enqueued (bdis_match_host_async)
+    # before step i-1's result is waited for, on two pinned buffer sets, so one
+    # step's copies overlap its neighbours' matches; every step's copies are timed
+    sets = [(Lp, Rp, Op), (Lp.clone().pin_memory(), Rp.clone().pin_memory(),
+                           torch.empty_like(Op).pin_memory())]
+
+    def stream_of(n):
+        prev = None
+        for i in range(n):
+            lt, rt, ot = sets[i % 2]
+            t, _ = m.match_host_async(lt, rt, params, out=ot)
+            if prev is not None:
+                m.host_wait(prev)
+            prev = t
+        m.host_wait(prev)
+
+    stream_of(max(2, args.warmup))
+    t0 = time.perf_counter()
+    stream_of(k)
+    dt = time.perf_counter() - t0
     res["e2e"] = {"value": B * k / dt, "unit": "pairs/s", "h2d_bytes_per_step": 2 * B * W * H,
-                  "d2h_bytes_per_step": 4 * B * W * H,
-                  "path": "bdis_match_host: pinned host uint8 in, float32 disparity out"}
+                  "d2h_bytes_per_step": 4 * B * W * H, "steps": k,
+                  "path": "bdis_match_host_async + bdis_host_wait, one call per step, step i "
+                          "enqueued before step i-1 is waited for: pinned host uint8 in, "
+                          "float32 disparity out, host wall clock over all steps"}
+    res["e2e_blocking"] = blocking
+    # both buffer sets hold exactly the device entry's result for these pairs
+    ref_t = m.match(left, right, params)
+    torch.cuda.synchronize(device)
+    ref = ref_t.cpu().numpy()
+    same = True
+    for o in (sets[0][2].numpy(), sets[1][2].numpy()):
+        same = same and np.array_equal(np.isnan(o), np.isnan(ref)) and \
+            np.array_equal(o[~np.isnan(o)], ref[~np.isnan(ref)])
+    res["e2e"]["equals_device_result"] = bool(same)
     # single-pair latency (device-resident inputs, host wall clock incl. sync)
     l1, r1 = left[0], right[0]
     o1 = torch.empty((H, W), dtype=torch.float32, device=device)

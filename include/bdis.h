@@ -234,6 +234,34 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
                             int width, int height, int count, const bdis_params *p,
                             float *disparity_out);
 
+/* Asynchronous form of bdis_match_host, for streams of batches (video,
+ * serving): the call enqueues the copy-in, the match (Sec. 2, as at
+ * bdis_match) and the copy-out of one whole batch and returns at once with
+ * a ticket (> 0) in *ticket. Successive calls overlap: a call's copy-in
+ * runs beside the previous call's match, its copy-out beside the next one's.
+ * The device holds two batches' inputs and outputs (slot = ticket & 1); a
+ * slot is refilled only after the match and the copy-out of the call two
+ * before have finished.
+ * Ownership: left, right and disparity_out stay the caller's; they must not
+ * be written (inputs) or read (output) until bdis_host_wait(h, ticket) has
+ * returned. Use pinned host memory: with pageable memory the copies, and so
+ * the call, block. Any other call on the handle that uses its workspace
+ * (bdis_match and its variants, bdis_match_host, bdis_reserve) first waits
+ * for every asynchronous call in flight; so does a call with another
+ * geometry, batch size or scale range.
+ * Errors: argument, parameter and geometry errors as at bdis_match_host,
+ * returned at once with nothing enqueued; CUDA errors of the enqueue at
+ * once; CUDA errors of the work itself from bdis_host_wait. */
+bdis_status bdis_match_host_async(bdis_handle *h, const uint8_t *left, const uint8_t *right,
+                                  int width, int height, int count, const bdis_params *p,
+                                  float *disparity_out, uint64_t *ticket);
+
+/* Returns when the asynchronous call `ticket` (and every call before it) has
+ * finished and its result is in its disparity_out. Waiting for the latest
+ * ticket leaves the handle's streams idle. BDIS_E_INVALID_ARG for a ticket
+ * this handle has not issued. */
+bdis_status bdis_host_wait(bdis_handle *h, uint64_t ticket);
+
 /* ------------------------------------------------------------------ steps
  * The method's steps, one launch sequence each, on dense device batches of
  * `count` planes. bdis_match runs exactly these kernels. */

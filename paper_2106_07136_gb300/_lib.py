@@ -17,6 +17,7 @@ EXPORTED = [
     "bdis_default_params", "bdis_status_string", "bdis_last_error_string", "bdis_version",
     "bdis_level_dims", "bdis_grid", "bdis_patch_count", "bdis_create", "bdis_reserve",
     "bdis_workspace_bytes", "bdis_destroy", "bdis_match", "bdis_match_host",
+    "bdis_match_host_async", "bdis_host_wait",
     "bdis_prepare_level0", "bdis_pyramid_level", "bdis_search_level", "bdis_densify_level",
     "bdis_upsample", "bdis_enable_timing", "bdis_read_timing", "bdis_pack_right",
     "bdis_match_static", "bdis_probe_fp32_tflops", "bdis_set_search_variant",
@@ -123,6 +124,9 @@ def load():
     lib.bdis_match.argtypes = [c_void_p, ip, ip, pp, c_void_p]
     lib.bdis_match_host.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, pp,
                                     c_void_p]
+    lib.bdis_match_host_async.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int,
+                                          pp, c_void_p, P(ctypes.c_uint64)]
+    lib.bdis_host_wait.argtypes = [c_void_p, ctypes.c_uint64]
     lib.bdis_prepare_level0.argtypes = [ip, ip, c_void_p, c_void_p, c_void_p, c_void_p]
     lib.bdis_pyramid_level.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p,
                                        c_void_p, c_void_p, c_void_p]

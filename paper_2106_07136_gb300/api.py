@@ -88,11 +88,13 @@ class Matcher:
         check(self._lib.bdis_create(ctypes.byref(h), dev.index or 0,
                                     ctypes.c_void_p(int(self.stream.cuda_stream))), "bdis_create")
         self._h = h
+        self._inflight = {}  # ticket -> host buffers of bdis_match_host_async calls
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
-            self._lib.bdis_destroy(self._h)
+            self._lib.bdis_destroy(self._h)  # waits for all work, asynchronous calls included
             self._h = None
+            self._inflight = {}
 
     def __del__(self):
         try:
@@ -217,6 +219,38 @@ class Matcher:
         check(self._lib.bdis_match_host(self._h, lt.data_ptr(), rt.data_ptr(), w, h, b,
                                         ctypes.byref(params), ot.data_ptr()), "bdis_match_host")
         return out
+
+    def match_host_async(self, left, right, params: BdisParams = None, out=None):
+        """bdis_match_host_async: enqueue one batch with host buffers and return
+        (ticket, out) at once. `left`, `right` and `out` must be left alone
+        until host_wait(ticket); they are kept referenced until then. Pinned
+        buffers make the call asynchronous."""
+        params = params if params is not None else default_params()
+        lt, rt = torch.as_tensor(left), torch.as_tensor(right)
+        if lt.dtype != torch.uint8 or rt.dtype != torch.uint8 or lt.device.type != "cpu":
+            raise TypeError("match_host_async takes uint8 host images")
+        if not (lt.is_contiguous() and rt.is_contiguous()):
+            raise ValueError("match_host_async takes dense host images")
+        b = 1 if lt.dim() == 2 else lt.shape[0]
+        h, w = lt.shape[-2], lt.shape[-1]
+        if out is None:
+            out = torch.empty(lt.shape, dtype=torch.float32).pin_memory() if lt.is_pinned() \
+                else torch.empty(lt.shape, dtype=torch.float32)
+        ot = torch.as_tensor(out)
+        if not (ot.is_contiguous() and ot.dtype == torch.float32 and ot.numel() == b * h * w):
+            raise ValueError("out must be a dense float32 host buffer of B*H*W elements")
+        ticket = ctypes.c_uint64(0)
+        check(self._lib.bdis_match_host_async(self._h, lt.data_ptr(), rt.data_ptr(), w, h, b,
+                                              ctypes.byref(params), ot.data_ptr(),
+                                              ctypes.byref(ticket)), "bdis_match_host_async")
+        self._inflight[ticket.value] = (lt, rt, ot)
+        return ticket.value, out
+
+    def host_wait(self, ticket: int):
+        """bdis_host_wait: return once call `ticket` (and all before it) is done."""
+        check(self._lib.bdis_host_wait(self._h, ticket), "bdis_host_wait")
+        for t in [t for t in self._inflight if t <= ticket]:
+            del self._inflight[t]
 
 
 def match_static(left: torch.Tensor, right: torch.Tensor, params: BdisParams = None,

@@ -33,6 +33,11 @@ struct bdis_handle {
   // and per buffer slot the events "inputs copied", "matched", "output copied"
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
   cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {};
+  // bdis_match_host_async: calls enqueued since the streams were last idle,
+  // the next ticket, and the workspace layout those calls use (slot buffers)
+  int async_pending = 0;
+  uint64_t async_next = 1;
+  size_t async_key[7] = {};
 };
 
 namespace bdis {
@@ -101,7 +106,24 @@ Layout plan_layout(int w, int h, int count, const bdis_params &p, bool host_stag
 
 namespace {
 
-bdis_status ensure_workspace(bdis_handle *h, size_t bytes) {
+// Let every asynchronous host match finish: all three streams idle.
+cudaError_t drain_async(bdis_handle *h) {
+  if (!h->async_pending) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(h->copy_in);
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  cudaError_t e3 = cudaStreamSynchronize(h->copy_out);
+  h->async_pending = 0;
+  return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : e3);
+}
+
+// Every entry that uses the workspace comes through here. A call other than
+// an asynchronous host match first lets those finish: its own layout may
+// overlap their input and output slots.
+bdis_status ensure_workspace(bdis_handle *h, size_t bytes, bool from_async = false) {
+  if (!from_async || bytes > h->ws_bytes) {
+    cudaError_t e = drain_async(h);
+    if (e != cudaSuccess) return record_cuda(e);
+  }
   if (bytes <= h->ws_bytes) return BDIS_OK;
   // The old block may still be read by work already on the stream.
   if (h->ws) {
@@ -852,6 +874,87 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
   }
   if (s != BDIS_OK) return s;
   if (e == cudaSuccess) e = e2;
+  return record_cuda(e);
+}
+
+bdis_status bdis_match_host_async(bdis_handle *h, const uint8_t *left, const uint8_t *right,
+                                  int width, int height, int count, const bdis_params *p,
+                                  float *disparity_out, uint64_t *ticket) {
+  if (!h || !left || !right || !disparity_out || !ticket || width < 1 || height < 1 ||
+      count < 1)
+    return BDIS_E_INVALID_ARG;
+  bdis_status s = check_params(p);
+  if (s != BDIS_OK) return s;
+  s = check_geometry(width, height, *p);
+  if (s != BDIS_OK) return s;
+  s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  s = ensure_pipeline(h);
+  if (s != BDIS_OK) return s;
+  // One whole batch per call, its device inputs and output in slot (ticket & 1):
+  // the copy-in of this call overlaps the match of the previous one, and its
+  // copy-out the match of the next. A slot is refilled only after the match
+  // that read its inputs (ev_done) and the copy-out that read its output
+  // (ev_out) of the call two before have finished.
+  const size_t wh = (size_t)width * height;
+  const Layout lay = plan_layout(width, height, count, *p, true);
+  const size_t in_b = wh * count, out_b = wh * count * sizeof(float);
+  size_t off = lay.bytes;
+  auto take = [&](size_t n) {
+    const size_t o = off;
+    off += (n + 255) / 256 * 256;
+    return o;
+  };
+  const size_t slot_l[2] = {lay.in_left, take(in_b)};
+  const size_t slot_r[2] = {lay.in_right, take(in_b)};
+  const size_t slot_o[2] = {lay.out, take(out_b)};
+  const size_t key[7] = {off, slot_l[0], slot_l[1], slot_r[0], slot_r[1], slot_o[0], slot_o[1]};
+  if (h->async_pending && memcmp(key, h->async_key, sizeof key) != 0) {
+    cudaError_t e = drain_async(h);  // calls in flight use another layout
+    if (e != cudaSuccess) return record_cuda(e);
+  }
+  s = ensure_workspace(h, off, true);
+  if (s != BDIS_OK) return s;
+  memcpy(h->async_key, key, sizeof key);
+  const uint64_t t = h->async_next;
+  const int slot = (int)(t & 1u);
+  char *base = static_cast<char *>(h->ws);
+  cudaError_t e = cudaStreamWaitEvent(h->copy_in, h->ev_done[slot], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + slot_l[slot], left, in_b, cudaMemcpyHostToDevice, h->copy_in);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(base + slot_r[slot], right, in_b, cudaMemcpyHostToDevice, h->copy_in);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[slot], h->copy_in);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_in[slot], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_out[slot], 0);
+  if (e != cudaSuccess) return record_cuda(e);
+  h->async_pending += 1;  // work is on the streams from here on
+  bdis_image L{base + slot_l[slot], width, height, (size_t)width, wh, count, BDIS_U8};
+  bdis_image R = L;
+  R.data = base + slot_r[slot];
+  float *dout = reinterpret_cast<float *>(base + slot_o[slot]);
+  s = run_match(h, L, R, *p, dout, lay);
+  if (s != BDIS_OK) return s;
+  e = cudaEventRecord(h->ev_done[slot], h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_out, h->ev_done[slot], 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(disparity_out, dout, out_b, cudaMemcpyDeviceToHost, h->copy_out);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[slot], h->copy_out);
+  if (e != cudaSuccess) return record_cuda(e);
+  h->async_next = t + 1;
+  *ticket = t;
+  return BDIS_OK;
+}
+
+bdis_status bdis_host_wait(bdis_handle *h, uint64_t ticket) {
+  if (!h || ticket == 0 || ticket >= h->async_next) return BDIS_E_INVALID_ARG;
+  bdis_status s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  if (!h->async_pending) return BDIS_OK;  // drained since (by a later call or wait)
+  // The slot's copy-out event was recorded by this call or by a later one on
+  // the same in-order stream: once it has completed, so has this call.
+  cudaError_t e = cudaEventSynchronize(h->ev_out[ticket & 1u]);
+  if (e == cudaSuccess && ticket + 1 == h->async_next) e = drain_async(h);
   return record_cuda(e);
 }
 
