@@ -545,6 +545,8 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     import synth
     U = Lh.shape[0]
     res["variants"]["mixed_batch_graph"] = measure_mixed_batch(args, bd, device, stream)
+    res["variants"]["mixed_batch_graph_scaled"] = measure_mixed_batch(args, bd, device, stream,
+                                                                      scale_to_width=True)
     res["serving"] = measure_serving(args, bd, device)
     res["learned_vs_plain"] = measure_learned(args, bd, m, left, right, Lh, Rh, Dgt, device,
                                               stream)
@@ -673,9 +675,12 @@ def measure_serving(args, bd, device, seconds=3.0, rate=2000.0, videos=4, frames
 MIXED_GROUPS = [(64, 240, 320), (96, 480, 640), (64, 720, 1280), (32, 1080, 1920)]
 
 
-def measure_mixed_batch(args, bd, device, stream, unique=4):
+def measure_mixed_batch(args, bd, device, stream, unique=4, scale_to_width=False):
     """256 pairs of four sizes (disparity range width/10, scales 4..0) as one
-    autotuned CUDA-graph plan; pairs/s over graph launches."""
+    autotuned CUDA-graph plan; pairs/s over graph launches, and the error
+    against ground truth of each size's distinct pairs. scale_to_width: each
+    group's coarsest scale raised so the range is at most 4 px there
+    (BDIS_PLAN_SCALE_TO_WIDTH)."""
     import torch
     import synth
     groups = []
@@ -688,7 +693,8 @@ def measure_mixed_batch(args, bd, device, stream, unique=4):
                        torch.empty((b, h, w), dtype=torch.float32, device=device)))
     params = bd.default_params(**params_kw(args.patch))
     t0 = time.perf_counter()
-    plan = bd.Plan(groups, params, autotune=True, device=device, stream=stream)
+    plan = bd.Plan(groups, params, autotune=True, device=device, stream=stream,
+                   scale_to_width=scale_to_width)
     build_s = time.perf_counter() - t0
     for _ in range(3):
         plan.run(stream)
@@ -704,11 +710,19 @@ def measure_mixed_batch(args, bd, device, stream, unique=4):
     n = sum(g[0] for g in MIXED_GROUPS)
     mpix = sum(g[0] * g[1] * g[2] for g in MIXED_GROUPS) / 1e6
     choice = {f"{w}x{h}": plan.choice(gi, 0) for gi, (_, h, w) in enumerate(MIXED_GROUPS)}
+    accuracy = {}
+    for gi, (b, h, w) in enumerate(MIXED_GROUPS):
+        est = groups[gi][2][:unique].cpu().numpy()
+        gt = np.stack([synth.make_cfg2(seed=synth.stereo.pair_seed(3, 100 * gi + i), h=h,
+                                       w=w).disp for i in range(unique)])
+        accuracy[f"{w}x{h}"] = synth.error_stats(est, gt)
     out = {"value": n / (ms / 1e3), "unit": "pairs/s", "mpix_per_s": mpix / (ms / 1e3),
            "ms_per_step": ms, "pairs": n,
            "groups": [f"{b}x{w}x{h}" for b, h, w in MIXED_GROUPS],
            "workspace_gb": plan.workspace_bytes / 1e9, "plan_build_s": build_s,
-           "level0_choices": choice, "l2": "not flushed (back-to-back graph launches)"}
+           "level0_choices": choice, "accuracy_vs_ground_truth": accuracy,
+           "scale_to_width": scale_to_width,
+           "l2": "not flushed (back-to-back graph launches)"}
     plan.close()
     return out
 

@@ -381,6 +381,13 @@ bdis_status bdis_probe_fp32_tflops(int iterations, double *tflops, void *stream)
  * float rounding whatever is chosen. bdis_plan_create synchronises `stream`
  * (autotuning reads the inputs) and may take a second; run is asynchronous. */
 #define BDIS_PLAN_AUTOTUNE 1
+/* Per group, raise the coarsest scale to the smallest c >= p->coarsest_scale
+ * with 2^c >= width / 40, so that a disparity range of a tenth of the width
+ * (the mixed-size batch's) is at most 4 px at the coarsest level, where each
+ * patch starts from 0 (Sec. 2.1); c is lowered again while the coarsest level
+ * would be smaller than a patch. Not in the paper: an option of the batched
+ * path. bdis_plan_info reports each group's scale. */
+#define BDIS_PLAN_SCALE_TO_WIDTH 2
 
 typedef struct {
     bdis_image left, right;  /* device, as for bdis_match */
@@ -393,6 +400,7 @@ typedef struct {
     int densify_tile_height;     /* 0 = strip kernel (stride divides the patch
                                     size), else tiles of 32; 8/16/32 = tiles */
     size_t workspace_bytes;      /* of the whole group */
+    int coarsest_scale;          /* of the group (BDIS_PLAN_SCALE_TO_WIDTH may raise it) */
 } bdis_plan_choice;
 
 typedef struct bdis_plan bdis_plan;

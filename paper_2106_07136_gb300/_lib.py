@@ -32,6 +32,7 @@ EXPORTED = [
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
+BDIS_PLAN_SCALE_TO_WIDTH = 2
 
 STATIC_SCRATCH_BYTES = 24 << 20  # BDIS_STATIC_SCRATCH_BYTES
 
@@ -69,7 +70,8 @@ class BdisGroup(ctypes.Structure):
 
 class BdisPlanChoice(ctypes.Structure):
     _fields_ = [("search_columns_per_lane", c_int), ("search_block_threads", c_int),
-                ("densify_tile_height", c_int), ("workspace_bytes", c_size_t)]
+                ("densify_tile_height", c_int), ("workspace_bytes", c_size_t),
+                ("coarsest_scale", c_int)]
 
 
 class BdisTiming(ctypes.Structure):

@@ -331,10 +331,12 @@ class Plan:
 
     groups: list of (left, right, out) CUDA tensors, each (B, H, W) with one
     size per group; the plan binds their addresses, so refill them in place
-    between runs."""
+    between runs. scale_to_width: raise each group's coarsest scale to keep a
+    disparity range of a tenth of its width within 4 px there
+    (BDIS_PLAN_SCALE_TO_WIDTH)."""
 
     def __init__(self, groups, params: BdisParams = None, autotune: bool = True, device=None,
-                 stream=None):
+                 stream=None, scale_to_width: bool = False):
         self._lib = _lib.load()
         params = params if params is not None else default_params()
         self._keep = []
@@ -352,7 +354,9 @@ class Plan:
             torch.device(device)
         h = ctypes.c_void_p()
         check(self._lib.bdis_plan_create(dev.index or 0, arr, len(groups), ctypes.byref(params),
-                                         _lib.BDIS_PLAN_AUTOTUNE if autotune else 0,
+                                         (_lib.BDIS_PLAN_AUTOTUNE if autotune else 0)
+                                         | (_lib.BDIS_PLAN_SCALE_TO_WIDTH if scale_to_width
+                                            else 0),
                                          _stream_ptr(stream), ctypes.byref(h)),
               "bdis_plan_create")
         self._h = h
@@ -368,7 +372,8 @@ class Plan:
         return {"search_columns_per_lane": c.search_columns_per_lane,
                 "search_block_threads": c.search_block_threads,
                 "densify_tile_height": c.densify_tile_height,
-                "workspace_bytes": int(c.workspace_bytes)}
+                "workspace_bytes": int(c.workspace_bytes),
+                "coarsest_scale": c.coarsest_scale}
 
     @property
     def workspace_bytes(self) -> int:

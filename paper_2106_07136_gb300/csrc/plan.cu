@@ -18,6 +18,7 @@ struct bdis_plan {
   int device = 0;
   bdis_params params{};
   struct Group {
+    bdis_params params{};  // the plan's, with the coarsest scale raised per group if asked
     bdis_image left{}, right{};
     float *out = nullptr;
     void *ws = nullptr;
@@ -49,6 +50,18 @@ void release(bdis_plan *pl) {
   if (pl->fork) cudaEventDestroy(pl->fork);
   if (pl->capture) cudaStreamDestroy(pl->capture);
   delete pl;
+}
+
+// The smallest coarsest scale c at which a disparity range of a tenth of the
+// width is at most 4 px at the coarsest level (2^c >= W / 40), never below
+// the plan's own and lowered until the coarsest level still holds a patch.
+int scaled_coarsest(const bdis_params &p, int w, int h) {
+  int c = p.coarsest_scale;
+  while (c < 15 && (40LL << c) < (long long)w) ++c;
+  while (c > p.coarsest_scale &&
+         (bdis::level_dim(w, c) < p.patch_size || bdis::level_dim(h, c) < p.patch_size))
+    --c;
+  return c;
 }
 
 }  // namespace
@@ -83,10 +96,13 @@ bdis_status bdis_plan_create(int device, const bdis_group *groups, int n_groups,
   cudaStream_t user = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < n_groups && e == cudaSuccess; ++i) {
     auto &g = pl->groups[i];
+    g.params = *p;
+    if (flags & BDIS_PLAN_SCALE_TO_WIDTH)
+      g.params.coarsest_scale = scaled_coarsest(*p, groups[i].left.width, groups[i].left.height);
     g.left = groups[i].left;
     g.right = groups[i].right;
     g.out = groups[i].disparity_out;
-    g.ws_bytes = bdis::match_scratch_bytes(g.left.width, g.left.height, g.left.count, *p);
+    g.ws_bytes = bdis::match_scratch_bytes(g.left.width, g.left.height, g.left.count, g.params);
     e = cudaMalloc(&g.ws, g.ws_bytes);
     if (e != cudaSuccess) {
       g.ws = nullptr;
@@ -109,7 +125,8 @@ bdis_status bdis_plan_create(int device, const bdis_group *groups, int n_groups,
     if (user) e = cudaStreamSynchronize(user);  // the inputs may still be written there
     for (auto &g : pl->groups) {
       if (e != cudaSuccess) break;
-      s = bdis::autotune_match(g.ws, g.ws_bytes, g.stream, g.left, g.right, *p, g.out, &g.tune);
+      s = bdis::autotune_match(g.ws, g.ws_bytes, g.stream, g.left, g.right, g.params, g.out,
+                               &g.tune);
       if (s != BDIS_OK) {
         release(pl);
         return s;
@@ -130,8 +147,8 @@ bdis_status bdis_plan_create(int device, const bdis_group *groups, int n_groups,
     if (e != cudaSuccess || run_status != BDIS_OK) break;
     e = cudaStreamWaitEvent(g.stream, pl->fork, 0);
     if (e == cudaSuccess)
-      run_status = bdis::run_match_in(g.ws, g.ws_bytes, g.stream, g.left, g.right, *p, g.out,
-                                      (flags & BDIS_PLAN_AUTOTUNE) ? &g.tune : nullptr);
+      run_status = bdis::run_match_in(g.ws, g.ws_bytes, g.stream, g.left, g.right, g.params,
+                                      g.out, (flags & BDIS_PLAN_AUTOTUNE) ? &g.tune : nullptr);
     if (e == cudaSuccess && run_status == BDIS_OK) e = cudaEventRecord(g.done, g.stream);
     if (e == cudaSuccess && run_status == BDIS_OK) e = cudaStreamWaitEvent(pl->capture, g.done, 0);
   }
@@ -167,6 +184,7 @@ bdis_status bdis_plan_info(const bdis_plan *pl, int group, int level, bdis_plan_
   out->search_block_threads = t.search_threads;
   out->densify_tile_height = t.densify_tile_y;
   out->workspace_bytes = pl->groups[group].ws_bytes;
+  out->coarsest_scale = pl->groups[group].params.coarsest_scale;
   return BDIS_OK;
 }
 

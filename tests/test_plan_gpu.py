@@ -56,7 +56,8 @@ def test_plan_matches_per_group_calls_and_oracle(orc, autotune):
                 ch = plan.choice(gi, lvl)
                 assert ch["search_columns_per_lane"] in (1, 2)
                 assert ch["search_block_threads"] in (64, 128)
-                assert ch["densify_tile_height"] in (8, 16, 32)
+                assert ch["densify_tile_height"] in (0, 8, 16, 32)  # 0: strip kernel
+                assert ch["coarsest_scale"] == KW["coarsest_scale"]
     # second launch: identical
     plan.run()
     torch.cuda.synchronize()
@@ -74,3 +75,28 @@ def test_plan_matches_per_group_calls_and_oracle(orc, autotune):
     assert_e2e(new[0], orc.match(pp[0].left, pp[0].right, op), "refilled group")
     plan.close()
     m.close()
+
+
+def test_plan_scale_to_width():
+    """BDIS_PLAN_SCALE_TO_WIDTH: a group's coarsest scale becomes the smallest
+    c >= the plan's with 2^c >= width / 40, lowered while the coarsest level
+    would be smaller than a patch; each group then computes exactly what
+    bdis_match computes with that scale (no autotuning: the same kernels)."""
+    params = bd.default_params(**KW)
+    sizes = [(1, 160, 640), (2, 120, 160), (1, 140, 1300)]
+    # 640: 2^4 * 40 >= 640 -> 4. 160: 2^2 * 40 >= 160 -> stays 3. 1300: 6, but
+    # 140 rows are 3 at scale 6 and 5 at scale 5, 9 at scale 4 -> 4.
+    expect = [4, 3, 4]
+    groups = [make_group(b, h, w, 50 + 10 * i)[1:] for i, (b, h, w) in enumerate(sizes)]
+    plan = bd.Plan(groups, params, autotune=False, scale_to_width=True)
+    plan.run()
+    torch.cuda.synchronize()
+    m = bd.Matcher()
+    for gi, (L, R, out) in enumerate(groups):
+        c = plan.choice(gi, 0)["coarsest_scale"]
+        assert c == expect[gi]
+        ref = host(m.match(L, R, bd.default_params(**dict(KW, coarsest_scale=c))))
+        got = host(out)
+        assert np.array_equal(np.isnan(got), np.isnan(ref))
+        assert np.array_equal(got[~np.isnan(got)], ref[~np.isnan(ref)])
+    plan.close()
