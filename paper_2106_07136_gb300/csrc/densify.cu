@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
     }
     float out;
     if (den > 0.f)
-      out = num / den;
+      out = __fdividef(num, den);  // den >= the smallest mask weight, far below 2^126
     else if (a.is_finest)
       out = __int_as_float(0x7fc00000);  // NaN: not estimated
     else if (a.coarse)
@@ -270,14 +270,15 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
     for (int t = 0; t < S; ++t) {
       const int y = g * S + t;
       if (y >= yend) break;
-      float num = 0.f, den = 0.f;
+      // (numerator, denominator) as one packed f32x2 FMA per covering row:
+      // per component the same fma as the tiled kernel
+      float2 nd2 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         const int j = g - M + 1 + k;
         if (j < 0 || j > a.ny - 2) continue;
         const float my = smask[t + (M - 1 - k) * S];
-        num = fmaf(my, rA[k], num);
-        den = fmaf(my, rB[k], den);
+        nd2 = __ffma2_rn(make_float2(my, my), make_float2(rA[k], rB[k]), nd2);
       }
       if (y >= ylast) {
         if (!have_last) {
@@ -285,12 +286,12 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
           have_last = true;
         }
         const float my = mask_at(y - ylast);
-        num = fmaf(my, lastA, num);
-        den = fmaf(my, lastB, den);
+        nd2 = __ffma2_rn(make_float2(my, my), make_float2(lastA, lastB), nd2);
       }
+      const float num = nd2.x, den = nd2.y;
       float out;
       if (den > 0.f)
-        out = num / den;
+        out = __fdividef(num, den);  // den >= the smallest mask weight, far below 2^126
       else if (a.is_finest)
         out = __int_as_float(0x7fc00000);  // NaN: not estimated
       else if (a.coarse)
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(256) densify_dis_kernel(const DensifyArgs a) {
   }
   float out;
   if (den > 0.f)
-    out = num / den;
+    out = __fdividef(num, den);  // den >= the smallest mask weight, far below 2^126
   else if (a.is_finest)
     out = __int_as_float(0x7fc00000);
   else if (a.coarse)

@@ -172,9 +172,12 @@ constexpr int kCx = kPyrX + 2;                               // computed columns
 __global__ void __launch_bounds__(256) pyramid_fused_kernel(
     const float *__restrict__ L, const float2 *__restrict__ R, int w, int h, int dw, int dh,
     float *__restrict__ L1, float2 *__restrict__ R1, float *__restrict__ G1) {
-  __shared__ float inL[kStY][kStP], inR[kStY][kStP];
-  __shared__ float hL[kStY][kCx], hR[kStY][kCx];
-  __shared__ float sL[kPyrY + 2][kCx], sR[kPyrY + 2][kCx];
+  // the two views side by side, (L, R) per pixel, so that every tap of both
+  // is one 8-byte shared load and one packed f32x2 FMA (per component the
+  // same fma, in the same order, as down_kernel)
+  __shared__ float2 inLR[kStY][kStP];
+  __shared__ float2 hLR[kStY][kCx];
+  __shared__ float2 sLR[kPyrY + 2][kCx];
   const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const float *Lb = L + (long long)b * w * h;
@@ -200,8 +203,8 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
     for (int u = 0; u < 3; ++u) {
       if (!xok[u]) continue;
       const int c = lane + 32 * u;
-      const unsigned dl = (unsigned)__cvta_generic_to_shared(&inL[r][c]);
-      const unsigned dr = (unsigned)__cvta_generic_to_shared(&inR[r][c]);
+      const unsigned dl = (unsigned)__cvta_generic_to_shared(&inLR[r][c].x);
+      const unsigned dr = (unsigned)__cvta_generic_to_shared(&inLR[r][c].y);
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dl),
                    "l"(Lb + rowoff + xsrc[u]));
       asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr),
@@ -226,14 +229,10 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (!cok[u]) continue;
-      float hl = 0.f, hr = 0.f;
+      float2 hv = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < 5; ++i) {
-        hl = fmaf(k[i], inL[r][c0[u] + i], hl);
-        hr = fmaf(k[i], inR[r][c0[u] + i], hr);
-      }
-      hL[r][lane + 32 * u] = hl;
-      hR[r][lane + 32 * u] = hr;
+      for (int i = 0; i < 5; ++i) hv = __ffma2_rn(make_float2(k[i], k[i]), inLR[r][c0[u] + i], hv);
+      hLR[r][lane + 32 * u] = hv;
     }
   }
   __syncthreads();
@@ -246,14 +245,10 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
     for (int u = 0; u < 2; ++u) {
       if (!cok[u]) continue;
       const int cx = lane + 32 * u;
-      float accL = 0.f, accR = 0.f;
+      float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 5; ++j) {
-        accL = fmaf(k[j], hL[r0 + j][cx], accL);
-        accR = fmaf(k[j], hR[r0 + j][cx], accR);
-      }
-      sL[cy][cx] = accL;
-      sR[cy][cx] = accR;
+      for (int j = 0; j < 5; ++j) acc = __ffma2_rn(make_float2(k[j], k[j]), hLR[r0 + j][cx], acc);
+      sLR[cy][cx] = acc;
     }
   }
   __syncthreads();
@@ -261,13 +256,14 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
   for (int cy = 1 + warp; cy <= kPyrY; cy += nwarp) {
     const int X = X0 + cx - 1, Y = Y0 + cy - 1;
     if (X >= dw || Y >= dh) continue;
-    const float dm = sL[cy - 1][cx + 1] - sL[cy - 1][cx - 1];
-    const float d0 = sL[cy][cx + 1] - sL[cy][cx - 1];
-    const float dp = sL[cy + 1][cx + 1] - sL[cy + 1][cx - 1];
+    const float dm = sLR[cy - 1][cx + 1].x - sLR[cy - 1][cx - 1].x;
+    const float d0 = sLR[cy][cx + 1].x - sLR[cy][cx - 1].x;
+    const float dp = sLR[cy + 1][cx + 1].x - sLR[cy + 1][cx - 1].x;
     const size_t o = (size_t)b * dw * dh + (size_t)Y * dw + X;
-    L1[o] = sL[cy][cx];
+    const float2 v = sLR[cy][cx];
+    L1[o] = v.x;
     G1[o] = (dm + 2.f * d0 + dp) * 0.125f;
-    R1[o] = make_float2(sR[cy][cx], X + 1 < dw ? sR[cy][cx + 1] - sR[cy][cx] : 0.f);
+    R1[o] = make_float2(v.y, X + 1 < dw ? sLR[cy][cx + 1].y - v.y : 0.f);
   }
 }
 
