@@ -107,6 +107,8 @@ struct SearchArgs {
   int cw, ch;
   long long cplane;
   int ps, stride, nx, ny, np;
+  // floor(k / nx) = umulhi(k, nx_mul) for every patch index k < np (0: divide)
+  unsigned nx_mul;
   long long total;  // count * np
   int iters, s;
   float step, kappa;
@@ -120,6 +122,7 @@ struct SearchArgs {
   uint8_t *flags;
   int32_t *n_valid;
   uint8_t *steps;
+  int debug;  // any of the per-patch debug outputs above is wanted (set at launch)
 };
 
 struct DensifyArgs {

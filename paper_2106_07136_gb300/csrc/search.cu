@@ -127,11 +127,13 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
       a.d_star[k] = D;
       a.weight[k] = drop ? 0.f : post * (float)nvalid / (float)(ps * ps);
     }
-    if (a.u_init) a.u_init[k] = u0;
-    if (a.posterior) a.posterior[k] = post;
-    if (a.flags) a.flags[k] = flags;
-    if (a.n_valid) a.n_valid[k] = nvalid;
-    if (a.steps) a.steps[k] = (uint8_t)steps;
+    if (a.debug) {
+      if (a.u_init) a.u_init[k] = u0;
+      if (a.posterior) a.posterior[k] = post;
+      if (a.flags) a.flags[k] = flags;
+      if (a.n_valid) a.n_valid[k] = nvalid;
+      if (a.steps) a.steps[k] = (uint8_t)steps;
+    }
   }
 }
 
@@ -623,7 +625,8 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
   const int kp = live ? kk : a.np - 1;  // past the end: redo the last patch, store nothing
   const int b = blockIdx.y;
   const long long k = (long long)b * a.np + kp;
-  const int pj = kp / a.nx, pi = kp - pj * a.nx;
+  const int pj = a.nx_mul ? (int)__umulhi((unsigned)kp, a.nx_mul) : kp / a.nx;
+  const int pi = kp - pj * a.nx;
   const int w = a.w, x0 = grid_origin(pi, a.nx, w, PS, a.stride);
   const int y0 = grid_origin(pj, a.ny, a.h, PS, a.stride);
   float u0 = 0.f;
@@ -945,6 +948,14 @@ void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params 
   a.nx = grid_count(w, p.patch_size, a.stride);
   a.ny = grid_count(h, p.patch_size, a.stride);
   a.np = a.nx * a.ny;
+  // m = ceil(2^32 / nx) = (2^32 + e) / nx gives k m / 2^32 = k / nx + k e / (nx 2^32),
+  // whose floor is floor(k / nx) while k e < 2^32 (the remainder is at most nx - 1)
+  a.nx_mul = 0;
+  if (a.nx >= 2) {
+    const unsigned long long m = ((1ull << 32) + (unsigned long long)a.nx - 1) / a.nx;
+    const unsigned long long e = m * (unsigned long long)a.nx - (1ull << 32);
+    if ((unsigned long long)(a.np - 1) * e < (1ull << 32)) a.nx_mul = (unsigned)m;
+  }
   a.total = (long long)a.np * count;
   a.iters = p.iterations;
   a.s = p.window_samples;
@@ -957,8 +968,10 @@ void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params 
   a.fusion = p.fusion;
 }
 
-cudaError_t launch_search(const SearchArgs &a, cudaStream_t st) {
-  if (a.total == 0) return cudaSuccess;
+cudaError_t launch_search(const SearchArgs &args, cudaStream_t st) {
+  if (args.total == 0) return cudaSuccess;
+  SearchArgs a = args;
+  a.debug = (a.u_init || a.posterior || a.flags || a.n_valid || a.steps || a.energies) ? 1 : 0;
   const int count = (int)(a.total / a.np);
   if (a.s == 5 && a.step == 0.5f && count <= 65535) {
     const int cpl = a.cols_per_lane;
