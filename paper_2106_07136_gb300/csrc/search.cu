@@ -46,6 +46,13 @@ __device__ __forceinline__ float group_sum(float v) {
   return v;
 }
 
+template <int G>
+__device__ __forceinline__ int group_sum_int(int v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
 // Split a sample position x - D into integer base and fraction computed from
 // D alone (exact in float): x - D = (x + k) + t with t in [0, 1).
 __device__ __forceinline__ void split_disp(float D, int &k, float &t) {
@@ -266,7 +273,7 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
           s2 = __ffma2_rn(g2[jp][r], m2[jp], s2);  // adds g where valid, exactly
         }
       const float sg = group_sum<G>(s2.x + s2.y);
-      nn = PS * (int)group_sum<G>((float)__popc(code));
+      nn = PS * group_sum_int<G>(__popc(code));
       const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
       const float2 nmg = make_float2(-mg, -mg);
       float2 h2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
@@ -300,7 +307,7 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
           sg += g[j][r];
         }
       sg = group_sum<G>(sg);
-      nn = PS * (int)group_sum<G>((float)__popc(code));
+      nn = PS * group_sum_int<G>(__popc(code));
       const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
       hh = 0.f;
       ct = 0.f;
@@ -468,12 +475,12 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     vc[j] = act[j] && inr && ib + j >= 1 && ib + j + 1 <= lb;
     nc_lane += vc[j] ? 1 : 0;
   }
-  const int nvalid = PS * (int)group_sum<G>((float)nv_lane);
+  const int nvalid = PS * group_sum_int<G>(nv_lane);
   if (a.fusion == BDIS_FUSION_DIS) {
     finish_patch_dis(a, k, live && c == 0, D, u0, last_step, flat, steps, nvalid, PS);
     return;
   }
-  const int nc = PS * (int)group_sum<G>((float)nc_lane);
+  const int nc = PS * group_sum_int<G>(nc_lane);
   // One pass over the rows. Every sample of the lane's columns lies in
   // columns ib - 1 .. ib + CPL, so per row the lane reads those CPL + 2 packed
   // pairs once and interpolates each at both fractions (t for D* and D* +- 1,
