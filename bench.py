@@ -492,6 +492,24 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
                           "enqueued before step i-1 is waited for: pinned host uint8 in, "
                           "float32 disparity out, host wall clock over all steps"}
     res["e2e_blocking"] = blocking
+    # the host link on its own: one step's inputs in and output out as plain
+    # pinned copies (the bound the streamed e2e meets when copies outlast the match)
+    dev_in = torch.empty((2, B, H, W), dtype=torch.uint8, device=device)
+    dev_out = torch.zeros((B, H, W), dtype=torch.float32, device=device)
+    host_out = torch.empty_like(Op).pin_memory()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for rep in range(2):
+        ev[0].record()
+        dev_in[0].copy_(Lp, non_blocking=True)
+        dev_in[1].copy_(Rp, non_blocking=True)
+        ev[1].record()
+        ev[2].record()
+        host_out.copy_(dev_out, non_blocking=True)
+        ev[3].record()
+        torch.cuda.synchronize(device)
+    res["e2e"]["link_gbs"] = {"h2d": 2 * B * W * H / ev[0].elapsed_time(ev[1]) / 1e6,
+                              "d2h": 4 * B * W * H / ev[2].elapsed_time(ev[3]) / 1e6}
+    del dev_in, dev_out, host_out
     # both buffer sets hold exactly the device entry's result for these pairs
     ref_t = m.match(left, right, params)
     torch.cuda.synchronize(device)
