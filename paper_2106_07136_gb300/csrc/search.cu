@@ -38,6 +38,7 @@ namespace bdis {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSearchThreads = 128;  // the fast kernels' launch bound (threads per block)
 
 template <int G>
 __device__ __forceinline__ float group_sum(float v) {
@@ -207,15 +208,29 @@ struct TileRows {
   }
 };
 
-// Inverse-search state of one patch (the group's lanes hold the same scalars;
-// gc is the lane's columns of the centred gradient).
+// The lane's columns of the centred gradient: in registers, or (SHARED) in
+// shared memory with element (j, r) of thread t at p[(j * PS + r) * kSearchThreads]
+// (p = block array + t; consecutive threads hit consecutive banks). Shared
+// storage frees registers where they are the occupancy limit.
+template <int PS, int CPL, bool SHARED>
+struct GcStore {
+  float v[CPL][PS];
+  __device__ __forceinline__ float &at(int j, int r) { return v[j][r]; }
+};
 template <int PS, int CPL>
+struct GcStore<PS, CPL, true> {
+  float *p;
+  __device__ __forceinline__ float &at(int j, int r) { return p[(j * PS + r) * kSearchThreads]; }
+};
+
+// Inverse-search state of one patch (the group's lanes hold the same scalars).
+template <int PS, int CPL, bool SH>
 struct PatchState {
   float D, last_step;
   bool frozen, flat;
   int steps;
   unsigned prev;  // valid-column code the sums below were taken over
-  float gc[CPL][PS];
+  GcStore<PS, CPL, SH> gc;
   float invH, gcT;  // 1 / Hessian, template term of the sums
   // Within one integer base the interpolated sum is linear in the fraction:
   // sum gc (R + t dR) = A + t B, A = sum gc R, B = sum gc dR at base kc.
@@ -225,9 +240,9 @@ struct PatchState {
 
 // One update of Eq. 1 for every patch of the warp. FIRST: the first update,
 // where every patch computes its sums (no votes, no predicated stores).
-template <int PS, int CPL, bool FIRST, class Rows>
+template <int PS, int CPL, bool FIRST, bool SH, class Rows>
 __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &rows,
-                                            PatchState<PS, CPL> &st, const bool (&act)[CPL],
+                                            PatchState<PS, CPL, SH> &st, const bool (&act)[CPL],
                                             int xl, const float *Lc, const float *Gc,
                                             unsigned gbits, float u0) {
   constexpr int LANES = (PS + CPL - 1) / CPL;
@@ -283,8 +298,8 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
         for (int r = 0; r < PS; ++r) {
           const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2[jp]);
           if (need) {
-            st.gc[2 * jp][r] = q.x;
-            st.gc[2 * jp + 1][r] = q.y;
+            st.gc.at(2 * jp, r) = q.x;
+            st.gc.at(2 * jp + 1, r) = q.y;
           }
           float te[2];
 #pragma unroll
@@ -316,7 +331,7 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
 #pragma unroll
         for (int r = 0; r < PS; ++r) {
           const float q = v[j] ? g[j][r] - mg : 0.f;
-          if (need) st.gc[j][r] = q;
+          if (need) st.gc.at(j, r) = q;
           hh = fmaf(q, q, hh);
           ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
         }
@@ -348,8 +363,9 @@ __device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &row
 #pragma unroll
       for (int r = 0; r < PS; ++r) {
         const float2 q = rows.ld(p, r);
-        sa[r & 1] = fmaf(st.gc[j][r], q.x, sa[r & 1]);
-        sb[r & 1] = fmaf(st.gc[j][r], q.y, sb[r & 1]);
+        const float g = st.gc.at(j, r);
+        sa[r & 1] = fmaf(g, q.x, sa[r & 1]);
+        sb[r & 1] = fmaf(g, q.y, sb[r & 1]);
       }
     }
     st.A = group_sum<G>(sa[0] + sa[1]);
@@ -417,10 +433,10 @@ __device__ __forceinline__ void window_rows_pairs(const Rows &rows, int ib, floa
   }
 }
 
-template <int PS, int CPL, class Rows>
+template <int PS, int CPL, bool SH = false, class Rows>
 __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &rows, long long k,
                                             bool live, int c, unsigned gbits, int b, int x0,
-                                            int y0, float u0) {
+                                            int y0, float u0, float *sgc = nullptr) {
   constexpr int LANES = (PS + CPL - 1) / CPL;
   constexpr int G = pow2_at_least(LANES);
   constexpr int S = 5, HALF = 2;
@@ -437,16 +453,17 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
   // sums of a new valid run and in the window, not held through the steps.
 
   // ---- inverse-search iterations (Eq. 1)
-  PatchState<PS, CPL> st;
+  PatchState<PS, CPL, SH> st;
+  if constexpr (SH) st.gc.p = sgc + threadIdx.x;
   st.D = u0;
   st.last_step = 0.f;
   st.frozen = st.flat = false;
   st.steps = 0;
   if (a.iters > 0) {
-    search_step<PS, CPL, true>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
+    search_step<PS, CPL, true, SH>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
     for (int it = 1; it < a.iters; ++it) {
       if (__all_sync(kFull, st.frozen)) break;  // every patch of the warp has stopped
-      search_step<PS, CPL, false>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
+      search_step<PS, CPL, false, SH>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
     }
   }
   const float D = st.D, last_step = st.last_step;
@@ -619,8 +636,9 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
 
 // One patch per group, pairs on blockIdx.y, patches of a pair on blockIdx.x;
 // samples read from global memory (through L1).
-template <int PS, int CPL, int MINB>
-__global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArgs a) {
+// SH: the centred-gradient cache in shared memory (GcStore).
+template <int PS, int CPL, int MINB, bool SH>
+__global__ void __launch_bounds__(kSearchThreads, MINB) search_fixed_kernel(const SearchArgs a) {
   constexpr int LANES = (PS + CPL - 1) / CPL;
   constexpr int G = pow2_at_least(LANES);
   static_assert(G <= 32, "group size");
@@ -642,8 +660,9 @@ __global__ void __launch_bounds__(128, MINB) search_fixed_kernel(const SearchArg
     u0 = 2.f * bilinear_clamped(a.coarse + (long long)b * a.cplane, a.cw, a.ch, cx * 0.5f,
                                 cy * 0.5f);
   }
-  fixed_patch<PS, CPL>(a, GlobalRows{a.R2 + (long long)b * a.plane + (long long)y0 * w, w}, k,
-                      live, c, gbits, b, x0, y0, u0);
+  __shared__ float sgc[SH ? CPL * PS * kSearchThreads : 1];
+  fixed_patch<PS, CPL, SH>(a, GlobalRows{a.R2 + (long long)b * a.plane + (long long)y0 * w, w},
+                           k, live, c, gbits, b, x0, y0, u0, sgc);
 }
 
 __device__ __forceinline__ int warp_min(int v) {
@@ -672,7 +691,7 @@ __device__ __forceinline__ int warp_max(int v) {
 // the second code path cost more per patch than that saves: 5.4 vs 4.6 ms of
 // search per 128 pairs at patch size 8, so it is off by default.
 template <int PS, int CPL, int MINB, int TW>
-__global__ void __launch_bounds__(128, MINB) search_tiled_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(kSearchThreads, MINB) search_tiled_kernel(const SearchArgs a) {
   constexpr int LANES = (PS + CPL - 1) / CPL;
   constexpr int G = pow2_at_least(LANES);
   constexpr int P = 32 / G;  // patches per warp
@@ -870,13 +889,13 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
                expf(-(Ec - Emin) / a.kappa), z, ps);
 }
 
-template <int PS, int CPL, int MINB>
+template <int PS, int CPL, int MINB, bool SH = false>
 cudaError_t launch_fixed(const SearchArgs &a, cudaStream_t st) {
   constexpr int G = pow2_at_least((PS + CPL - 1) / CPL);
   const int threads = a.block_threads == 64 ? 64 : 128, per_block = threads / G;
   const int count = (int)(a.total / a.np);
   const dim3 grid((unsigned)((a.np + per_block - 1) / per_block), (unsigned)count);
-  search_fixed_kernel<PS, CPL, MINB><<<grid, threads, 0, st>>>(a);
+  search_fixed_kernel<PS, CPL, MINB, SH><<<grid, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -985,7 +1004,9 @@ cudaError_t launch_search(const SearchArgs &args, cudaStream_t st) {
     if (a.ps == 8) {
       if (cpl == 1) return launch_fast<8, 1, 8>(a, st);
       if (cpl == 4) return launch_fast<8, 4, 4>(a, st);
-      return launch_fast<8, 2, 7>(a, st);  // 72 registers, no spill: 7 blocks of 128 per SM
+      // 64 registers with the gradient cache in shared memory: 8 blocks of 128 per SM
+      // (the tiled variant keeps it in registers at 72: 7 blocks)
+      return a.tiled ? launch_tiled<8, 2, 7>(a, st) : launch_fixed<8, 2, 8, true>(a, st);
     }
     if (a.ps == 12) return cpl == 1 ? launch_fast<12, 1, 4>(a, st) : launch_fast<12, 3, 3>(a, st);
     if (a.ps == 16) return cpl == 1 ? launch_fast<16, 1, 4>(a, st) : launch_fast<16, 2, 3>(a, st);
