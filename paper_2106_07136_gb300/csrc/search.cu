@@ -1,27 +1,32 @@
 // search.cu -- patch-wise inverse search (Sec. 2.1, Eq. 1) with the Bayesian
 // patch posterior (Sec. 2.2, Eqs. 3-4) and the patch tests, one kernel.
 //
-// Layout: one patch per group of G lanes (G = 4, 8, 16 or 32, the smallest
-// power of two >= patch size), lane c owning column c of its patch and
-// walking the rows. Per lane the template T of its column (and the centred
-// gradient) stays in registers for the whole search; the right image is read
-// as packed (R[x], R[x+1] - R[x]) pairs, so one 8-byte load and one FMA give
-// a linearly interpolated sample. The G lanes of a group read consecutive
-// pairs of one row (coalesced); neighbouring patches overlap, so these loads
-// are served from L1/L2. Reductions over the patch are xor-butterflies inside
-// the group.
+// Layout (fast path): one patch per group of G lanes, each lane owning CPL
+// adjacent columns of its patch and walking the rows (default CPL = 2, G = 4,
+// 8 patches per warp; the generic path takes one column per lane). The right
+// image is read as packed (R[x], R[x+1] - R[x]) pairs, so one 8-byte load and
+// one FMA give a linearly interpolated sample. The G lanes of a group read
+// consecutive pairs of one row (coalesced); neighbouring patches overlap, so
+// these loads are served from L1/L2. Reductions over the patch are
+// xor-butterflies inside the group. The lane's centred gradient is kept
+// through the steps, in registers or (default kernel) in shared memory; the
+// template is re-read where it is used.
 //
 // Arithmetic per patch (the method's own, Eq. 1 and Eq. 3):
 //   - rows are aligned, so the set of pixels whose sample is inside the right
 //     image is a run of columns; its sums (centred gradient, Hessian,
 //     template term) are recomputed only when that run changes;
 //   - with mean normalisation, sum g_n (R~_n - T_n) = sum g_c R~ - sum g_c T
-//     where g_c is the gradient centred on the valid set, so an iteration is
-//     two FMAs and one load per pixel and one group reduction;
+//     where g_c is the gradient centred on the valid set; within one integer
+//     base sum g_c R~ = A + t B is linear in the fraction, so A and B are
+//     re-read (one load and two FMAs per pixel) only when the base or the run
+//     changes in some patch of the warp, and an update is otherwise one FMA;
 //   - the window energies are sums of residuals taken relative to a per-column
 //     shift (the column's first-row residual), merged exactly over the group,
 //     which keeps the saddle decisions well conditioned; per row a lane reads
-//     the CPL + 2 packed pairs that all five samples of its columns need once.
+//     the CPL + 2 packed pairs that all five samples of its columns need once;
+//   - a lane's two columns take the same operations, which run as packed
+//     f32x2 adds and FMAs (per component the scalar rounding).
 //
 // Two instantiations: a fast path with the patch size and window length fixed
 // at compile time (fully unrolled, no per-row guards) for the common settings,
