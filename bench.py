@@ -355,7 +355,9 @@ def main():
     kt = m.read_timing()
     ms = reduce_max_ms(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), device, world)
     value = whole_job_pairs_per_s(B, args.steps, world, ms)
-    launches = (kt["prepare_level0"][1] + 2 * kt["pyramid_level"][1] + kt["search"][1]
+    # a pyramid call is two kernels in variant 0, one otherwise
+    per_pyr = 2 if bd.get_pyramid_variant() == 0 else 1
+    launches = (kt["prepare_level0"][1] + per_pyr * kt["pyramid_level"][1] + kt["search"][1]
                 + kt["densify"][1] + kt["upsample"][1])
 
     gpu_maps = out[:U].cpu().numpy()

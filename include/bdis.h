@@ -354,11 +354,15 @@ int bdis_get_search_tiling(void);
 bdis_status bdis_set_densify_variant(int tile_height);
 int bdis_get_densify_variant(void);
 
-/* Tuning: the pyramid step. 1 (default) = one fused kernel per level
- * (downsample into shared memory, then L, packed R and the gradient written
- * once); 0 = a downsample kernel, then a gradient-and-packing kernel over
- * the new level. Results are identical. Process-wide. */
-void bdis_set_pyramid_variant(int fused);
+/* Tuning: the pyramid (Sec. 2.1). 2 (default) = level 0 and the first
+ * pyramid step in one kernel (the 8-bit views staged once; level 0 written
+ * and never read back for level 1), later steps as in 1; 1 = the level-0
+ * preparation, then one fused kernel per step (downsample into shared
+ * memory, then L, packed R and the gradient written once); 0 = the
+ * preparation, then per step a downsample kernel and a gradient-and-packing
+ * kernel over the new level. Results are identical. Values outside 0..2 are
+ * clamped. Process-wide. bdis_pyramid_level runs one step: fused unless 0. */
+void bdis_set_pyramid_variant(int variant);
 int bdis_get_pyramid_variant(void);
 
 /* Measurement utility, not part of the method: FP32 FMA throughput of the

@@ -300,13 +300,15 @@ def get_densify_variant() -> int:
     return int(_lib.load().bdis_get_densify_variant())
 
 
-def set_pyramid_variant(fused: bool):
-    """Pyramid step: one fused kernel per level (default) or downsample, then gradient."""
-    _lib.load().bdis_set_pyramid_variant(1 if fused else 0)
+def set_pyramid_variant(variant: int):
+    """Pyramid: 2 (default) level 0 and the first step in one kernel, later steps
+    fused; 1 every step one fused kernel; 0 downsample, then gradient, per step.
+    A bool selects 1 (True) or 0 (False)."""
+    _lib.load().bdis_set_pyramid_variant(int(variant))
 
 
-def get_pyramid_variant() -> bool:
-    return bool(_lib.load().bdis_get_pyramid_variant())
+def get_pyramid_variant() -> int:
+    return int(_lib.load().bdis_get_pyramid_variant())
 
 
 def set_net_variant(tensor_path: int):

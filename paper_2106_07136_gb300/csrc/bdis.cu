@@ -297,12 +297,16 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
                         F(lay.warm), st);
     if (e != cudaSuccess) return record_cuda(e);
   }
+  // level 0 and (pyramid variant 2) the first pyramid step in the same launch
+  const bool fuse0 = pyramid_fused() == 2 && p.coarsest_scale >= 1;
   {
     Timed tm(h, 0);
-    e = launch_prepare_level0(left, right, F(lay.L[0]), F2(lay.R[0]), F(lay.G[0]), st);
+    e = fuse0 ? launch_prepare_pyramid0(left, right, F(lay.L[0]), F2(lay.R[0]), F(lay.G[0]),
+                                        F(lay.L[1]), F2(lay.R[1]), F(lay.G[1]), st)
+              : launch_prepare_level0(left, right, F(lay.L[0]), F2(lay.R[0]), F(lay.G[0]), st);
   }
   if (e != cudaSuccess) return record_cuda(e);
-  for (int l = 0; l < p.coarsest_scale; ++l) {
+  for (int l = fuse0 ? 1 : 0; l < p.coarsest_scale; ++l) {
     {
       Timed tm(h, 1);
       e = launch_pyramid_level(F(lay.L[l]), F2(lay.R[l]), lay.lw[l], lay.lh[l], count,
@@ -659,7 +663,7 @@ bdis_status bdis_set_densify_variant(int tile_height) {
 
 int bdis_get_densify_variant(void) { return densify_tile(); }
 
-void bdis_set_pyramid_variant(int fused) { set_pyramid_fused(fused); }
+void bdis_set_pyramid_variant(int variant) { set_pyramid_fused(variant); }
 
 int bdis_get_pyramid_variant(void) { return pyramid_fused(); }
 

@@ -146,6 +146,11 @@ struct DensifyArgs {
 // Launchers (return the launch error, if any).
 cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &right, float *L0,
                                   float2 *R0, float *G0, cudaStream_t st);
+// Level 0 and the first pyramid step in one kernel (the outputs of
+// launch_prepare_level0 then launch_pyramid_level, bit for bit).
+cudaError_t launch_prepare_pyramid0(const bdis_image &left, const bdis_image &right, float *L0,
+                                    float2 *R0, float *G0, float *L1, float2 *R1, float *G1,
+                                    cudaStream_t st);
 cudaError_t launch_pyramid_level(const float *L, const float2 *R, int w, int h, int count,
                                  float *L1, float2 *R1, float *G1, cudaStream_t st);
 cudaError_t launch_pack_right(const float *R, int w, int h, int count, float2 *R2,
@@ -180,7 +185,7 @@ void set_search_tiled(int on);
 int densify_tile();
 void set_densify_tile(int tile_height);
 int pyramid_fused();
-void set_pyramid_fused(int on);
+void set_pyramid_fused(int variant);
 
 // Fill SearchArgs / DensifyArgs geometry from parameters (host).
 void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p);

@@ -169,61 +169,42 @@ constexpr int kStX = 2 * kPyrX + 7, kStY = 2 * kPyrY + 7;  // staged input colum
 constexpr int kStP = 72;                                     // staged row pitch (floats)
 constexpr int kCx = kPyrX + 2;                               // computed columns (with halo)
 
-__global__ void __launch_bounds__(256) pyramid_fused_kernel(
-    const float *__restrict__ L, const float2 *__restrict__ R, int w, int h, int dw, int dh,
-    float *__restrict__ L1, float2 *__restrict__ R1, float *__restrict__ G1) {
-  // the two views side by side, (L, R) per pixel, so that every tap of both
-  // is one 8-byte shared load and one packed f32x2 FMA (per component the
-  // same fma, in the same order, as down_kernel)
-  __shared__ float2 inLR[kStY][kStP];
-  __shared__ float2 hLR[kStY][kCx];
-  __shared__ float2 sLR[kPyrY + 2][kCx];
-  const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const float *Lb = L + (long long)b * w * h;
-  const float2 *Rb = R + (long long)b * w * h;
-  const float k[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
-  // Warps take stage rows, lanes take columns, so every reflected index is
-  // computed once per row (warp) or once per column (lane). Stage row r holds
-  // input row reflect101(2 Y0 - 4 + r), column c input column
-  // reflect101(2 X0 - 4 + c); anything past the last reflected tap is skipped.
-  int xsrc[3];
-  bool xok[3];
-#pragma unroll
-  for (int u = 0; u < 3; ++u) {
-    const int c = lane + 32 * u, xi = 2 * X0 - 4 + c;
-    xok[u] = c < kStX && xi <= w + 1;
-    xsrc[u] = xok[u] ? reflect101(xi, w) : 0;
-  }
-  for (int r = warp; r < kStY; r += nwarp) {
-    const int yi = 2 * Y0 - 4 + r;
-    if (yi > h + 1) break;  // rows only grow from here
-    const size_t rowoff = (size_t)reflect101(yi, h) * w;
-#pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      if (!xok[u]) continue;
-      const int c = lane + 32 * u;
-      const unsigned dl = (unsigned)__cvta_generic_to_shared(&inLR[r][c].x);
-      const unsigned dr = (unsigned)__cvta_generic_to_shared(&inLR[r][c].y);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dl),
-                   "l"(Lb + rowoff + xsrc[u]));
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr),
-                   "l"(Rb + rowoff + xsrc[u]));  // the value is the pair's first word
-    }
-  }
-  // per computed column of this lane (cx = lane, and lanes 0, 1 also take 32, 33):
-  // the stage column of tap 0, at the reflected output coordinate
-  int c0[2];
-  bool cok[2];
+// Stage columns of tap 0 for the computed columns of this lane (cx = lane,
+// and lanes 0, 1 also take 32, 33), at the reflected output coordinate.
+__device__ __forceinline__ void stage_taps(int lane, int X0, int dw, int (&c0)[2], bool (&cok)[2]) {
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
     const int cx = lane + 32 * u, Xr = X0 - 1 + cx;
     cok[u] = cx < kCx && Xr <= dw;
     c0[u] = cok[u] ? 2 * (reflect101(Xr, dw) - X0) + 2 : 0;
   }
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
-  __syncthreads();
-  // horizontal taps of every stage row at every computed column
+}
+
+// Columns of the stage this lane fills (c = lane + 32 u): the input column
+// reflect101(2 X0 - 4 + c), or none past the last reflected tap.
+__device__ __forceinline__ void stage_columns(int lane, int X0, int w, int (&xsrc)[3],
+                                              bool (&xok)[3]) {
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    const int c = lane + 32 * u, xi = 2 * X0 - 4 + c;
+    xok[u] = c < kStX && xi <= w + 1;
+    xsrc[u] = xok[u] ? reflect101(xi, w) : 0;
+  }
+}
+
+// The pyramid step on a staged tile (the stage complete and visible): a
+// horizontal 5-tap pass per stage row and computed column, a vertical 5-tap
+// pass per computed output, then L1, packed R1 and Sobel-x / 8 of L1. The two
+// views sit side by side, (L, R) per pixel, so that every tap of both is one
+// 8-byte shared load and one packed f32x2 FMA (per component the same fma, in
+// the same order, as down_kernel).
+__device__ __forceinline__ void pyramid_passes(const float2 (*inLR)[kStP], float2 (*hLR)[kCx],
+                                               float2 (*sLR)[kCx], const int (&c0)[2],
+                                               const bool (&cok)[2], int b, int X0, int Y0,
+                                               int h, int dw, int dh, float *__restrict__ L1,
+                                               float2 *__restrict__ R1, float *__restrict__ G1) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const float k[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
   for (int r = warp; r < kStY; r += nwarp) {
     if (2 * Y0 - 4 + r > h + 1) break;
 #pragma unroll
@@ -267,6 +248,107 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
   }
 }
 
+__global__ void __launch_bounds__(256) pyramid_fused_kernel(
+    const float *__restrict__ L, const float2 *__restrict__ R, int w, int h, int dw, int dh,
+    float *__restrict__ L1, float2 *__restrict__ R1, float *__restrict__ G1) {
+  __shared__ float2 inLR[kStY][kStP];
+  __shared__ float2 hLR[kStY][kCx];
+  __shared__ float2 sLR[kPyrY + 2][kCx];
+  const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const float *Lb = L + (long long)b * w * h;
+  const float2 *Rb = R + (long long)b * w * h;
+  // Warps take stage rows, lanes take columns, so every reflected index is
+  // computed once per row (warp) or once per column (lane). Stage row r holds
+  // input row reflect101(2 Y0 - 4 + r), column c input column
+  // reflect101(2 X0 - 4 + c); anything past the last reflected tap is skipped.
+  int xsrc[3];
+  bool xok[3];
+  stage_columns(lane, X0, w, xsrc, xok);
+  for (int r = warp; r < kStY; r += nwarp) {
+    const int yi = 2 * Y0 - 4 + r;
+    if (yi > h + 1) break;  // rows only grow from here
+    const size_t rowoff = (size_t)reflect101(yi, h) * w;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (!xok[u]) continue;
+      const int c = lane + 32 * u;
+      const unsigned dl = (unsigned)__cvta_generic_to_shared(&inLR[r][c].x);
+      const unsigned dr = (unsigned)__cvta_generic_to_shared(&inLR[r][c].y);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dl),
+                   "l"(Lb + rowoff + xsrc[u]));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dr),
+                   "l"(Rb + rowoff + xsrc[u]));  // the value is the pair's first word
+    }
+  }
+  int c0[2];
+  bool cok[2];
+  stage_taps(lane, X0, dw, c0, cok);  // while the copies travel
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  pyramid_passes(inLR, hLR, sLR, c0, cok, b, X0, Y0, h, dw, dh, L1, R1, G1);
+}
+
+// Level 0 and the first pyramid step in one pass over the input views: the
+// tile of the step is staged straight from the 8-bit (or float) images, the
+// block writes the level-0 pixels it owns (the 2 kPyrX x 2 kPyrY under its
+// output tile: L0, packed R0 and Sobel-x / 8 of L0, the same values and
+// operations as prepare_level0) from the stage, then runs the pyramid step on
+// it. Level 0 is thus written once and never read back for level 1.
+template <typename T>
+__global__ void __launch_bounds__(256) prepare_pyramid0_kernel(
+    const void *__restrict__ left, const void *__restrict__ right, size_t pitch, size_t stride,
+    int w, int h, int dw, int dh, float *__restrict__ L0, float2 *__restrict__ R0,
+    float *__restrict__ G0, float *__restrict__ L1, float2 *__restrict__ R1,
+    float *__restrict__ G1) {
+  __shared__ float2 inLR[kStY][kStP];
+  __shared__ float2 hLR[kStY][kCx];
+  __shared__ float2 sLR[kPyrY + 2][kCx];
+  const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const char *lb = reinterpret_cast<const char *>(left) + (size_t)b * stride;
+  const char *rb = reinterpret_cast<const char *>(right) + (size_t)b * stride;
+  int xsrc[3];
+  bool xok[3];
+  stage_columns(lane, X0, w, xsrc, xok);
+  for (int r = warp; r < kStY; r += nwarp) {
+    const int yi = 2 * Y0 - 4 + r;
+    if (yi > h + 1) break;
+    const int row = reflect101(yi, h);
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      if (!xok[u]) continue;
+      inLR[r][lane + 32 * u] =
+          make_float2(load_px<T>(lb, pitch, xsrc[u], row), load_px<T>(rb, pitch, xsrc[u], row));
+    }
+  }
+  int c0[2];
+  bool cok[2];
+  stage_taps(lane, X0, dw, c0, cok);
+  __syncthreads();
+  // level 0: pixel (2 X0 + i, 2 Y0 + j) is stage (row j + 4, column i + 4); its
+  // neighbours x +- 1, y +- 1 are the staged reflect-101 ones
+  for (int j = warp; j < 2 * kPyrY; j += nwarp) {
+    const int y = 2 * Y0 + j;
+    if (y >= h) break;
+    const int r = j + 4;
+    for (int i = lane; i < 2 * kPyrX; i += 32) {
+      const int x = 2 * X0 + i;
+      if (x >= w) break;
+      const int c = i + 4;
+      const float2 v = inLR[r][c];
+      const float dm = inLR[r - 1][c + 1].x - inLR[r - 1][c - 1].x;
+      const float d0 = inLR[r][c + 1].x - inLR[r][c - 1].x;
+      const float dp = inLR[r + 1][c + 1].x - inLR[r + 1][c - 1].x;
+      const size_t o = (size_t)b * w * h + (size_t)y * w + x;
+      L0[o] = v.x;
+      G0[o] = (dm + 2.f * d0 + dp) * 0.125f;
+      R0[o] = make_float2(v.y, x + 1 < w ? inLR[r][c + 1].y - v.y : 0.f);
+    }
+  }
+  pyramid_passes(inLR, hLR, sLR, c0, cok, b, X0, Y0, h, dw, dh, L1, R1, G1);
+}
+
 __global__ void pack_right_kernel(const float *__restrict__ R, int w, long long total,
                                   float2 *__restrict__ R2) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -281,12 +363,34 @@ inline unsigned blocks_for(long long n, int threads) {
   return (unsigned)((n + threads - 1) / threads);
 }
 
-int g_pyramid_fused = 1;  // one fused kernel per pyramid level (0: downsample, then gradient)
+// 2: level 0 and the first step in one kernel, later steps fused; 1: every
+// step one fused kernel after the level-0 preparation; 0: downsample, then
+// gradient and packing, per step
+int g_pyramid_fused = 2;
 
 }  // namespace
 
 int pyramid_fused() { return g_pyramid_fused; }
-void set_pyramid_fused(int on) { g_pyramid_fused = on ? 1 : 0; }
+void set_pyramid_fused(int variant) { g_pyramid_fused = variant < 0 ? 0 : (variant > 2 ? 2 : variant); }
+
+cudaError_t launch_prepare_pyramid0(const bdis_image &left, const bdis_image &right, float *L0,
+                                    float2 *R0, float *G0, float *L1, float2 *R1, float *G1,
+                                    cudaStream_t st) {
+  const int w = left.width, h = left.height, dw = (w + 1) / 2, dh = (h + 1) / 2;
+  if ((long long)w * h * left.count == 0) return cudaSuccess;
+  const size_t stride = left.count > 1 ? left.image_stride_bytes : 0;
+  const dim3 grid((unsigned)((dw + kPyrX - 1) / kPyrX), (unsigned)((dh + kPyrY - 1) / kPyrY),
+                  (unsigned)left.count);
+  if (left.format == BDIS_U8)
+    prepare_pyramid0_kernel<uint8_t><<<grid, 256, 0, st>>>(left.data, right.data,
+                                                           left.pitch_bytes, stride, w, h, dw,
+                                                           dh, L0, R0, G0, L1, R1, G1);
+  else
+    prepare_pyramid0_kernel<float><<<grid, 256, 0, st>>>(left.data, right.data, left.pitch_bytes,
+                                                         stride, w, h, dw, dh, L0, R0, G0, L1,
+                                                         R1, G1);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &right, float *L0,
                                   float2 *R0, float *G0, cudaStream_t st) {

@@ -101,6 +101,38 @@ def test_fused_pyramid_matches_two_pass(shape):
             assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("shape", [(61, 97), (35, 47), (120, 160)])
+def test_level0_with_first_step_matches_separate_kernels(matcher, shape):
+    """Pyramid variant 2 (level 0 and the first step from one staging of the
+    input views) gives exactly the disparity of variants 1 and 0 (level 0
+    written, then read back for the first step), for 8-bit views in a pitched
+    buffer and for float views."""
+    h, w = shape
+    pairs = [synth.make_cfg2(seed=synth.stereo.pair_seed(6, i), h=h, w=w) for i in range(2)]
+    L = np.stack([p.left for p in pairs])
+    R = np.stack([p.right for p in pairs])
+    big_l = torch.zeros((2, h, w + 13), dtype=torch.uint8, device="cuda")
+    big_r = torch.zeros_like(big_l)
+    big_l[:, :, 5:5 + w] = dev(L, torch.uint8)
+    big_r[:, :, 5:5 + w] = dev(R, torch.uint8)
+    inputs = [(big_l[:, :, 5:5 + w], big_r[:, :, 5:5 + w]), (dev(L), dev(R))]
+    gp = bd.default_params(patch_size=8, overlap=0.75, iterations=12, coarsest_scale=2,
+                           finest_scale=0, gamma=0.5)
+    old = bd.get_pyramid_variant()
+    try:
+        for l, r in inputs:
+            outs = []
+            for variant in (2, 1, 0):
+                bd.set_pyramid_variant(variant)
+                outs.append(host(matcher.match(l, r, gp)))
+            for o in outs[1:]:
+                assert np.array_equal(np.isnan(o), np.isnan(outs[0]))
+                assert np.array_equal(o[~np.isnan(o)], outs[0][~np.isnan(outs[0])])
+    finally:
+        bd.set_pyramid_variant(old)
+    assert bd.get_pyramid_variant() == 2
+
+
 def test_pitched_and_float_inputs(orc):
     pair = synth.make_cfg1()
     h, w = pair.shape
