@@ -53,6 +53,9 @@ def parse():
                     help="search lane layout: 1, 2 or 4 columns per lane; 0 = library default")
     ap.add_argument("--tiling", type=int, default=0, choices=(0, 1),
                     help="search kernel: 1 = warp-tiled shared-memory sampling (default 0)")
+    ap.add_argument("--pyramid", type=int, default=2, choices=(0, 1, 2),
+                    help="pyramid variant: 2 = level 0 with the first step in one kernel "
+                         "(default), 1 = separate level-0 preparation, 0 = two kernels per step")
     ap.add_argument("--latency-iters", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -314,6 +317,7 @@ def main():
     if args.variant:
         bd.set_search_variant(args.variant)
     bd.set_search_tiling(bool(args.tiling))
+    bd.set_pyramid_variant(args.pyramid)
     B, U = args.batch, min(args.unique, args.batch)
     first = rank_first_pair(rank, U)
     Lh, Rh, Dgt = make_pairs(first, U)
@@ -430,6 +434,7 @@ def main():
                    "patches_per_pair": n_patches,
                    "search_variant": bd.get_search_variant(),
                    "search_tiling": int(bd.get_search_tiling()),
+                   "pyramid_variant": bd.get_pyramid_variant(),
                    "l2": "flushed between timed steps (256 MB write, outside the events)",
                    "parallelism": f"replicas x{world}"},
         "mpix_per_s": value * W * H / 1e6,
