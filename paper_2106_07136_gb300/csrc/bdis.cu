@@ -2,11 +2,12 @@
 // of the BDIS CUDA library (arXiv 2106.07136, Sec. 2).
 //
 // bdis_match enqueues, on the handle's stream:
-//   prepare_level0, (pyramid_level) x coarsest,
-//   then for l = coarsest .. finest: search(l), densify(l),
-//   and an upsample when finest > 0.
-// That is 1 + 2 * coarsest + 2 * (coarsest - finest + 1) (+1) launches per
-// batch, independent of the number of pairs in it.
+//   level 0 with the first pyramid step (one kernel), (pyramid_level) x
+//   (coarsest - 1), then for l = coarsest .. finest: search(l), densify(l),
+//   and an upsample when finest > 0 (pyramid variants 1 and 0: the level-0
+//   preparation, then every step; variant 0 two kernels per step).
+// That is coarsest + 2 * (coarsest - finest + 1) (+1) launches per batch by
+// default, independent of the number of pairs in it.
 #include <stdint.h>
 #include <stdio.h>
 #include <string.h>
