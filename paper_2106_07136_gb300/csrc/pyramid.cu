@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
 template <typename T>
 __global__ void __launch_bounds__(256) prepare_pyramid0_kernel(
     const void *__restrict__ left, const void *__restrict__ right, size_t pitch, size_t stride,
-    int w, int h, int dw, int dh, float *__restrict__ L0, float2 *__restrict__ R0,
+    int w, int h, int dw, int dh, int words, float *__restrict__ L0, float2 *__restrict__ R0,
     float *__restrict__ G0, float *__restrict__ L1, float2 *__restrict__ R1,
     float *__restrict__ G1) {
   __shared__ float2 inLR[kStY][kStP];
@@ -311,15 +311,45 @@ __global__ void __launch_bounds__(256) prepare_pyramid0_kernel(
   int xsrc[3];
   bool xok[3];
   stage_columns(lane, X0, w, xsrc, xok);
-  for (int r = warp; r < kStY; r += nwarp) {
-    const int yi = 2 * Y0 - 4 + r;
-    if (yi > h + 1) break;
-    const int row = reflect101(yi, h);
+  // 8-bit views with 4-byte aligned rows (words != 0), block inside the image
+  // in x: a stage row is 18 aligned 32-bit words (columns 2 X0 - 4 ..
+  // 2 X0 + 67), one per lane, and all of the warp's rows are loaded before any
+  // is stored. Otherwise one element per lane and column, reflected.
+  constexpr int kRowsPerWarp = (kStY + 7) / 8, kWords = (kStX + 3) / 4;
+  if (sizeof(T) == 1 && words && 2 * X0 - 4 >= 0 && 2 * X0 + 4 * kWords - 4 <= w && nwarp == 8) {
+    uint32_t wl[kRowsPerWarp], wr[kRowsPerWarp];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      if (!xok[u]) continue;
-      inLR[r][lane + 32 * u] =
-          make_float2(load_px<T>(lb, pitch, xsrc[u], row), load_px<T>(rb, pitch, xsrc[u], row));
+    for (int q = 0; q < kRowsPerWarp; ++q) {
+      const int r = warp + 8 * q, yi = 2 * Y0 - 4 + r;
+      const bool rok = lane < kWords && r < kStY && yi <= h + 1;
+      const size_t off = (size_t)(rok ? reflect101(yi, h) : 0) * pitch + (size_t)(2 * X0 - 4);
+      wl[q] = rok ? __ldg(reinterpret_cast<const uint32_t *>(lb + off) + lane) : 0u;
+      wr[q] = rok ? __ldg(reinterpret_cast<const uint32_t *>(rb + off) + lane) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < kRowsPerWarp; ++q) {
+      const int r = warp + 8 * q;
+      if (r >= kStY || 2 * Y0 - 4 + r > h + 1) break;
+      if (lane >= kWords) continue;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = 4 * lane + e;
+        if (c < kStX)
+          inLR[r][c] = make_float2((float)((wl[q] >> (8 * e)) & 0xffu),
+                                   (float)((wr[q] >> (8 * e)) & 0xffu));
+      }
+    }
+  } else {
+    for (int r = warp; r < kStY; r += nwarp) {
+      const int yi = 2 * Y0 - 4 + r;
+      if (yi > h + 1) break;
+      const int row = reflect101(yi, h);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        if (!xok[u]) continue;
+        inLR[r][lane + 32 * u] = make_float2(load_px<T>(lb, pitch, xsrc[u], row),
+                                             load_px<T>(rb, pitch, xsrc[u], row));
+      }
     }
   }
   int c0[2];
@@ -381,13 +411,18 @@ cudaError_t launch_prepare_pyramid0(const bdis_image &left, const bdis_image &ri
   const size_t stride = left.count > 1 ? left.image_stride_bytes : 0;
   const dim3 grid((unsigned)((dw + kPyrX - 1) / kPyrX), (unsigned)((dh + kPyrY - 1) / kPyrY),
                   (unsigned)left.count);
+  // whole aligned 32-bit words per row for the 8-bit staging fast path
+  const int words = left.format == BDIS_U8 && left.pitch_bytes % 4 == 0 && stride % 4 == 0 &&
+                    right.pitch_bytes == left.pitch_bytes &&
+                    (reinterpret_cast<uintptr_t>(left.data) & 3) == 0 &&
+                    (reinterpret_cast<uintptr_t>(right.data) & 3) == 0;
   if (left.format == BDIS_U8)
     prepare_pyramid0_kernel<uint8_t><<<grid, 256, 0, st>>>(left.data, right.data,
                                                            left.pitch_bytes, stride, w, h, dw,
-                                                           dh, L0, R0, G0, L1, R1, G1);
+                                                           dh, words, L0, R0, G0, L1, R1, G1);
   else
     prepare_pyramid0_kernel<float><<<grid, 256, 0, st>>>(left.data, right.data, left.pitch_bytes,
-                                                         stride, w, h, dw, dh, L0, R0, G0, L1,
+                                                         stride, w, h, dw, dh, 0, L0, R0, G0, L1,
                                                          R1, G1);
   return cudaGetLastError();
 }

@@ -106,7 +106,8 @@ def test_level0_with_first_step_matches_separate_kernels(matcher, shape):
     """Pyramid variant 2 (level 0 and the first step from one staging of the
     input views) gives exactly the disparity of variants 1 and 0 (level 0
     written, then read back for the first step), for 8-bit views in a pitched
-    buffer and for float views."""
+    buffer, dense 8-bit views (at 160 wide the middle block stages whole
+    32-bit words) and float views."""
     h, w = shape
     pairs = [synth.make_cfg2(seed=synth.stereo.pair_seed(6, i), h=h, w=w) for i in range(2)]
     L = np.stack([p.left for p in pairs])
@@ -115,7 +116,8 @@ def test_level0_with_first_step_matches_separate_kernels(matcher, shape):
     big_r = torch.zeros_like(big_l)
     big_l[:, :, 5:5 + w] = dev(L, torch.uint8)
     big_r[:, :, 5:5 + w] = dev(R, torch.uint8)
-    inputs = [(big_l[:, :, 5:5 + w], big_r[:, :, 5:5 + w]), (dev(L), dev(R))]
+    inputs = [(big_l[:, :, 5:5 + w], big_r[:, :, 5:5 + w]), (dev(L), dev(R)),
+              (dev(L, torch.uint8), dev(R, torch.uint8))]  # dense: 4-byte rows where w % 4 == 0
     gp = bd.default_params(patch_size=8, overlap=0.75, iterations=12, coarsest_scale=2,
                            finest_scale=0, gamma=0.5)
     old = bd.get_pyramid_variant()
