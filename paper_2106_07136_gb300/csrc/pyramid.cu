@@ -14,7 +14,10 @@
 // prepare_level0: reads 2 B/px (uint8 pair), writes 16 B/px (L, packed R, G).
 // pyramid_level (per output px): reads 4 input px of each view (~24 B with
 // halo reuse from L1), writes 8 B; the gradient/packing pass reads 8 B and
-// writes 8 B.
+// writes 8 B. The fused pyramid step reads 12 B per input px once (staged
+// tile) and writes 16 B per output px. prepare_pyramid0 (the default first
+// launch) reads 2 B per level-0 px and writes level 0 (16 B/px) and level 1
+// (16 B per level-1 px): level 0 is not read back for the first step.
 #include "bdis_internal.cuh"
 
 namespace bdis {
