@@ -235,17 +235,18 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
     sum_row(wv, dv, A, B);
   };
   const int ylast = a.h - PS;  // first pixel row the last patch row covers
-  float lastA = 0.f, lastB = 0.f;
+  float2 last = make_float2(0.f, 0.f);
   bool have_last = false;
-  // ring of the regular rows g - M + 1 .. g (slot k holds row g - M + 1 + k)
-  float rA[M], rB[M];
+  // ring of the regular rows g - M + 1 .. g (slot k holds row g - M + 1 + k),
+  // each as its (x-weighted numerator, denominator) pair
+  float2 rAB[M];
 #pragma unroll
   for (int k = 0; k < M - 1; ++k) {
     const int j = g0 - M + 1 + k;
-    rA[k + 1] = 0.f;
-    rB[k + 1] = 0.f;
-    if (j >= 0 && j <= a.ny - 2) row_sums(j, rA[k + 1], rB[k + 1]);
+    rAB[k + 1] = make_float2(0.f, 0.f);
+    if (j >= 0 && j <= a.ny - 2) row_sums(j, rAB[k + 1].x, rAB[k + 1].y);
   }
+
   const long long obase = (long long)b * a.plane + x;
   const int yend = min(Y0 + K, a.h);
   float nw[M + 1], nd[M + 1];  // row g's loads, issued during group g - 1
@@ -259,13 +260,16 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
     }
     if (g + 1 <= a.ny - 2 && (g + 1) * S < yend) load_row(g + 1, nw, nd);
 #pragma unroll
-    for (int k = 0; k < M - 1; ++k) {
-      rA[k] = rA[k + 1];
-      rB[k] = rB[k + 1];
+    for (int k = 0; k < M - 1; ++k) rAB[k] = rAB[k + 1];
+    rAB[M - 1] = make_float2(0.f, 0.f);
+    if (g <= a.ny - 2) sum_row(cw, cd, rAB[M - 1].x, rAB[M - 1].y);
+    // the covering regular rows of this group (the same for all its pixel rows)
+    bool kin[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const int j = g - M + 1 + k;
+      kin[k] = j >= 0 && j <= a.ny - 2;
     }
-    rA[M - 1] = 0.f;
-    rB[M - 1] = 0.f;
-    if (g <= a.ny - 2) sum_row(cw, cd, rA[M - 1], rB[M - 1]);
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       const int y = g * S + t;
@@ -274,19 +278,18 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
       // per component the same fma as the tiled kernel
       float2 nd2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        const int j = g - M + 1 + k;
-        if (j < 0 || j > a.ny - 2) continue;
-        const float my = smask[t + (M - 1 - k) * S];
-        nd2 = __ffma2_rn(make_float2(my, my), make_float2(rA[k], rB[k]), nd2);
-      }
+      for (int k = 0; k < M; ++k)
+        if (kin[k]) {
+          const float my = smask[t + (M - 1 - k) * S];
+          nd2 = __ffma2_rn(make_float2(my, my), rAB[k], nd2);
+        }
       if (y >= ylast) {
         if (!have_last) {
-          row_sums(a.ny - 1, lastA, lastB);
+          row_sums(a.ny - 1, last.x, last.y);
           have_last = true;
         }
         const float my = mask_at(y - ylast);
-        nd2 = __ffma2_rn(make_float2(my, my), make_float2(lastA, lastB), nd2);
+        nd2 = __ffma2_rn(make_float2(my, my), last, nd2);
       }
       const float num = nd2.x, den = nd2.y;
       float out;
