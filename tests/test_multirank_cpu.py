@@ -4,6 +4,7 @@ The path has no exchange step (pairs are independent), so ranks are
 replicas: each works on its own seeded pairs and the ranks meet only to take
 the slowest rank's time. No GPU is used here.
 """
+import json
 import os
 import socket
 import subprocess
@@ -61,3 +62,17 @@ def test_reference_arm_runs_on_rank0_only():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True,
                        text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_recorded_traffic_only_for_the_source_it_was_taken_on(monkeypatch):
+    """bench.py reports the search class's DRAM traffic from the committed
+    counters only while csrc/search.cu is the source they were taken on;
+    for any other source the roofline's traffic is null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "search_traffic.json")))["ps8"]
+    monkeypatch.setattr(bench, "search_src_sha", lambda: rec["search_cu_sha256_16"])
+    assert bench.recorded_traffic(8) == rec["dram_bytes_per_pair"]
+    assert bench.recorded_traffic(12) is None  # no record for patch 12
+    monkeypatch.setattr(bench, "search_src_sha", lambda: "0" * 16)
+    assert bench.recorded_traffic(8) is None
