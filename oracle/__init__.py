@@ -24,6 +24,7 @@ from .oracle import (  # noqa: F401
     match,
     match_seeded,
     match_stages,
+    select_start,
     warm_map,
     FLAG_FLAT,
     FLAG_DIVERGED,

@@ -525,6 +525,30 @@ void orc_upsample(const double *M, int mw, int mh, int f, int w, int h, double *
 
 /* ------------------------------------------------------------ the method */
 
+/* R16, the per-patch choice on the level searched twice: result a (searched
+ * from the seed) is kept only if a is kept, it is not within
+ * ORC_SAME_SOLUTION px of a kept result b (searched from the plain start;
+ * that close, both found one solution and the plain one stands), and b is
+ * dropped or has no higher posterior. Otherwise b's D* and weight overwrite
+ * a's. use_a (may be NULL) receives 1 where a was kept, else 0. */
+void orc_select_start(int np, double *d_a, double *w_a, const double *post_a,
+                      const int *fl_a, const double *d_b, const double *w_b,
+                      const double *post_b, const int *fl_b, int *use_a)
+{
+    const int drop = ORC_FLAG_DIVERGED | ORC_FLAG_SADDLE | ORC_FLAG_GAMMA | ORC_FLAG_EMPTY |
+                     ORC_FLAG_UNCONVERGED;
+    for (int k = 0; k < np; ++k) {
+        int same = !(fl_a[k] & drop) && !(fl_b[k] & drop) &&
+                   fabs(d_a[k] - d_b[k]) <= ORC_SAME_SOLUTION;
+        int use_seed = !same && !(fl_a[k] & drop) && ((fl_b[k] & drop) || post_a[k] >= post_b[k]);
+        if (!use_seed) {
+            d_a[k] = d_b[k];
+            w_a[k] = w_b[k];
+        }
+        if (use_a) use_a[k] = use_seed;
+    }
+}
+
 int orc_match_warm(const double *left, const double *right, int w, int h, const orc_params *p,
                    const double *prev, double *out);
 int orc_match_seeded(const double *left, const double *right, int w, int h,
@@ -608,19 +632,7 @@ int orc_match_seeded(const double *left, const double *right, int w, int h,
                              fl_a, NULL, NULL, NULL);
             orc_search_level(Lp[l], Rp[l], G, W, H, NULL, 0, 0, p, NULL, dst_b, post_b, wgt_b,
                              fl_b, NULL, NULL, NULL);
-            const int drop = ORC_FLAG_DIVERGED | ORC_FLAG_SADDLE | ORC_FLAG_GAMMA |
-                             ORC_FLAG_EMPTY | ORC_FLAG_UNCONVERGED;
-            for (int k = 0; k < np; ++k) {
-                /* both kept and within ORC_SAME_SOLUTION px: one solution, the plain one */
-                int same = !(fl_a[k] & drop) && !(fl_b[k] & drop) &&
-                           fabs(dst[k] - dst_b[k]) <= ORC_SAME_SOLUTION;
-                int use_seed = !same && !(fl_a[k] & drop) &&
-                               ((fl_b[k] & drop) || post_a[k] >= post_b[k]);
-                if (!use_seed) {
-                    dst[k] = dst_b[k];
-                    wgt[k] = wgt_b[k];
-                }
-            }
+            orc_select_start(np, dst, wgt, post_a, fl_a, dst_b, wgt_b, post_b, fl_b, NULL);
             free(post_a);
             free(dst_b);
             free(wgt_b);

@@ -104,6 +104,7 @@ def load():
         lib.orc_match_warm.argtypes = [dp, dp, i, i, pp, dp, dp]
         lib.orc_warm_map.argtypes = [dp, i, i, i, dp]
         lib.orc_match_seeded.argtypes = [dp, dp, i, i, pp, dp, i, i, dp]
+        lib.orc_select_start.argtypes = [i, dp, dp, dp, ip, dp, dp, dp, ip, ip]
         _lib = lib
     return _lib
 
@@ -295,9 +296,29 @@ def match_seeded(left, right, params: OracleParams, seed, seed_level, fallback=T
     return out
 
 
-def match_stages(left, right, params: OracleParams) -> dict:
+def select_start(a: dict, b: dict):
+    """R16 per-patch choice between search_level results a (from the seed) and
+    b (from the plain start): returns (d_star, weight, use_a) after the choice."""
+    d = np.array(a["d_star"], dtype=np.float64, order="C")
+    wt = np.array(a["weight"], dtype=np.float64, order="C")
+    fa = np.ascontiguousarray(a["flags"], dtype=np.int32)
+    fb = np.ascontiguousarray(b["flags"], dtype=np.int32)
+    pa, pb = _f64(a["posterior"]), _f64(b["posterior"])
+    db, wb = _f64(b["d_star"]), _f64(b["weight"])
+    use = np.empty(d.shape, dtype=np.int32)
+    load().orc_select_start(int(d.size), _dp(d), _dp(wt), _dp(pa), _ip(fa), _dp(db), _dp(wb),
+                            _dp(pb), _ip(fb), _ip(use))
+    return d, wt, use.astype(bool)
+
+
+def match_stages(left, right, params: OracleParams, prev=None, seed=None, seed_level=0,
+                 fallback=False) -> dict:
     """The method step by step through the per-stage C functions, keeping
-    every intermediate: levels[l] = {L, R, G, search outputs, dense}."""
+    every intermediate: levels[l] = {L, R, G, coarse, search outputs, dense}.
+
+    prev: warm start from a previous full-size disparity (R15); seed /
+    seed_level / fallback: proposal start (R16); with fallback the coarsest
+    level also holds the plain search ("plain") and the choice ("use_seed")."""
     top, fin = params.coarsest_scale, params.finest_scale
     Ls, Rs = [_f64(left)], [_f64(right)]
     for _ in range(top):
@@ -305,12 +326,25 @@ def match_stages(left, right, params: OracleParams) -> dict:
         Rs.append(downsample(Rs[-1]))
     levels = {}
     coarse = None
+    if prev is not None:
+        coarse = warm_map(prev, top + 1)
+    elif seed is not None:
+        coarse = warm_map(seed, top + 1 - seed_level)
     for lvl in range(top, fin - 1, -1):
         G = sobel_x(Ls[lvl])
         srch = search_level(Ls[lvl], Rs[lvl], G, coarse, params)
-        dense = densify_level(Ls[lvl].shape, params, srch["d_star"], srch["weight"], coarse,
+        carry = coarse
+        extra = {}
+        if seed is not None and fallback and lvl == top:
+            plain = search_level(Ls[lvl], Rs[lvl], G, None, params)
+            d, wt, use = select_start(srch, plain)
+            extra = dict(seeded=dict(srch), plain=plain, use_seed=use)
+            srch = dict(srch, d_star=d, weight=wt)
+            carry = None  # carried pixels keep the plain start
+        dense = densify_level(Ls[lvl].shape, params, srch["d_star"], srch["weight"], carry,
                               lvl == fin, Ls[lvl], Rs[lvl])
-        levels[lvl] = dict(L=Ls[lvl], R=Rs[lvl], G=G, coarse=coarse, dense=dense, **srch)
+        levels[lvl] = dict(L=Ls[lvl], R=Rs[lvl], G=G, coarse=coarse, carry=carry, dense=dense,
+                           **srch, **extra)
         coarse = dense
     out = coarse if fin == 0 else upsample(coarse, fin, left.shape)
     return {"levels": levels, "out": out, "pyramid_L": Ls, "pyramid_R": Rs}

@@ -664,3 +664,56 @@ def test_good_proposal_is_kept_where_the_plain_start_fails(orc):
     est = np.isfinite(out) & np.isfinite(pair.disp)
     assert est.sum() > 0.9 * np.isfinite(pair.disp).sum()
     assert np.median(np.abs(out[est] - k)) < 1e-3
+
+
+def test_stagewise_warm_and_seeded_equal_match(orc):
+    """The staged run with a warm start (R15) or a seed map with and without
+    the fallback search (R16) is exactly the oracle's whole-method entry."""
+    pair = synth.make_cfg2(seed=synth.stereo.pair_seed(2, 9), h=120, w=160)
+    p = orc.OracleParams.make(patch_size=8, overlap=0.75, iterations=12, coarsest_scale=2,
+                              gamma=0.5)
+    prev = orc.match(pair.left, pair.right, p)
+    a = orc.match_stages(pair.left, pair.right, p, prev=prev)["out"]
+    b = orc.match(pair.left, pair.right, p, prev=prev)
+    assert np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(a[~np.isnan(a)],
+                                                                       b[~np.isnan(b)])
+    seed = orc.match_stages(pair.left, pair.right, p)["levels"][1]["dense"] + 0.7
+    for fb in (False, True):
+        st = orc.match_stages(pair.left, pair.right, p, seed=seed, seed_level=1, fallback=fb)
+        b = orc.match_seeded(pair.left, pair.right, p, seed, 1, fallback=fb)
+        a = st["out"]
+        assert np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(a[~np.isnan(a)],
+                                                                           b[~np.isnan(b)])
+        assert ("use_seed" in st["levels"][2]) == fb
+
+
+def test_select_start_truth_table(orc):
+    """R16's per-patch choice on hand-built cases: the seeded result a stands
+    only if it is kept, is not within 0.1 px of a kept plain result b, and b
+    is dropped or has no higher posterior."""
+    # (a kept, b kept, d_a, d_b, p_a, p_b) -> keep a?
+    cases = [
+        (True, True, 3.0, 1.0, 0.5, 0.4, True),    # both kept, a more probable
+        (True, True, 3.0, 1.0, 0.4, 0.4, True),    # tie keeps a
+        (True, True, 3.0, 1.0, 0.3, 0.4, False),   # b more probable
+        (True, False, 3.0, 1.0, 0.1, 0.9, True),   # b dropped
+        (False, True, 3.0, 1.0, 0.9, 0.1, False),  # a dropped
+        (False, False, 3.0, 1.0, 0.9, 0.1, False),  # both dropped: b's (zero) weight
+        (True, True, 1.05, 1.0, 0.9, 0.1, False),  # one solution: the plain one
+        (True, True, 1.09375, 1.0, 0.9, 0.1, False),  # within 0.1 px: one solution
+        (True, True, 1.2, 1.0, 0.9, 0.1, True),
+        (True, False, 1.05, 1.0, 0.9, 0.1, True),  # b dropped: no same-solution rule
+    ]
+    a = {k: np.array(v, dtype=np.float64) for k, v in
+         {"d_star": [c[2] for c in cases], "posterior": [c[4] for c in cases],
+          "weight": [10.0 + i for i in range(len(cases))]}.items()}
+    a["flags"] = np.array([0 if c[0] else 4 for c in cases], dtype=np.int32)
+    b = {k: np.array(v, dtype=np.float64) for k, v in
+         {"d_star": [c[3] for c in cases], "posterior": [c[5] for c in cases],
+          "weight": [20.0 + i for i in range(len(cases))]}.items()}
+    b["flags"] = np.array([0 if c[1] else 8 for c in cases], dtype=np.int32)
+    d, w, use = orc.select_start(a, b)
+    want = np.array([c[6] for c in cases])
+    assert np.array_equal(use, want)
+    assert np.array_equal(d, np.where(want, a["d_star"], b["d_star"]))
+    assert np.array_equal(w, np.where(want, a["weight"], b["weight"]))
