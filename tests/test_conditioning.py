@@ -7,12 +7,13 @@ input. The measure used here is how far the oracle lands from itself when the
 coarse-level disparity that seeds each finer level carries one float32
 rounding (relative 1e-6, several draws).
 
-The GPU end-to-end tests hold most inputs to the fixed R13 bar (99.9% of
-pixels within 0.01 px, at most 0.1% beyond 0.05 px or with a different mask).
-That bar is only meaningful where the oracle itself stays well inside it, so
-each such input is pinned here as well-conditioned: in every draw, within the
-bar. One ill-conditioned input is pinned as such; its GPU test uses the
-oracle's own spread as the bar instead.
+Every GPU end-to-end test explains each of its differences from the oracle
+level by level (tests/attribution.py). Most inputs are also held to the
+method's 99.9% bar (pixels within 0.01 px). That bar is only meaningful where
+the oracle itself stays well inside it, so each such input is pinned here as
+well-conditioned: in every draw, within the bar (99.9% within 0.01 px, at most
+0.1% beyond 0.05 px or with a different mask). One ill-conditioned input is
+pinned as such; its GPU test is held to the attribution alone.
 """
 import numpy as np
 import pytest
@@ -83,7 +84,7 @@ def test_warm_start_stream_is_well_conditioned(orc):
 
 
 def test_ill_conditioned_pair_exceeds_the_fixed_bar(orc):
-    """The pair whose GPU test uses the self-sensitivity bar: one float32
+    """The pair whose GPU test is held to the attribution alone: one float32
     rounding of the oracle's own coarse maps already moves it past the fixed
     bar in some draw."""
     p = synth.make_pair(*ILL_CONDITIONED_PAIR)

@@ -6,7 +6,7 @@ import torch
 
 import paper_2106_07136_gb300 as bd
 import synth
-from gpu_helpers import SEEDED_PAIR, assert_e2e, dev, host
+from gpu_helpers import SEEDED_PAIR, assert_explained, dev, host
 
 pytestmark = pytest.mark.gpu
 
@@ -41,8 +41,8 @@ def test_seeded_matches_oracle(orc, pair, matcher, fallback):
     seed = level3_proposal(orc, pair)
     out = host(matcher.match_seeded(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8),
                                     dev(seed), 3, gp, fallback=fallback))
-    ref = orc.match_seeded(pair.left, pair.right, op, seed, 3, fallback=fallback)
-    assert_e2e(out, ref, f"seeded fallback={fallback}")
+    assert_explained(orc, out, pair.left, pair.right, gp, op, f"seeded fallback={fallback}",
+                     seed=seed, seed_level=3, fallback=fallback)
 
 
 def test_rejected_proposal_gives_the_plain_result(pair, matcher):
@@ -67,6 +67,6 @@ def test_learned_start_equals_seeding_with_the_net_output(orc, pair, matcher):
     b = host(matcher.match_seeded(L, R, prop, 3, gp, fallback=True))
     assert np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(a[np.isfinite(a)],
                                                                        b[np.isfinite(b)])
-    ref = orc.match_seeded(pair.left, pair.right, op, host(prop)[0], 3, fallback=True)
-    assert_e2e(a, ref, "learned vs oracle seeded with the same proposal")
+    assert_explained(orc, a, pair.left, pair.right, gp, op,
+                     "learned vs oracle seeded with the same proposal", net=net, fallback=True)
     net.close()

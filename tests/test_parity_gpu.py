@@ -11,9 +11,7 @@ import torch
 import paper_2106_07136_gb300 as bd
 import synth
 from gpu_helpers import (DENSE_ATOL, DROP, DSTAR_ATOL, ILL_CONDITIONED_PAIR, POST_ATOL, PYR_ATOL,
-                         assert_e2e,
-                         assert_e2e_within_self_sensitivity, dev, explained_flag_mismatch, host,
-                         oracle_unstable)
+                         assert_explained, dev, explained_flag_mismatch, host, oracle_unstable)
 
 pytestmark = pytest.mark.gpu
 
@@ -320,31 +318,28 @@ def test_upsample_stage(orc):
 
 def test_e2e_cfg1(orc, cfg1, matcher):
     gp, op = params(orc, **CFG1)
-    ref = orc.match(cfg1.left, cfg1.right, op)
     out = host(matcher.match(dev(cfg1.left, torch.uint8), dev(cfg1.right, torch.uint8), gp))
-    assert_e2e(out, ref, "cfg1")
+    assert_explained(orc, out, cfg1.left, cfg1.right, gp, op, "cfg1")
 
 
 @pytest.mark.parametrize("search_variant", [1, 2, 4], indirect=True)
 @pytest.mark.parametrize("ps", [8, 12])
 def test_e2e_cfg2(orc, cfg2, matcher, ps, search_variant):
     gp, op = params(orc, **dict(CFG2, patch_size=ps))
-    ref = orc.match(cfg2.left, cfg2.right, op)
     out = host(matcher.match(dev(cfg2.left, torch.uint8), dev(cfg2.right, torch.uint8), gp))
-    assert_e2e(out, ref, f"cfg2 ps{ps}")
+    assert_explained(orc, out, cfg2.left, cfg2.right, gp, op, f"cfg2 ps{ps}")
 
 
 @pytest.mark.parametrize("search_variant", [1, 2, 4], indirect=True)
 def test_e2e_ill_conditioned_pair(orc, matcher, search_variant):
     """A pair on which one float32 rounding of the oracle's own coarse maps
-    already moves it past the fixed bar: the kernels may differ from the
-    oracle by no more than the oracle differs from itself."""
+    already moves it past the 99.9% bar: every difference from the oracle must
+    still be explained by decisions float32 cannot resolve."""
     pair = synth.make_pair(*ILL_CONDITIONED_PAIR)
     gp, op = params(orc, **CFG2)
-    ref = orc.match(pair.left, pair.right, op)
     out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
-    assert_e2e_within_self_sensitivity(out, ref, orc, pair.left, pair.right, op,
-                                       f"ill-conditioned pair, variant {search_variant}")
+    assert_explained(orc, out, pair.left, pair.right, gp, op,
+                     f"ill-conditioned pair, variant {search_variant}", budget=False)
 
 
 @pytest.mark.parametrize("shape,kw", [
@@ -357,9 +352,8 @@ def test_e2e_ragged_and_variants(orc, shape, kw, matcher):
     h, w = shape
     pair = synth.make_cfg1(seed=synth.stereo.pair_seed(1, 7), h=h, w=w)
     gp, op = params(orc, **kw)
-    ref = orc.match(pair.left, pair.right, op)
     out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
-    assert_e2e(out, ref, str((shape, kw)))
+    assert_explained(orc, out, pair.left, pair.right, gp, op, str((shape, kw)))
 
 
 def test_batch_equals_single_pairs(orc, matcher):
@@ -370,7 +364,7 @@ def test_batch_equals_single_pairs(orc, matcher):
         single = host(matcher.match(dev(L[b], torch.uint8), dev(R[b], torch.uint8), gp))
         assert np.array_equal(np.isnan(single), np.isnan(outb[b]))
         assert np.array_equal(single[~np.isnan(single)], outb[b][~np.isnan(single)])
-        assert_e2e(outb[b], orc.match(L[b], R[b], op), f"pair {b}")
+        assert_explained(orc, outb[b], L[b], R[b], gp, op, f"pair {b}")
 
 
 @pytest.mark.parametrize("count,pinned", [(1, True), (2, True), (3, True), (8, True), (13, True),
@@ -485,7 +479,7 @@ def test_bench_launch_configuration(orc, matcher):
     gp, op = params(orc, **CFG2)
     out = host(matcher.match(dev(Lb, torch.uint8), dev(Rb, torch.uint8), gp))
     for i in (0, 5):
-        assert_e2e(out[i], orc.match(L[i], R[i], op), f"batch pair {i}")
+        assert_explained(orc, out[i], L[i], R[i], gp, op, f"batch pair {i}")
     for i in (0, 5, 11):
         for rep in (1, 7):
             a, b = out[i], out[i + 16 * rep]
@@ -497,9 +491,8 @@ def test_full_hd_frame(orc, matcher):
     pair = synth.make_cfg2(seed=synth.stereo.pair_seed(3, 0), h=1080, w=1920)
     kw = dict(CFG2, coarsest_scale=5)
     gp, op = params(orc, **kw)
-    ref = orc.match(pair.left, pair.right, op)
     out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
-    assert_e2e(out, ref, "1920x1080")
+    assert_explained(orc, out, pair.left, pair.right, gp, op, "1920x1080")
 
 
 # ----------------------------------------------------- DIS fusion (Eq. 2)
@@ -532,6 +525,7 @@ def test_dis_search_and_densify_stages(orc, cfg1):
 def test_dis_e2e(orc, cfg1, cfg2, matcher, which):
     pair, kw = (cfg1, CFG1) if which == "cfg1" else (cfg2, CFG2)
     gp, op = params(orc, **dict(kw, fusion=1))
-    ref = orc.match(pair.left, pair.right, op)
     out = host(matcher.match(dev(pair.left, torch.uint8), dev(pair.right, torch.uint8), gp))
-    assert_e2e_within_self_sensitivity(out, ref, orc, pair.left, pair.right, op, f"dis {which}")
+    # DIS fuses every patch, runaway ones included: ill-conditioned at float32
+    # resolution (R14), so no 99.9% bar, but every difference explained
+    assert_explained(orc, out, pair.left, pair.right, gp, op, f"dis {which}", budget=False)

@@ -1,10 +1,11 @@
 """Mixed-resolution batches in one CUDA graph (bdis_plan_*), GPU.
 
-The plan must reproduce, for every group, what bdis_match computes for that
-group alone (within the end-to-end tolerance: the autotuner may pick other
-lane layouts, which change float rounding only), the oracle on a sampled pair
-of each size, and identical results on a second graph launch; refilled inputs
-must be picked up because the graph binds buffers by address.
+The plan must reproduce, for every pair of every group, exactly what the
+library's step entry points compute with the lane layout the autotuner chose
+for each level (other layouts change float rounding only), the oracle on a
+sampled pair of each size with every difference explained, and identical
+results on a second graph launch; refilled inputs must be picked up because
+the graph binds buffers by address.
 """
 import numpy as np
 import pytest
@@ -12,7 +13,7 @@ import torch
 
 import paper_2106_07136_gb300 as bd
 import synth
-from gpu_helpers import assert_e2e, dev, host
+from gpu_helpers import assert_explained, dev, gpu_stages, host, same_map
 
 pytestmark = pytest.mark.gpu
 
@@ -44,13 +45,15 @@ def test_plan_matches_per_group_calls_and_oracle(orc, autotune):
     plan.run()
     torch.cuda.synchronize()
     first_run = [host(g[2]).copy() for g in groups]
-    m = bd.Matcher()
+    variants = []
     for gi, (L, R, out) in enumerate(groups):
-        single = host(m.match(L, R, params))
+        var = {lvl: plan.choice(gi, lvl)["search_columns_per_lane"] for lvl in plan.levels}
+        variants.append(var)
         for b in range(L.shape[0]):
-            assert_e2e(first_run[gi][b], single[b], f"group {gi} pair {b} vs bdis_match")
-        ref = orc.match(pairs[gi][0].left, pairs[gi][0].right, op)
-        assert_e2e(first_run[gi][0], ref, f"group {gi} vs oracle")
+            _, g_out = gpu_stages(pairs[gi][b].left, pairs[gi][b].right, params, variants=var)
+            assert same_map(first_run[gi][b], g_out), (gi, b)
+        assert_explained(orc, first_run[gi][0], pairs[gi][0].left, pairs[gi][0].right, params,
+                         op, f"group {gi} vs oracle", variants=var)
         if autotune:
             for lvl in plan.levels:
                 ch = plan.choice(gi, lvl)
@@ -72,9 +75,9 @@ def test_plan_matches_per_group_calls_and_oracle(orc, autotune):
     plan.run()
     torch.cuda.synchronize()
     new = host(groups[0][2])
-    assert_e2e(new[0], orc.match(pp[0].left, pp[0].right, op), "refilled group")
+    assert_explained(orc, new[0], pp[0].left, pp[0].right, params, op, "refilled group",
+                     variants=variants[0])
     plan.close()
-    m.close()
 
 
 def test_plan_scale_to_width():

@@ -11,7 +11,7 @@ import torch
 
 import paper_2106_07136_gb300 as bd
 import synth
-from gpu_helpers import WARM_STREAM, assert_e2e, dev, host
+from gpu_helpers import WARM_STREAM, assert_explained, dev, host
 from paper_2106_07136_gb300 import serve
 
 pytestmark = pytest.mark.gpu
@@ -72,12 +72,11 @@ def test_warm_start_gpu_matches_oracle(orc):
     m = bd.Matcher()
     d0 = host(m.match(dev(f0.left, torch.uint8), dev(f0.right, torch.uint8), params))
     ref0 = orc.match(f0.left, f0.right, op)
-    assert_e2e(d0, ref0, "frame 0")
+    assert_explained(orc, d0, f0.left, f0.right, params, op, "frame 0")
     # both sides warm-start frame 1 from the same previous map (the oracle's)
     out = host(m.match_warm(dev(f1.left, torch.uint8), dev(f1.right, torch.uint8), dev(ref0),
                             params))
-    ref1 = orc.match(f1.left, f1.right, op, prev=ref0)
-    assert_e2e(out, ref1, "frame 1 warm")
+    assert_explained(orc, out, f1.left, f1.right, params, op, "frame 1 warm", prev=ref0)
     wm = host(bd.warm_map(dev(ref0), KW["coarsest_scale"] + 1))[0]
     np.testing.assert_allclose(wm, orc.warm_map(ref0, KW["coarsest_scale"] + 1), atol=1e-4)
     # in place: prev aliases the output
