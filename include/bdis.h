@@ -17,7 +17,9 @@
  *   - Images and maps are row-major. "Dense" means pitch = width elements
  *     and consecutive images of a batch packed back to back.
  *   - Pointers documented as "device" must be CUDA device (or managed)
- *     memory on the handle's device; the caller owns them.
+ *     memory on the handle's device (for bdis_match_static: the current
+ *     device); the caller owns them. Device memory of another GPU is refused
+ *     with BDIS_E_INVALID_ARG before anything is launched.
  *   - Work is enqueued on the given CUDA stream and returns before it
  *     finishes; argument errors return synchronously without enqueuing
  *     anything; a CUDA error is returned by the call that observes it.
@@ -262,6 +264,22 @@ bdis_status bdis_match_host_async(bdis_handle *h, const uint8_t *left, const uin
  * this handle has not issued. */
 bdis_status bdis_host_wait(bdis_handle *h, uint64_t ticket);
 
+/* Bounded form of bdis_host_wait for loops that must not block (serving):
+ * polls the call's completion against a host-side deadline of timeout_ms
+ * (>= 0; 0 = just look) and returns BDIS_E_TIMEOUT when the deadline passes
+ * first. The call stays in flight and its buffers stay the library's until a
+ * later wait returns BDIS_OK. Other errors as at bdis_host_wait. Not in the
+ * paper (its program is one blocking loop). */
+bdis_status bdis_host_wait_timeout(bdis_handle *h, uint64_t ticket, double timeout_ms);
+
+/* Host-side fault injection, for tests of failure handling: the next `count`
+ * device allocations the library makes (a handle's workspace grows, plan
+ * workspaces, network buffers) fail as if the device were out of memory,
+ * without asking the driver. The calls that hit one return BDIS_E_NOMEM and
+ * leave their handle, plan or network usable. count <= 0 clears it.
+ * Process-wide. Nothing on the GPU is touched. */
+void bdis_inject_alloc_failures(int count);
+
 /* ------------------------------------------------------------------ steps
  * The method's steps, one launch sequence each, on dense device batches of
  * `count` planes. bdis_match runs exactly these kernels. */
@@ -320,6 +338,19 @@ bdis_status bdis_densify_level(int width, int height, int count, const bdis_para
  * ceil(H/2^level) x ceil(W/2^level). */
 bdis_status bdis_warm_map(const float *prev, int width, int height, int level, int count,
                           float *out, void *stream);
+
+/* The per-patch choice on the coarsest level when it is searched twice
+ * (bdis_match_seeded with fallback; R16, not in the paper): result a
+ * (searched from the seed) is kept only if it is kept by the patch tests, it
+ * is not within 0.1 px of a kept result b (searched from the plain start;
+ * that close, both found one solution and the plain one stands), and b is
+ * dropped or has no higher posterior; elsewhere b's D* and weight overwrite
+ * a's. All arrays device, `total` patches (bdis_search_level's outputs and
+ * its debug posterior and flags). */
+bdis_status bdis_select_start(float *d_star_a, float *weight_a, const float *posterior_a,
+                              const uint8_t *flags_a, const float *d_star_b,
+                              const float *weight_b, const float *posterior_b,
+                              const uint8_t *flags_b, int64_t total, void *stream);
 
 /* Bring a map of level f to full size: bilinear over finite neighbours,
  * values times 2^f; NaN where no finite neighbour has weight. */
@@ -459,6 +490,21 @@ bdis_status bdis_net_train_step(bdis_net *net, const float *L, const float *R, i
                                 int width, int height, int count, const float *label, float lr,
                                 float *loss_out, void *stream);
 
+/* Whether a forward pass of the network timed out since the last call:
+ * waits for `stream`, then returns BDIS_E_TIMEOUT (and clears the record) if
+ * a tensor-core forward kernel's bounded wait for its own MMAs (about 200 ms)
+ * ran out since the last bdis_net_status; that kernel then wrote NaN for the
+ * tile and returned, so a proposal (and bdis_match_learned's seed) may hold
+ * NaN there, which the seed map treats as missing. BDIS_OK otherwise. The
+ * forward entry points themselves return before the kernels run, so this is
+ * how a caller learns of it. */
+bdis_status bdis_net_status(bdis_net *net, void *stream);
+
+/* Host-side fault injection, for tests of the path above: records a timeout
+ * exactly as the kernel's timeout path does (the network's device fault word
+ * is written from the host); the next bdis_net_status returns BDIS_E_TIMEOUT. */
+bdis_status bdis_net_inject_timeout(bdis_net *net);
+
 /* Copy the FP32 master weights to host memory (waits for the device). */
 bdis_status bdis_net_get_weights(bdis_net *net, float *weights_out);
 void bdis_net_destroy(bdis_net *net);
@@ -470,16 +516,20 @@ void bdis_net_destroy(bdis_net *net);
  * synchronise the device or fail at run time. bdis_match_static runs the
  * same kernels as bdis_match with no handle and no allocation: its scratch
  * memory (pyramid planes, per-patch arrays) is a fixed array of
- * BDIS_STATIC_SCRATCH_BYTES compiled into this library, which every GPU that
- * loads the library holds until the process exits. The paper has no
+ * BDIS_STATIC_SCRATCH_BYTES compiled into this library. The paper has no
  * counterpart; this is a deployment variant of bdis_match.
  *
  *   - Arguments, output and errors as bdis_match, on the CURRENT CUDA device
  *     and the given stream (cudaStream_t, NULL = legacy default stream).
  *   - No cudaMalloc, cudaFree or other allocating call is made.
- *   - The first call on a device looks the array's device address up (once
- *     per device, with that device current). Make that first call before any
- *     stream capture.
+ *   - Each call looks the array's device address up on the current device
+ *     (cudaGetSymbolAddress). Under CUDA's lazy module loading the FIRST call
+ *     on a device is what loads the array onto that device: the driver then
+ *     reserves its 24 MiB, which may synchronise and may fail (returned as
+ *     BDIS_E_NOMEM). So make one call per device at start-up, as a warm-up,
+ *     before any stream capture and before the path that must not allocate.
+ *     From then on the device holds the array until the process exits (or
+ *     until cudaDeviceReset, after which the next call loads it again).
  *   - Work whose scratch need exceeds BDIS_STATIC_SCRATCH_BYTES is refused
  *     with BDIS_E_UNSUPPORTED and a message in bdis_last_error_string(). The
  *     24 MiB hold one 1280x720 pair or three 640x480 pairs at the defaults.

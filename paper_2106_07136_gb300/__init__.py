@@ -17,6 +17,7 @@ from .api import (  # noqa: F401
     densify_level,
     grid,
     image_desc,
+    inject_alloc_failures,
     level_dims,
     match_static,
     pack_right,
@@ -35,6 +36,7 @@ from .api import (  # noqa: F401
     prepare_level0,
     pyramid_level,
     search_level,
+    select_start,
     upsample,
     warm_map,
 )

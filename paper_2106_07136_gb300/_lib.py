@@ -28,7 +28,8 @@ EXPORTED = [
     "bdis_plan_workspace_bytes", "bdis_plan_destroy", "bdis_match_warm", "bdis_warm_map",
     "bdis_net_weight_count", "bdis_net_create", "bdis_net_forward", "bdis_net_gradient",
     "bdis_net_train_step", "bdis_net_get_weights", "bdis_net_destroy", "bdis_match_seeded",
-    "bdis_match_learned",
+    "bdis_match_learned", "bdis_select_start", "bdis_host_wait_timeout",
+    "bdis_inject_alloc_failures", "bdis_net_status", "bdis_net_inject_timeout",
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
@@ -181,6 +182,12 @@ def load():
                                        c_void_p]
     lib.bdis_upsample.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p,
                                   c_void_p]
+    lib.bdis_select_start.argtypes = [c_void_p] * 8 + [ctypes.c_int64, c_void_p]
+    lib.bdis_host_wait_timeout.argtypes = [c_void_p, ctypes.c_uint64, ctypes.c_double]
+    lib.bdis_inject_alloc_failures.argtypes = [c_int]
+    lib.bdis_inject_alloc_failures.restype = None
+    lib.bdis_net_status.argtypes = [c_void_p, c_void_p]
+    lib.bdis_net_inject_timeout.argtypes = [c_void_p]
     lib.bdis_enable_timing.argtypes = [c_void_p, c_int]
     lib.bdis_read_timing.argtypes = [c_void_p, P(BdisTiming)]
     _lib = lib

@@ -246,9 +246,15 @@ class Matcher:
         self._inflight[ticket.value] = (lt, rt, ot)
         return ticket.value, out
 
-    def host_wait(self, ticket: int):
-        """bdis_host_wait: return once call `ticket` (and all before it) is done."""
-        check(self._lib.bdis_host_wait(self._h, ticket), "bdis_host_wait")
+    def host_wait(self, ticket: int, timeout_s: float | None = None):
+        """bdis_host_wait: return once call `ticket` (and all before it) is done.
+        With timeout_s, bdis_host_wait_timeout: raise BdisError (status
+        BDIS_E_TIMEOUT) if it is not done by then; the call stays in flight."""
+        if timeout_s is None:
+            check(self._lib.bdis_host_wait(self._h, ticket), "bdis_host_wait")
+        else:
+            check(self._lib.bdis_host_wait_timeout(self._h, ticket, 1e3 * float(timeout_s)),
+                  "bdis_host_wait_timeout")
         for t in [t for t in self._inflight if t <= ticket]:
             del self._inflight[t]
 
@@ -271,6 +277,12 @@ def match_static(left: torch.Tensor, right: torch.Tensor, params: BdisParams = N
     check(_lib.load().bdis_match_static(ctypes.byref(li), ctypes.byref(ri), ctypes.byref(params),
                                         out.data_ptr(), _stream_ptr(stream)), "bdis_match_static")
     return out.view(b, h, w)[0] if squeeze else out
+
+
+def inject_alloc_failures(count: int):
+    """Host-side fault injection: the library's next `count` device allocations
+    fail as out of memory (bdis_inject_alloc_failures); 0 clears it."""
+    _lib.load().bdis_inject_alloc_failures(int(count))
 
 
 def set_search_variant(columns_per_lane: int):
@@ -500,6 +512,15 @@ class ProposalNet:
                                             _stream_ptr(stream)), "bdis_net_train_step")
         return loss.value
 
+    def status(self, stream=None):
+        """bdis_net_status: raise BdisError (BDIS_E_TIMEOUT) if a forward pass's
+        bounded wait ran out since the last check; waits for the stream."""
+        check(self._lib.bdis_net_status(self._h, _stream_ptr(stream)), "bdis_net_status")
+
+    def inject_timeout(self):
+        """Host-side fault injection: record a forward-pass timeout."""
+        check(self._lib.bdis_net_inject_timeout(self._h), "bdis_net_inject_timeout")
+
     def weights(self) -> np.ndarray:
         w = np.empty(net_weight_count(), dtype=np.float32)
         check(self._lib.bdis_net_get_weights(self._h, w.ctypes.data), "bdis_net_get_weights")
@@ -622,6 +643,21 @@ def densify_level(shape, params: BdisParams, d_star, weight, coarse, is_finest, 
                                          out.data_ptr(), _stream_ptr(stream)),
           "bdis_densify_level")
     return out
+
+
+def select_start(a: dict, b: dict, stream=None):
+    """R16 choice on a level searched twice: search_level results a (from a
+    seed) and b (from the plain start), both with debug outputs. Returns the
+    chosen (d_star, weight) as new tensors; a and b are left unchanged."""
+    d, w = a["d_star"].clone(), a["weight"].clone()
+    pa, fa = a["posterior"].contiguous(), a["flags"].contiguous()
+    db, wb = b["d_star"].contiguous(), b["weight"].contiguous()
+    pb, fb = b["posterior"].contiguous(), b["flags"].contiguous()
+    check(_lib.load().bdis_select_start(d.data_ptr(), w.data_ptr(), pa.data_ptr(), fa.data_ptr(),
+                                        db.data_ptr(), wb.data_ptr(), pb.data_ptr(),
+                                        fb.data_ptr(), d.numel(), _stream_ptr(stream)),
+          "bdis_select_start")
+    return d, w
 
 
 def warm_map(prev: torch.Tensor, level: int, stream=None) -> torch.Tensor:

@@ -12,7 +12,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
+#include <chrono>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "bdis_internal.cuh"
@@ -45,6 +48,9 @@ namespace bdis {
 namespace {
 
 thread_local char g_last_error[256] = "";
+
+// Device allocations still to fail (bdis_inject_alloc_failures).
+std::atomic<int> g_alloc_failures{0};
 
 constexpr size_t kAlign = 256;
 
@@ -135,7 +141,7 @@ bdis_status ensure_workspace(bdis_handle *h, size_t bytes, bool from_async = fal
     h->ws_bytes = 0;
   }
   void *p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
+  cudaError_t e = device_alloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();  // clear the sticky-free allocation error
     snprintf(g_last_error, sizeof g_last_error, "workspace of %zu bytes: %s", bytes,
@@ -171,6 +177,9 @@ bdis_status check_pair(const bdis_image *l, const bdis_image *r) {
   return BDIS_OK;
 }
 
+// Device (or managed) memory that kernels on the CURRENT device may read: a
+// plain device allocation must live on that device (another GPU's memory
+// without peer access would be an illegal address there, not an argument error).
 bdis_status check_device_ptr(const void *p) {
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -180,6 +189,14 @@ bdis_status check_device_ptr(const void *p) {
   }
   if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
     return BDIS_E_INVALID_ARG;
+  if (at.type == cudaMemoryTypeDevice) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      return BDIS_E_INVALID_ARG;
+    }
+    if (at.device != cur) return BDIS_E_INVALID_ARG;
+  }
   return BDIS_OK;
 }
 
@@ -496,6 +513,14 @@ bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t st,
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return record_cuda(e);
+}
+
+cudaError_t device_alloc(void **p, size_t bytes) {
+  int n = g_alloc_failures.load();
+  while (n > 0) {
+    if (g_alloc_failures.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
 }
 
 void set_last_error(const char *msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
@@ -963,6 +988,33 @@ bdis_status bdis_host_wait(bdis_handle *h, uint64_t ticket) {
   return record_cuda(e);
 }
 
+bdis_status bdis_host_wait_timeout(bdis_handle *h, uint64_t ticket, double timeout_ms) {
+  if (!h || ticket == 0 || ticket >= h->async_next || !(timeout_ms >= 0.0))
+    return BDIS_E_INVALID_ARG;
+  bdis_status s = bind_device(h);
+  if (s != BDIS_OK) return s;
+  if (!h->async_pending) return BDIS_OK;
+  // poll the slot's copy-out event (see bdis_host_wait) against a host deadline
+  const auto deadline = std::chrono::steady_clock::now() +
+                        std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                            std::chrono::duration<double, std::milli>(timeout_ms));
+  while (true) {
+    cudaError_t e = cudaEventQuery(h->ev_out[ticket & 1u]);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return record_cuda(e);
+    cudaGetLastError();  // not-ready is not an error
+    if (std::chrono::steady_clock::now() >= deadline) {
+      set_last_error("bdis_host_wait_timeout: the call's result is not ready yet");
+      return BDIS_E_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  if (ticket + 1 == h->async_next) return record_cuda(drain_async(h));
+  return BDIS_OK;
+}
+
+void bdis_inject_alloc_failures(int count) { g_alloc_failures.store(count > 0 ? count : 0); }
+
 static bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
 
 bdis_status bdis_prepare_level0(const bdis_image *left, const bdis_image *right, float *L0,
@@ -1049,6 +1101,18 @@ bdis_status bdis_densify_level(int width, int height, int count, const bdis_para
   a.R2 = reinterpret_cast<const float2 *>(R);
   a.out = out;
   return record_cuda(launch_densify(a, static_cast<cudaStream_t>(stream)));
+}
+
+bdis_status bdis_select_start(float *d_star_a, float *weight_a, const float *posterior_a,
+                              const uint8_t *flags_a, const float *d_star_b,
+                              const float *weight_b, const float *posterior_b,
+                              const uint8_t *flags_b, int64_t total, void *stream) {
+  if (!d_star_a || !weight_a || !posterior_a || !flags_a || !d_star_b || !weight_b ||
+      !posterior_b || !flags_b || total < 0)
+    return BDIS_E_INVALID_ARG;
+  return record_cuda(launch_select_start(d_star_a, weight_a, posterior_a, flags_a, d_star_b,
+                                         weight_b, posterior_b, flags_b, (long long)total,
+                                         static_cast<cudaStream_t>(stream)));
 }
 
 bdis_status bdis_upsample(const float *map, int map_width, int map_height, int level, int width,

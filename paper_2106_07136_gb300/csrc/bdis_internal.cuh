@@ -191,6 +191,11 @@ void set_pyramid_fused(int variant);
 void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params &p);
 void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_params &p);
 
+// Every device allocation of the library goes through here, so that host-side
+// fault injection (bdis_inject_alloc_failures) can make the next ones fail as
+// out of memory without touching the GPU.
+cudaError_t device_alloc(void **p, size_t bytes);
+
 // Record a CUDA error for bdis_last_error_string() and map it to a status.
 bdis_status record_cuda(cudaError_t e);
 void set_last_error(const char *msg);

@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(128) conv_mma_kernel(
 // commits them to an mbarrier; every thread then reads its row of D (warp w
 // owns tensor-memory lanes 32 w .. 32 w + 31) and, if its position is a real
 // pixel, writes the layer output. Waits are bounded by the global timer: on a
-// timeout the block writes NaN, frees its tensor memory and returns.
+// timeout the block writes NaN, sets the network's fault word (read by
+// bdis_net_status), frees its tensor memory and returns.
 
 __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
@@ -256,7 +257,7 @@ template <int CIN, int COUT, int MODE>
 __global__ void __launch_bounds__(128) conv_tc_kernel(
     const __nv_bfloat16 *__restrict__ in, const __nv_bfloat16 *__restrict__ wt,
     const float *__restrict__ bias, int dil, int H, int W, int count,
-    void *__restrict__ out) {
+    void *__restrict__ out, int *__restrict__ fault) {
   static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "tile");
   static_assert(MODE == kFwdRelu || MODE == kFwdLinearF32, "forward only");
   constexpr int KG = 9 * CIN / 8;  // 8-element k-groups of the weights
@@ -343,7 +344,10 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               mbar_a));
     }
-    ok = mbar_wait(mbar_a, parity);
+    // every thread of the block takes the same branch below (the loads are
+    // warp-collective and the loop has block barriers)
+    ok = __syncthreads_and(mbar_wait(mbar_a, parity)) != 0;
+    if (!ok && tid == 0) atomicOr(fault, 1);  // reported by bdis_net_status
     parity ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     float d[COUT];
@@ -611,6 +615,8 @@ struct bdis_net {
   long long cap = 0;
   __nv_bfloat16 *x0 = nullptr, *a[5] = {}, *gbuf[2] = {}, *g6 = nullptr;
   float *z6 = nullptr;
+  // device word set when a forward kernel's bounded wait ran out
+  int *fault = nullptr;
 };
 
 namespace {
@@ -634,7 +640,7 @@ bdis_status net_reserve(bdis_net *n, long long pixels) {
   net_free_acts(n);
   cudaError_t e = cudaSuccess;
   auto alloc = [&](void **p, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = bdis::device_alloc(p, bytes);
   };
   alloc((void **)&n->x0, pixels * 16 * 2);
   for (auto &p : n->a) alloc((void **)&p, pixels * 32 * 2);
@@ -675,7 +681,7 @@ constexpr int kTcSmemMax = 200 * 1024;
 
 template <int CIN, int COUT, int MODE>
 bool conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, int dil,
-             int H, int W, long long total, void *out, cudaStream_t st) {
+             int H, int W, long long total, void *out, int *fault, cudaStream_t st) {
   const int smem = tc_smem_bytes<CIN, COUT>(dil, W);
   if (smem > kTcSmemMax) return false;
   // the shared-memory limit is a per-device attribute of the kernel
@@ -696,13 +702,15 @@ bool conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias
   const long long tiles = (totalp + 127) / 128;
   const int per_sm = std::max(1, std::min(4, (227 * 1024) / (smem + 1024)));
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)per_sm * g_sms);
-  conv_tc_kernel<CIN, COUT, MODE><<<grid, 128, smem, st>>>(in, wt, bias, dil, H, W, count, out);
+  conv_tc_kernel<CIN, COUT, MODE><<<grid, 128, smem, st>>>(in, wt, bias, dil, H, W, count, out,
+                                                             fault);
   return true;
 }
 
 template <int CIN, int COUT, int MODE>
 void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, int dil, int H,
-          int W, long long total, const __nv_bfloat16 *mask, void *out, cudaStream_t st) {
+          int W, long long total, const __nv_bfloat16 *mask, void *out, int *fault,
+          cudaStream_t st) {
   if (!g_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -710,7 +718,8 @@ void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, i
     if (g_sms <= 0) g_sms = 152;
   }
   if constexpr (MODE == kFwdRelu || MODE == kFwdLinearF32) {
-    if (g_net_tc && conv_tc<CIN, COUT, MODE>(in, wt, bias, dil, H, W, total, out, st)) return;
+    if (g_net_tc && conv_tc<CIN, COUT, MODE>(in, wt, bias, dil, H, W, total, out, fault, st))
+      return;
   }
   const long long tiles = (total + 255) / 256;  // 64 pixels x 4 m-tiles per block tile
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)g_sms * 3);
@@ -721,12 +730,13 @@ void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, i
 cudaError_t forward(bdis_net *n, const float *L3, const float *R3, int r_stride, int H, int W,
                     long long total, cudaStream_t st) {
   pack_input_kernel<<<nblocks(total, 256), 256, 0, st>>>(L3, R3, r_stride, total, n->x0);
-  conv<16, 32, kFwdRelu>(n->x0, n->wf[0], n->bias[0], kDil[0], H, W, total, nullptr, n->a[0], st);
+  conv<16, 32, kFwdRelu>(n->x0, n->wf[0], n->bias[0], kDil[0], H, W, total, nullptr, n->a[0],
+                         n->fault, st);
   for (int l = 1; l < 5; ++l)
     conv<32, 32, kFwdRelu>(n->a[l - 1], n->wf[l], n->bias[l], kDil[l], H, W, total, nullptr,
-                           n->a[l], st);
+                           n->a[l], n->fault, st);
   conv<32, 16, kFwdLinearF32>(n->a[4], n->wf[5], n->bias[5], kDil[5], H, W, total, nullptr,
-                              n->z6, st);
+                              n->z6, n->fault, st);
   return cudaGetLastError();
 }
 
@@ -746,14 +756,14 @@ cudaError_t backward(bdis_net *n, int H, int W, long long total, cudaStream_t st
                                                      n->dW[5], n->db[5]);
   // g5 = (W6^T g6) * relu'(a5)
   conv<16, 32, kBwdDataMasked>(n->g6, n->wb[5], nullptr, kDil[5], H, W, total, n->a[4],
-                               n->gbuf[0], st);
+                               n->gbuf[0], n->fault, st);
   int cur = 0;
   for (int l = 4; l >= 1; --l) {
     // gradient of layer l (0-based) output is gbuf[cur]; its input is a[l-1]
     conv_wgrad_kernel<32, 32><<<wblocks, 128, 0, st>>>(n->a[l - 1], n->gbuf[cur], kDil[l], H, W,
                                                        total, n->dW[l], n->db[l]);
     conv<32, 32, kBwdDataMasked>(n->gbuf[cur], n->wb[l], nullptr, kDil[l], H, W, total,
-                                 n->a[l - 1], n->gbuf[cur ^ 1], st);
+                                 n->a[l - 1], n->gbuf[cur ^ 1], n->fault, st);
     cur ^= 1;
   }
   conv_wgrad_kernel<16, 32><<<wblocks, 128, 0, st>>>(n->x0, n->gbuf[cur], kDil[0], H, W, total,
@@ -775,6 +785,7 @@ void net_release(bdis_net *n) {
   cudaFree(n->v);
   cudaFree(n->grad);
   cudaFree(n->loss);
+  cudaFree(n->fault);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(n->wf[l]);
     cudaFree(n->wb[l]);
@@ -821,7 +832,7 @@ bdis_status bdis_net_create(int device, const float *weights, bdis_net **out) {
   if (!n) return BDIS_E_NOMEM;
   n->device = device;
   auto alloc = [&](void **p, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = bdis::device_alloc(p, bytes);
   };
   const size_t wb = sizeof(float) * kMasterCount;
   alloc((void **)&n->w, wb);
@@ -829,6 +840,7 @@ bdis_status bdis_net_create(int device, const float *weights, bdis_net **out) {
   alloc((void **)&n->v, wb);
   alloc((void **)&n->grad, wb);
   alloc((void **)&n->loss, sizeof(float));
+  alloc((void **)&n->fault, sizeof(int));
   for (int l = 0; l < kLayers; ++l) {
     alloc((void **)&n->wf[l], 2 * kCoutP[l] * 9 * kCinP[l]);
     if (l > 0) alloc((void **)&n->wb[l], 2 * kCoutP[l] * 9 * kCinP[l]);
@@ -839,6 +851,7 @@ bdis_status bdis_net_create(int device, const float *weights, bdis_net **out) {
   if (e == cudaSuccess) e = cudaMemcpy(n->w, weights, wb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, wb);
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, wb);
+  if (e == cudaSuccess) e = cudaMemset(n->fault, 0, sizeof(int));
   if (e == cudaSuccess) e = pack_all(n, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -921,6 +934,32 @@ bdis_status bdis_net_get_weights(bdis_net *n, float *weights_out) {
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess)
     e = cudaMemcpy(weights_out, n->w, sizeof(float) * kMasterCount, cudaMemcpyDeviceToHost);
+  return bdis::record_cuda(e);
+}
+
+bdis_status bdis_net_status(bdis_net *n, void *stream) {
+  if (!n) return BDIS_E_INVALID_ARG;
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess && cur != n->device) e = cudaSetDevice(n->device);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  int fault = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&fault, n->fault, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && fault) e = cudaMemset(n->fault, 0, sizeof(int));
+  if (e != cudaSuccess) return bdis::record_cuda(e);
+  if (fault) {
+    bdis::set_last_error("proposal network: a forward pass's bounded wait ran out (its tile "
+                         "was written as NaN)");
+    return BDIS_E_TIMEOUT;
+  }
+  return BDIS_OK;
+}
+
+bdis_status bdis_net_inject_timeout(bdis_net *n) {
+  if (!n) return BDIS_E_INVALID_ARG;
+  const int one = 1;
+  cudaError_t e = cudaSetDevice(n->device);
+  if (e == cudaSuccess) e = cudaMemcpy(n->fault, &one, sizeof(int), cudaMemcpyHostToDevice);
   return bdis::record_cuda(e);
 }
 

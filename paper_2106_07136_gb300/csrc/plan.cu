@@ -103,7 +103,7 @@ bdis_status bdis_plan_create(int device, const bdis_group *groups, int n_groups,
     g.right = groups[i].right;
     g.out = groups[i].disparity_out;
     g.ws_bytes = bdis::match_scratch_bytes(g.left.width, g.left.height, g.left.count, g.params);
-    e = cudaMalloc(&g.ws, g.ws_bytes);
+    e = bdis::device_alloc(&g.ws, g.ws_bytes);
     if (e != cudaSuccess) {
       g.ws = nullptr;
       cudaGetLastError();

@@ -19,6 +19,12 @@ schedules. Design:
   immediately preceding result.
 - Per request the server records arrival, launch and completion times
   (completion = its disparity is back in host memory).
+- Faults stay with the request or stream they belong to: a malformed frame
+  (wrong size or type, unknown stream) is refused at submit with ValueError
+  and recorded in `rejected`; a stream closed while its frames wait or run
+  is dropped (queued frames removed, a running frame's result discarded and
+  recorded in `dropped`), and every other stream carries on. Waits on the
+  device are polled against host deadlines.
 
 The result of a request does not depend on which other requests share its
 batch: each pair's kernels read only that pair's data.
@@ -47,6 +53,7 @@ class Request:
     disparity: np.ndarray | None = None  # (H, W) float32 when done
     batch_size: int = 0
     warm: bool = False
+    dropped: bool = False  # its stream was closed before the result arrived
 
     @property
     def latency(self) -> float:
@@ -82,7 +89,7 @@ class _Worker:
                 prev=torch.empty((max_batch, h, w), dtype=torch.float32, device=device),
                 out=torch.empty((max_batch, h, w), dtype=torch.float32, device=device))
         self.event = torch.cuda.Event()
-        self.batch = None  # (shape, [requests]) in flight
+        self.batch = None  # (shape, [requests], [stream states]) in flight
 
     def close(self):
         self.matcher.close()
@@ -116,6 +123,8 @@ class StereoServer:
         self.waiting = {s: collections.deque() for s in self.shapes}
         self.completed: list[Request] = []
         self.refused: list[int] = []
+        self.rejected: list[tuple] = []   # (stream_id, frame, reason) of malformed frames
+        self.dropped: list[Request] = []  # frames of streams closed before they finished
 
     # --------------------------------------------------------- admission
     def stream_bytes(self, shape) -> int:
@@ -136,11 +145,47 @@ class StereoServer:
         return True
 
     def close_stream(self, stream_id: int):
+        """Drop a stream: its waiting frames are removed; a frame of it already
+        on the GPU finishes there but its result is discarded (`dropped`)."""
         st = self.streams.pop(stream_id)
         self.state_bytes -= self.stream_bytes(st.shape)
+        for r in list(st.frames):
+            r.dropped = True
+            self.dropped.append(r)
+        st.frames.clear()
+        q = self.waiting[st.shape]
+        keep = [r for r in q if r.stream_id != stream_id]
+        for r in q:
+            if r.stream_id == stream_id:
+                r.dropped = True
+                self.dropped.append(r)
+        q.clear()
+        q.extend(keep)
 
     # --------------------------------------------------------- requests
+    def _check_frame(self, req: Request):
+        st = self.streams.get(req.stream_id)
+        if st is None:
+            return "unknown or closed stream"
+        for img in (req.left, req.right):
+            shape = tuple(img.shape) if hasattr(img, "shape") else None
+            dtype = getattr(img, "dtype", None)
+            if shape != st.shape:
+                return f"frame of shape {shape}, stream is {st.shape}"
+            if dtype not in (np.uint8, torch.uint8):
+                return f"frame of type {dtype}, need uint8"
+            if isinstance(img, torch.Tensor) and (img.device.type != "cpu"
+                                                  or not img.is_contiguous()):
+                return "frame tensors must be dense host tensors"
+        return None
+
     def submit(self, req: Request, now: float | None = None):
+        """Queue a frame. A malformed one is refused with ValueError (and
+        recorded in `rejected`); the server and every stream carry on."""
+        why = self._check_frame(req)
+        if why is not None:
+            self.rejected.append((req.stream_id, req.frame, why))
+            raise ValueError(f"malformed frame {req.frame} of stream {req.stream_id}: {why}")
         st = self.streams[req.stream_id]
         req.arrival = time.perf_counter() if now is None else now
         st.frames.append(req)
@@ -173,6 +218,7 @@ class StereoServer:
         for r in batch:
             r.launched = now
             r.batch_size = n
+        states = [self.streams[r.stream_id].state for r in batch]
         with torch.cuda.stream(worker.cuda_stream):
             for i, r in enumerate(batch):
                 src_l = r.left if isinstance(r.left, torch.Tensor) else b["hl"][i]
@@ -187,20 +233,26 @@ class StereoServer:
             worker.matcher.match_warm(b["dl"][:n], b["dr"][:n], b["prev"][:n] if warm else None,
                                       self.params, out=b["out"][:n])
             for i, r in enumerate(batch):
-                self.streams[r.stream_id].state.copy_(b["out"][i], non_blocking=True)
+                states[i].copy_(b["out"][i], non_blocking=True)
             b["ho"][:n].copy_(b["out"][:n], non_blocking=True)
             worker.event.record(worker.cuda_stream)
-        worker.batch = (shape, batch)
+        # the stream states stay referenced until the batch is done (a stream
+        # closed meanwhile must not hand its tensor back while a copy is pending)
+        worker.batch = (shape, batch, states)
 
     def _finish(self, worker: _Worker):
-        shape, batch = worker.batch
+        shape, batch, _ = worker.batch
         now = time.perf_counter()
         ho = worker.buffers[shape]["ho"]
         for i, r in enumerate(batch):
+            r.done = now
+            st = self.streams.get(r.stream_id)
+            if st is None:  # the stream was closed while this frame ran
+                r.dropped = True
+                self.dropped.append(r)
+                continue
             if self.keep_results:
                 r.disparity = ho[i].numpy().copy()
-            r.done = now
-            st = self.streams[r.stream_id]
             st.has_state = True
             st.busy = False
             self._release(st)
@@ -235,10 +287,15 @@ class StereoServer:
             if self.poll() == 0:
                 time.sleep(5e-5)
 
-    def close(self):
+    def close(self, timeout_s: float = 30.0):
+        """Wait (polling, against a host deadline) for the batches on the GPU,
+        then release the workers. TimeoutError if they do not finish."""
+        t_end = time.perf_counter() + timeout_s
         for w in self.workers:
-            if w.batch is not None:
-                w.event.synchronize()
+            while w.batch is not None and not w.event.query():
+                if time.perf_counter() > t_end:
+                    raise TimeoutError("a batch did not finish on the GPU")
+                time.sleep(1e-4)
             w.close()
 
     # --------------------------------------------------------- reporting
