@@ -36,8 +36,31 @@ if ROOT not in sys.path:
 METRIC = "640x480 pairs/s and p99 ms, plain vs learned-init BDIS, at matched oracle error"
 W, H = 640, 480
 L2_FLUSH_BYTES = 256 << 20
-FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070
-ALU_PEAK_TFLOPS = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
+FP32_LANES_PER_SM = 128       # FP32 lanes per SM (Blackwell)
+SM_MAX_MHZ_FALLBACK = 2070    # GB300 maximum SM clock, when nvidia-smi gives none
+HBM_FALLBACK_GBS = 6800.0     # earlier GB300 copy measurement, when no measured peak is present
+
+
+def alu_peak(device, sm_max_mhz):
+    """FP32 peak from the device's own SM count (cudaDevAttrMultiProcessorCount,
+    through torch) and the maximum SM clock nvidia-smi reports."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    mhz = sm_max_mhz or SM_MAX_MHZ_FALLBACK
+    tflops = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    src = (f"derived: {sms} SMs (device attribute) x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+           f"{mhz:.0f} MHz ({'nvidia-smi clocks.max.sm' if sm_max_mhz else 'nominal maximum'})")
+    return tflops, src
+
+
+def hbm_peak():
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else
+    the earlier measurement."""
+    try:
+        v = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        return v, "of measured (MEASURED_PEAKS.json hbm_gbs, a STREAM-style copy)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s, an earlier GB300 copy measurement)"
 
 
 def parse():
@@ -219,6 +242,28 @@ def search_flops_per_pair(bd, ps, params, left, right):
     return ps * ps * 8 * (steps + n * params.window_samples), n, by_level
 
 
+def memory_bytes_per_pair(bd, params, pyramid_variant):
+    """Algorithmic DRAM bytes per pair of each memory-shaped kernel class:
+    level 0 (2 B of 8-bit views read, L, packed R and G written: 16 B per
+    pixel) with, in pyramid variant 2, the first pyramid step written from the
+    same staging (16 B per level-1 pixel); each further pyramid step (L and
+    packed R read: 12 B per input pixel; 16 B written per output pixel);
+    densification (4 B written per pixel, D* and weight read: 8 B per patch)."""
+    dims = [bd.level_dims(W, H, lvl) for lvl in range(params.coarsest_scale + 1)]
+    px = [w * h for w, h in dims]
+    first_step = pyramid_variant == 2 and params.coarsest_scale >= 1
+    prep = 18 * px[0] + (16 * px[1] if first_step else 0)
+    steps = range(1 if first_step else 0, params.coarsest_scale)
+    pyr = sum(12 * px[lvl] + 16 * px[lvl + 1] for lvl in steps)
+    dens = 0
+    for lvl in range(params.finest_scale, params.coarsest_scale + 1):
+        w, h = dims[lvl]
+        nx = bd.grid(w, params.patch_size, params.overlap)[1]
+        ny = bd.grid(h, params.patch_size, params.overlap)[1]
+        dens += 4 * px[lvl] + 8 * nx * ny
+    return {"prepare_level0": prep, "pyramid_level": pyr, "densify": dens}
+
+
 def search_src_sha():
     p = os.path.join(ROOT, "paper_2106_07136_gb300", "csrc", "search.cu")
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
@@ -380,20 +425,34 @@ def main():
     achieved = flops * B * args.steps / (s_ms / 1e3) / 1e12
     traffic = recorded_traffic(ps)
     probe = statistics.median(bd.probe_fp32_tflops() for _ in range(3))
-    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / ALU_PEAK_TFLOPS,
+    alu_tflops, alu_src = alu_peak(device, (clk or {}).get("sm_max_mhz"))
+    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_tflops,
+                "unit": "TFLOP/s", "frac": achieved / alu_tflops,
                 "traffic": None if traffic is None else traffic * B / (s_n / args.steps),
                 "kernel": "search (inverse search + posterior, all scales)",
                 "kernel_ms_per_launch": s_ms / s_n,
                 "algorithmic_flops_per_launch": flops * B / (s_n / args.steps),
                 "mean_updates_per_patch_by_level": steps_by_level,
                 "iterations_max": params.iterations,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                "peak_source": alu_src,
                 "peak_measured": probe,
                 "peak_measured_source": "FP32 FMA probe (bdis_probe_fp32_tflops) on this GPU",
                 "frac_of_measured": achieved / probe}
     kernel_share = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                     for k, v in kt.items() if v[1]}
+    hbm, hbm_src = hbm_peak()
+    by_kernel = {"search": {"bound": "alu", "achieved": achieved, "peak": alu_tflops,
+                            "unit": "TFLOP/s", "frac": achieved / alu_tflops}}
+    for cls, per_pair in memory_bytes_per_pair(bd, params, bd.get_pyramid_variant()).items():
+        c_ms, c_n = kt[cls]
+        if not c_n or not per_pair:
+            continue
+        gbs = per_pair * B * args.steps / (c_ms / 1e3) / 1e9
+        by_kernel[cls] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                          "frac": gbs / hbm, "algorithmic_bytes_per_step": per_pair * B,
+                          "ms_per_step": c_ms / args.steps,
+                          "launches_per_step": c_n / args.steps}
+    by_kernel["peak_sources"] = {"alu": alu_src, "hbm": hbm_src}
 
     acc = {"gpu_vs_ground_truth": synth.error_stats(gpu_maps, Dgt)}
     cpu = None
@@ -431,6 +490,9 @@ def main():
                                "rects, dark ellipses, right-only speculars), plain BDIS, "
                                f"patch {ps}, overlap 0.75, 12 it, scales 4..0, gamma 0.75",
                    "pairs_per_step_per_gpu": B, "unique_pairs_per_gpu": U,
+                   "batch": f"{U} distinct seeded pairs tiled {B // U}x"
+                            + (f" (+{B % U})" if B % U else "")
+                            + " into each step's batch; every pair is matched in full",
                    "patches_per_pair": n_patches,
                    "search_variant": bd.get_search_variant(),
                    "search_tiling": int(bd.get_search_tiling()),
@@ -440,6 +502,7 @@ def main():
         "mpix_per_s": value * W * H / 1e6,
         "roofline": roofline,
         "kernels": kernel_share,
+        "roofline_by_kernel": by_kernel,
         "gpu_launches": launches,
         "clocks": clk,
         "accuracy": acc,

@@ -7,8 +7,6 @@
 // into the library; the kernels are the same. The paper has no counterpart.
 #include <stdio.h>
 
-#include <mutex>
-
 #include "bdis_internal.cuh"
 
 namespace {
@@ -20,21 +18,15 @@ constexpr size_t kScratchBytes = BDIS_STATIC_SCRATCH_BYTES;
 // cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_setup_mu;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_scratch on `device` (which must be current); looked up
-// once per device.
-bdis_status scratch_address(int device, void **out) {
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[device]) {
-    void *ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
-    if (e != cudaSuccess) return bdis::record_cuda(e);
-    g_scratch_addr[device] = ptr;
-  }
-  *out = g_scratch_addr[device];
+// Device address of g_scratch on the current device. Looked up on every call
+// (cheap once the module is loaded), so that a context recreated after
+// cudaDeviceReset never sees a stale address. The first lookup on a device
+// loads the module there (lazy loading), which is when the array is reserved.
+bdis_status scratch_address(void **out) {
+  void *ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e != cudaSuccess) return bdis::record_cuda(e);
+  *out = ptr;
   return BDIS_OK;
 }
 
@@ -55,14 +47,10 @@ extern "C" bdis_status bdis_match_static(const bdis_image *left, const bdis_imag
     bdis::set_last_error(msg);
     return BDIS_E_UNSUPPORTED;
   }
-  int device = -1;
-  cudaError_t e = cudaGetDevice(&device);
-  if (e != cudaSuccess) return bdis::record_cuda(e);
-  if (device < 0 || device >= kMaxDevices) return BDIS_E_UNSUPPORTED;
   s = bdis::check_match_pointers(left, right, disparity_out);
   if (s != BDIS_OK) return s;
   void *scratch = nullptr;
-  s = scratch_address(device, &scratch);
+  s = scratch_address(&scratch);
   if (s != BDIS_OK) return s;
   return bdis::run_match_in(scratch, kScratchBytes, static_cast<cudaStream_t>(stream), *left,
                             *right, *p, disparity_out);
