@@ -243,149 +243,202 @@ struct PatchState {
   int kc;
 };
 
-// One update of Eq. 1 for every patch of the warp. FIRST: the first update,
-// where every patch computes its sums (no votes, no predicated stores).
-template <int PS, int CPL, bool FIRST, bool SH, class Rows>
-__device__ __forceinline__ void search_step(const SearchArgs &a, const Rows &rows,
-                                            PatchState<PS, CPL, SH> &st, const bool (&act)[CPL],
-                                            int xl, const float *Lc, const float *Gc,
-                                            unsigned gbits, float u0) {
+// Sums of a patch's valid column set (bit j of `code`: the lane's column j is
+// valid): centred gradient (kept in st.gc where `need`), Hessian and template
+// term. Every lane of the warp takes part (group reductions); only groups
+// with `need` keep the result.
+template <int PS, int CPL, bool SH>
+__device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, CPL, SH> &st,
+                                           const bool (&act)[CPL], unsigned code, bool need,
+                                           const float *Lc, const float *Gc) {
   constexpr int LANES = (PS + CPL - 1) / CPL;
   constexpr int G = pow2_at_least(LANES);
   const int w = a.w;
+  bool v[CPL];
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) v[j] = (code >> j) & 1u;
+  float hh, ct;
+  int nn;
+  if constexpr (CPL % 2 == 0) {
+    // column pairs as packed f32x2; the lane's own columns are always
+    // readable, and an invalid column's terms are multiplied by 0
+    float2 g2[CPL / 2][PS], m2[CPL / 2], s2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int jp = 0; jp < CPL / 2; ++jp)
+      m2[jp] = make_float2(v[2 * jp] ? 1.f : 0.f, v[2 * jp + 1] ? 1.f : 0.f);
+#pragma unroll
+    for (int jp = 0; jp < CPL / 2; ++jp)
+#pragma unroll
+      for (int r = 0; r < PS; ++r) {
+        float ge[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          ge[e] = act[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
+        g2[jp][r] = make_float2(ge[0], ge[1]);
+        s2 = __ffma2_rn(g2[jp][r], m2[jp], s2);  // adds g where valid, exactly
+      }
+    const float sg = group_sum<G>(s2.x + s2.y);
+    nn = PS * group_sum_int<G>(__popc(code));
+    const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
+    const float2 nmg = make_float2(-mg, -mg);
+    float2 h2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int jp = 0; jp < CPL / 2; ++jp) {
+#pragma unroll
+      for (int r = 0; r < PS; ++r) {
+        const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2[jp]);
+        if (need) {
+          st.gc.at(2 * jp, r) = q.x;
+          st.gc.at(2 * jp + 1, r) = q.y;
+        }
+        float te[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+          te[e] = act[2 * jp + e] ? __ldg(Lc + (size_t)r * w + 2 * jp + e) : 0.f;
+        h2 = __ffma2_rn(q, q, h2);
+        c2 = __ffma2_rn(q, make_float2(te[0], te[1]), c2);
+      }
+    }
+    hh = h2.x + h2.y;
+    ct = c2.x + c2.y;
+  } else {
+    float g[CPL][PS];
+    float sg = 0.f;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j)
+#pragma unroll
+      for (int r = 0; r < PS; ++r) {
+        g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
+        sg += g[j][r];
+      }
+    sg = group_sum<G>(sg);
+    nn = PS * group_sum_int<G>(__popc(code));
+    const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
+    hh = 0.f;
+    ct = 0.f;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j)
+#pragma unroll
+      for (int r = 0; r < PS; ++r) {
+        const float q = v[j] ? g[j][r] - mg : 0.f;
+        if (need) st.gc.at(j, r) = q;
+        hh = fmaf(q, q, hh);
+        ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
+      }
+  }
+  hh = group_sum<G>(hh);
+  ct = group_sum<G>(ct);
+  if (need) {  // implies not frozen (frozen is the same in every lane of a group)
+    st.invH = hh > 0.f ? __fdividef(1.f, hh) : 0.f;  // hh is far below 2^126
+    st.gcT = ct;
+    st.prev = code;
+    if (nn == 0 || hh <= kFlatEps * (float)nn) {  // the Hessian and count change only here
+      st.frozen = true;
+      st.flat = true;
+    }
+  }
+}
+
+// A and B of the lane's columns at integer base kd (sample columns ib + j):
+// no branches inside; an invalid column has gc = 0 and reads a clamped,
+// readable column, so it adds exactly 0.
+template <int PS, int CPL, bool SH, class Rows>
+__device__ __forceinline__ void patch_ab(const Rows &rows, PatchState<PS, CPL, SH> &st, int ib,
+                                         int kd) {
+  constexpr int LANES = (PS + CPL - 1) / CPL;
+  constexpr int G = pow2_at_least(LANES);
+  float sa[2] = {0.f, 0.f}, sb[2] = {0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) {
+    const auto p = rows.col_clamped(ib + j);
+#pragma unroll
+    for (int r = 0; r < PS; ++r) {
+      const float2 q = rows.ld(p, r);
+      const float g = st.gc.at(j, r);
+      sa[r & 1] = fmaf(g, q.x, sa[r & 1]);
+      sb[r & 1] = fmaf(g, q.y, sb[r & 1]);
+    }
+  }
+  st.A = group_sum<G>(sa[0] + sa[1]);
+  st.B = group_sum<G>(sb[0] + sb[1]);
+  st.kc = kd;
+}
+
+// Valid-column code of the lane at sample base ib (x - D = ib + j + t).
+template <int CPL>
+__device__ __forceinline__ unsigned valid_code(const bool (&act)[CPL], int ib, float t, int w) {
+  const int lb = last_base(t, w);
+  unsigned code = 0u;
+#pragma unroll
+  for (int j = 0; j < CPL; ++j) code |= (unsigned)(act[j] && ib + j >= 0 && ib + j <= lb) << j;
+  return code;
+}
+
+// The patch's D* update (Eq. 1) from the step sum; a stopped patch keeps its
+// state. Stops on a non-finite D, on leaving the search range (dropped
+// later) or on convergence (update below kStepTol).
+template <int PS, int CPL, bool SH>
+__device__ __forceinline__ void patch_update(PatchState<PS, CPL, SH> &st, float Ssum, float u0) {
+  const float step = (Ssum - st.gcT) * st.invH;
+  const bool live = !st.frozen;
+  const float D = st.D + step;
+  st.D = live ? D : st.D;
+  st.last_step = live ? step : st.last_step;
+  st.steps += live ? 1 : 0;
+  st.frozen = !live || !isfinite(D) || fabsf(D - u0) > (float)PS || fabsf(step) < kStepTol;
+}
+
+// The first update of Eq. 1 for every patch of the warp: every patch computes
+// its sums (no votes, no predicated stores).
+template <int PS, int CPL, bool SH, class Rows>
+__device__ __forceinline__ void search_first_step(const SearchArgs &a, const Rows &rows,
+                                                  PatchState<PS, CPL, SH> &st,
+                                                  const bool (&act)[CPL], int xl, const float *Lc,
+                                                  const float *Gc, float u0) {
   int kd;
   float t;
   split_disp(st.D, kd, t);
   const int ib = xl + kd;
-  const int lb = last_base(t, w);
-  bool v[CPL];
-  unsigned code = 0u;
-#pragma unroll
-  for (int j = 0; j < CPL; ++j) {
-    v[j] = act[j] && ib + j >= 0 && ib + j <= lb;
-    code |= (unsigned)v[j] << j;
+  patch_sums<PS, CPL, SH>(a, st, act, valid_code<CPL>(act, ib, t, a.w), true, Lc, Gc);
+  rows.ready();  // staged rows (if any) arrive while the sums above load
+  patch_ab<PS, CPL, SH>(rows, st, ib, kd);
+  if (!st.frozen) patch_update<PS, CPL, SH>(st, fmaf(t, st.B, st.A), u0);
+}
+
+// A later update for every patch of the warp. Returns false, taking no step,
+// when every patch of the warp has already stopped. One warp reduction
+// decides what the warp recomputes:
+//   - a patch whose valid column set changed (group-wise) takes new sums;
+//   - A and B are re-read when some patch needs new sums or moved to another
+//     integer base. A patch whose base and gradient did not change gets the
+//     same sums again, so its result does not depend on its neighbours.
+// The valid set can only change near the image border: while every column of
+// the patch samples inside [0, w - 2] (kd in [-x0, w - 1 - PS - x0]) it is the
+// full set, with no per-column tests.
+template <int PS, int CPL, bool SH, class Rows>
+__device__ __forceinline__ bool search_next_step(const SearchArgs &a, const Rows &rows,
+                                                 PatchState<PS, CPL, SH> &st,
+                                                 const bool (&act)[CPL], int xl, int x0,
+                                                 unsigned full, const float *Lc,
+                                                 const float *Gc, unsigned gbits, float u0) {
+  int kd;
+  float t;
+  split_disp(st.D, kd, t);
+  const int ib = xl + kd;
+  unsigned code = full;
+  if ((unsigned)(kd + x0) > (unsigned)(a.w - 1 - PS)) code = valid_code<CPL>(act, ib, t, a.w);
+  const bool chg = !st.frozen && code != st.prev;
+  const bool mv = !st.frozen && kd != st.kc;
+  const unsigned r = __reduce_or_sync(kFull, (chg ? 1u : 0u) | (mv ? 2u : 0u) |
+                                                 (st.frozen ? 0u : 4u));
+  if (!(r & 4u)) return false;  // every patch of the warp has stopped
+  if (r & 1u) {
+    const bool need = (__ballot_sync(kFull, chg) & gbits) != 0u;
+    patch_sums<PS, CPL, SH>(a, st, act, code, need, Lc, Gc);
   }
-  // the first step computes every patch's sums; later ones only where the
-  // valid run changed (the whole group recomputes)
-  unsigned need_bits = kFull;
-  if constexpr (!FIRST) need_bits = __ballot_sync(kFull, !st.frozen && code != st.prev);
-  const bool need = FIRST || (need_bits & gbits) != 0u;
-  if (FIRST || need_bits != 0u) {
-    // sums of the new valid set: centred gradient, Hessian, template term
-    float hh, ct;
-    int nn;
-    if constexpr (CPL % 2 == 0) {
-      // column pairs as packed f32x2; the lane's own columns are always
-      // readable, and an invalid column's terms are multiplied by 0
-      float2 g2[CPL / 2][PS], m2[CPL / 2], s2 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int jp = 0; jp < CPL / 2; ++jp)
-        m2[jp] = make_float2(v[2 * jp] ? 1.f : 0.f, v[2 * jp + 1] ? 1.f : 0.f);
-#pragma unroll
-      for (int jp = 0; jp < CPL / 2; ++jp)
-#pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          float ge[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e)
-            ge[e] = act[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
-          g2[jp][r] = make_float2(ge[0], ge[1]);
-          s2 = __ffma2_rn(g2[jp][r], m2[jp], s2);  // adds g where valid, exactly
-        }
-      const float sg = group_sum<G>(s2.x + s2.y);
-      nn = PS * group_sum_int<G>(__popc(code));
-      const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
-      const float2 nmg = make_float2(-mg, -mg);
-      float2 h2 = make_float2(0.f, 0.f), c2 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int jp = 0; jp < CPL / 2; ++jp) {
-#pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          const float2 q = __fmul2_rn(__fadd2_rn(g2[jp][r], nmg), m2[jp]);
-          if (need) {
-            st.gc.at(2 * jp, r) = q.x;
-            st.gc.at(2 * jp + 1, r) = q.y;
-          }
-          float te[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e)
-            te[e] = act[2 * jp + e] ? __ldg(Lc + (size_t)r * w + 2 * jp + e) : 0.f;
-          h2 = __ffma2_rn(q, q, h2);
-          c2 = __ffma2_rn(q, make_float2(te[0], te[1]), c2);
-        }
-      }
-      hh = h2.x + h2.y;
-      ct = c2.x + c2.y;
-    } else {
-      float g[CPL][PS];
-      float sg = 0.f;
-#pragma unroll
-      for (int j = 0; j < CPL; ++j)
-#pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
-          sg += g[j][r];
-        }
-      sg = group_sum<G>(sg);
-      nn = PS * group_sum_int<G>(__popc(code));
-      const float mg = (a.normalize && nn > 0) ? __fdividef(sg, (float)nn) : 0.f;
-      hh = 0.f;
-      ct = 0.f;
-#pragma unroll
-      for (int j = 0; j < CPL; ++j)
-#pragma unroll
-        for (int r = 0; r < PS; ++r) {
-          const float q = v[j] ? g[j][r] - mg : 0.f;
-          if (need) st.gc.at(j, r) = q;
-          hh = fmaf(q, q, hh);
-          ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
-        }
-    }
-    hh = group_sum<G>(hh);
-    ct = group_sum<G>(ct);
-    if (need) {  // implies not frozen (frozen is the same in every lane of a group)
-      st.invH = hh > 0.f ? __fdividef(1.f, hh) : 0.f;  // hh is far below 2^126
-      st.gcT = ct;
-      st.prev = code;
-      if (nn == 0 || hh <= kFlatEps * (float)nn) {  // the Hessian and count change only here
-        st.frozen = true;
-        st.flat = true;
-      }
-    }
-  }
-  if constexpr (FIRST) rows.ready();  // staged rows (if any) arrive while the sums above load
-  // A and B change only with the base or the centred gradient. When some
-  // patch of the warp needs them anew the whole warp recomputes (a patch
-  // whose base and gradient did not change gets the same sums again, so the
-  // result does not depend on its neighbours). No branches inside: an
-  // invalid column has gc = 0 and reads a clamped (readable) column, so it
-  // adds exactly 0; a frozen patch's sums are not used.
-  if (FIRST || __any_sync(kFull, !st.frozen && (need || kd != st.kc))) {
-    float sa[2] = {0.f, 0.f}, sb[2] = {0.f, 0.f};
-#pragma unroll
-    for (int j = 0; j < CPL; ++j) {
-      const auto p = rows.col_clamped(ib + j);
-#pragma unroll
-      for (int r = 0; r < PS; ++r) {
-        const float2 q = rows.ld(p, r);
-        const float g = st.gc.at(j, r);
-        sa[r & 1] = fmaf(g, q.x, sa[r & 1]);
-        sb[r & 1] = fmaf(g, q.y, sb[r & 1]);
-      }
-    }
-    st.A = group_sum<G>(sa[0] + sa[1]);
-    st.B = group_sum<G>(sb[0] + sb[1]);
-    st.kc = kd;
-  }
-  const float Ssum = fmaf(t, st.B, st.A);
-  if (!st.frozen) {
-    st.last_step = (Ssum - st.gcT) * st.invH;
-    st.D += st.last_step;
-    ++st.steps;
-    // non-finite, or left the search range (dropped below), or converged
-    if (!isfinite(st.D) || fabsf(st.D - u0) > (float)PS || fabsf(st.last_step) < kStepTol)
-      st.frozen = true;
-  }
+  if (r & 3u) patch_ab<PS, CPL, SH>(rows, st, ib, kd);
+  patch_update<PS, CPL, SH>(st, fmaf(t, st.B, st.A), u0);
+  return true;
 }
 
 // The window's row pass for column pairs (packed f32x2). Each of the CPL + 2
@@ -465,11 +518,13 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
   st.frozen = st.flat = false;
   st.steps = 0;
   if (a.iters > 0) {
-    search_step<PS, CPL, true, SH>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
-    for (int it = 1; it < a.iters; ++it) {
-      if (__all_sync(kFull, st.frozen)) break;  // every patch of the warp has stopped
-      search_step<PS, CPL, false, SH>(a, rows, st, act, xl, Lc, Gc, gbits, u0);
-    }
+    unsigned full = 0u;  // the lane's columns that are part of the patch
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) full |= (unsigned)act[j] << j;
+    search_first_step<PS, CPL, SH>(a, rows, st, act, xl, Lc, Gc, u0);
+    for (int it = 1; it < a.iters; ++it)
+      if (!search_next_step<PS, CPL, SH>(a, rows, st, act, xl, x0, full, Lc, Gc, gbits, u0))
+        break;  // every patch of the warp has stopped
   }
   const float D = st.D, last_step = st.last_step;
   const bool flat = st.flat;
