@@ -650,6 +650,8 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     torch.cuda.synchronize()
     import synth
     U = Lh.shape[0]
+    res["variants"]["batched_640x480"] = measure_batched_same_pairs(args, bd, m, params, left,
+                                                                    right, device, stream)
     res["variants"]["mixed_batch_graph"] = measure_mixed_batch(args, bd, device, stream)
     res["variants"]["mixed_batch_graph_scaled"] = measure_mixed_batch(args, bd, device, stream,
                                                                       scale_to_width=True)
@@ -737,11 +739,16 @@ def measure_learned(args, bd, m, left, right, Lh, Rh, Dgt, device, stream,
                                      "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}}
 
 
-def measure_serving(args, bd, device, seconds=3.0, rate=2000.0, videos=4, frames=4):
+def measure_serving(args, bd, device, seconds=3.0, rate=2000.0, videos=4, frames=4,
+                    curve_rates=(2000.0, 5000.0, 10000.0, 20000.0, 40000.0),
+                    curve_seconds=1.5):
     """64 synthetic stereo video streams (32 at 1280x1024, 32 at 640x480) with
     Poisson arrivals at `rate` pairs/s, served with continuous batching and
     per-stream warm starts; p50/p99 latency from arrival to the disparity
-    being back in host memory."""
+    being back in host memory. `curve`: the same server under a sweep of
+    offered rates up to saturation (a stream has one frame in flight, so
+    beyond the server's capacity the queues grow), with the served rate, the
+    latencies and the mean batch at each."""
     import torch
     import synth
     from paper_2106_07136_gb300 import serve
@@ -759,23 +766,89 @@ def measure_serving(args, bd, device, seconds=3.0, rate=2000.0, videos=4, frames
     server = serve.StereoServer(shapes, params, device=device, max_batch=16, inflight=3,
                                 keep_results=False)
     admitted = [server.admit(sid, shapes[sid % 2]) for sid in range(n_streams)]
-    n = int(rate * seconds)
-    rng = np.random.Generator(np.random.PCG64(2026))
-    order = [int(x) for x in rng.integers(0, n_streams, size=n)]
-    arrivals = serve.poisson_arrivals(rate, n, seed=2027)
     # warm-up: one frame per stream, untimed
     serve.simulate(server, frames_by_stream, np.zeros(n_streams), list(range(n_streams)))
-    server.completed.clear()
-    reqs, wall = serve.simulate(server, frames_by_stream, arrivals, order)
-    server.close()
+
+    def run(r, secs, seed):
+        n = int(r * secs)
+        rng = np.random.Generator(np.random.PCG64(seed))
+        order = [int(x) for x in rng.integers(0, n_streams, size=n)]
+        arrivals = serve.poisson_arrivals(r, n, seed=seed + 1)
+        server.completed.clear()
+        reqs, wall = serve.simulate(server, frames_by_stream, arrivals, order)
+        return reqs, wall
+
+    reqs, wall = run(rate, seconds, 2026)
     stats = serve.StereoServer.latency_stats(reqs)
     mpix = sum(shapes[r.stream_id % 2][0] * shapes[r.stream_id % 2][1] for r in reqs) / 1e6
+    curve = []
+    for i, r in enumerate(curve_rates):
+        rq, wl = run(r, curve_seconds, 3000 + 2 * i)
+        st = serve.StereoServer.latency_stats(rq)
+        curve.append({"offered_pairs_per_s": r, "served_pairs_per_s": len(rq) / wl,
+                      "mpix_per_s": sum(shapes[q.stream_id % 2][0] * shapes[q.stream_id % 2][1]
+                                        for q in rq) / 1e6 / wl,
+                      "p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"),
+                      "mean_batch": st.get("mean_batch"), "requests": len(rq)})
+    server.close()
     return {"offered_pairs_per_s": rate, "value": len(reqs) / wall, "unit": "pairs/s",
             "mpix_per_s": mpix / wall, "streams": n_streams, "admitted": int(sum(admitted)),
-            "latency": stats, "requests": len(reqs), "seconds": wall,
+            "latency": stats, "requests": len(reqs), "seconds": wall, "curve": curve,
             "workload": "32 streams 1280x1024 + 32 streams 640x480, drifting disparity, "
                         "Poisson arrivals, continuous batching (max batch 16, 3 in flight), "
-                        "warm start from the previous frame"}
+                        "warm start from the previous frame; curve: offered rates swept to "
+                        f"saturation, {curve_seconds} s each"}
+
+
+def measure_batched_same_pairs(args, bd, m, params, left, right, device, stream,
+                               splits=(1, 2, 4, 8)):
+    """The batched form (one autotuned CUDA-graph plan) against plain
+    bdis_match on the same 640x480 pairs: the step's batch as 1, 2, 4 or 8
+    equal groups, each a branch of the graph (groups overlap on the GPU).
+    Both sides run back to back on warm L2, timed with CUDA events."""
+    import torch
+    B = left.shape[0]
+    k = max(3, args.steps // 3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = torch.empty((B, H, W), dtype=torch.float32, device=device)
+
+    def rate(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(k):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return B * k / (ev0.elapsed_time(ev1) / 1e3)
+
+    plain = rate(lambda: m.match(left, right, params, out=out))
+    ref = out.clone()
+    rows = []
+    for g in splits:
+        if B % g:
+            continue
+        n = B // g
+        outs = torch.empty((B, H, W), dtype=torch.float32, device=device)
+        groups = [(left[i * n:(i + 1) * n], right[i * n:(i + 1) * n], outs[i * n:(i + 1) * n])
+                  for i in range(g)]
+        t0 = time.perf_counter()
+        plan = bd.Plan(groups, params, autotune=True, device=device, stream=stream)
+        build_s = time.perf_counter() - t0
+        r = rate(lambda: plan.run(stream))
+        same = bool(torch.equal(torch.isnan(outs), torch.isnan(ref)) and
+                    torch.equal(torch.nan_to_num(outs), torch.nan_to_num(ref)))
+        rows.append({"groups": g, "pairs_per_group": n, "pairs_per_s": r, "vs_plain": r / plain,
+                     "equals_plain_bitwise": same, "plan_build_s": build_s,
+                     "level0_choice": plan.choice(0, 0)})
+        plan.close()
+    best = max(rows, key=lambda x: x["pairs_per_s"]) if rows else None
+    return {"plain_pairs_per_s": plain, "plans": rows,
+            "best_vs_plain": best["vs_plain"] if best else None,
+            "best_groups": best["groups"] if best else None,
+            "l2": "not flushed (back-to-back launches, both sides)",
+            "workload": f"{B} pairs of 640x480 per step, the bench's pairs"}
 
 
 MIXED_GROUPS = [(64, 240, 320), (96, 480, 640), (64, 720, 1280), (32, 1080, 1920)]

@@ -410,10 +410,11 @@ bdis_status bdis_probe_fp32_tflops(int iterations, double *tflops, void *stream)
  * workspace (so groups run concurrently); the whole sequence is captured once
  * into a CUDA graph with one branch per group, and bdis_plan_run is a single
  * graph launch on `stream`. With BDIS_PLAN_AUTOTUNE, creation first runs each
- * group once and times, per level, the candidate search lane layouts (1 or 2
- * columns per lane) and block sizes (64, 128) and the densify tile heights
- * (8, 16, 32) on that data, keeping the fastest; results are the same up to
- * float rounding whatever is chosen. bdis_plan_create synchronises `stream`
+ * group once and times, per level, the candidate search lane layouts (1, the
+ * wide layout, and 4 columns per lane at patch size 8), block sizes (64, 128)
+ * and sampling (global or warp-tiled), and the densify kernels (strip, tiles
+ * of 8, 16, 32 rows) on that data, keeping the fastest; results are the same
+ * up to float rounding whatever is chosen. bdis_plan_create synchronises `stream`
  * (autotuning reads the inputs) and may take a second; run is asynchronous. */
 #define BDIS_PLAN_AUTOTUNE 1
 /* Per group, raise the coarsest scale to the smallest c >= p->coarsest_scale
@@ -436,6 +437,7 @@ typedef struct {
                                     size), else tiles of 32; 8/16/32 = tiles */
     size_t workspace_bytes;      /* of the whole group */
     int coarsest_scale;          /* of the group (BDIS_PLAN_SCALE_TO_WIDTH may raise it) */
+    int search_tiling;           /* 0 = global-memory sampling, 1 = warp-tiled */
 } bdis_plan_choice;
 
 typedef struct bdis_plan bdis_plan;

@@ -72,7 +72,7 @@ class BdisGroup(ctypes.Structure):
 class BdisPlanChoice(ctypes.Structure):
     _fields_ = [("search_columns_per_lane", c_int), ("search_block_threads", c_int),
                 ("densify_tile_height", c_int), ("workspace_bytes", c_size_t),
-                ("coarsest_scale", c_int)]
+                ("coarsest_scale", c_int), ("search_tiling", c_int)]
 
 
 class BdisTiming(ctypes.Structure):

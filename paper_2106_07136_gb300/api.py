@@ -387,7 +387,8 @@ class Plan:
                 "search_block_threads": c.search_block_threads,
                 "densify_tile_height": c.densify_tile_height,
                 "workspace_bytes": int(c.workspace_bytes),
-                "coarsest_scale": c.coarsest_scale}
+                "coarsest_scale": c.coarsest_scale,
+                "search_tiling": c.search_tiling}
 
     @property
     def workspace_bytes(self) -> int:

@@ -480,21 +480,29 @@ bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t st,
   const bool fixed = p.window_samples == 5 && p.window_step == 0.5f &&
                      (p.patch_size == 8 || p.patch_size == 12 || p.patch_size == 16);
   const int reps = 3;
+  // lane layouts of the fixed-size kernels: 1 and the wide one (2, or 3 at
+  // patch 12), and 4 columns per lane at patch 8
+  const int cpls[3] = {1, 2, 4};
+  const int n_cpl = !fixed ? 1 : (p.patch_size == 8 ? 3 : 2);
   for (int l = p.coarsest_scale; l >= p.finest_scale && e == cudaSuccess; --l) {
-    // search: lane layout x block size
+    // search: lane layout x block size x global or warp-tiled sampling
     float best = 1e30f;
-    for (int cpl = 1; cpl <= (fixed ? 2 : 1) && e == cudaSuccess; ++cpl)
-      for (int bt = 64; bt <= 128 && e == cudaSuccess; bt *= 2) {
-        SearchArgs sa = level_search_args(base, lay, p, left.count, l);
-        sa.cols_per_lane = cpl;
-        sa.block_threads = bt;
-        const float ms = time_launches(st, e0, e1, reps, [&] { return launch_search(sa, st); }, &e);
-        if (e == cudaSuccess && ms < best) {
-          best = ms;
-          tune->level[l].search_cpl = cpl;
-          tune->level[l].search_threads = bt;
+    for (int ci = 0; ci < n_cpl && e == cudaSuccess; ++ci)
+      for (int bt = 64; bt <= 128 && e == cudaSuccess; bt *= 2)
+        for (int tiled = 0; tiled <= (fixed ? 1 : 0) && e == cudaSuccess; ++tiled) {
+          SearchArgs sa = level_search_args(base, lay, p, left.count, l);
+          sa.cols_per_lane = cpls[ci];
+          sa.block_threads = bt;
+          sa.tiled = tiled;
+          const float ms =
+              time_launches(st, e0, e1, reps, [&] { return launch_search(sa, st); }, &e);
+          if (e == cudaSuccess && ms < best) {
+            best = ms;
+            tune->level[l].search_cpl = cpls[ci];
+            tune->level[l].search_threads = bt;
+            tune->level[l].search_tiled = tiled + 1;
+          }
         }
-      }
     // densify (the separable BDIS kernels): 0 = the strip kernel where it
     // applies, else a tile height of 8, 16 or 32
     if (p.fusion == BDIS_FUSION_BDIS) {

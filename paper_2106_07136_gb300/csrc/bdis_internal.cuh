@@ -72,8 +72,9 @@ inline int gamma_min_count(float gamma, int ps) {
 // Per-level launch choices (0 = the library default). The autotuner of
 // bdis_plan_create fills them by timing the candidates on the real data.
 struct LevelTuning {
-  int search_cpl = 0;      // fast search path: 1 column per lane, or 2 (wide)
+  int search_cpl = 0;      // fast search path: 1, 2 or 4 columns per lane
   int search_threads = 0;  // search block size: 64 or 128
+  int search_tiled = 0;    // search sampling: 1 = global memory, 2 = warp-tiled
   int densify_tile_y = 0;  // densify: 0 = strip kernel (or tiles of 32); 8, 16, 32 = tile height
 };
 struct Tuning {
@@ -219,6 +220,7 @@ bdis_status autotune_match(void *scratch, size_t scratch_bytes, cudaStream_t str
 inline void apply_tuning(SearchArgs &a, const LevelTuning &t) {
   if (t.search_cpl) a.cols_per_lane = t.search_cpl;
   if (t.search_threads) a.block_threads = t.search_threads;
+  if (t.search_tiled) a.tiled = t.search_tiled - 1;
 }
 inline void apply_tuning(DensifyArgs &a, const LevelTuning &t) {
   if (t.densify_tile_y) a.tile_y = t.densify_tile_y;

@@ -6,9 +6,9 @@
 // concurrently; the whole launch sequence (19 launches per group at 5
 // scales) is captured once into a CUDA graph whose groups are independent
 // branches, and each run is a single graph launch. Before capture the
-// autotuner times, per group and level, the candidate lane layouts and block
-// sizes of the search kernel and the tile heights of the densify kernel on
-// the group's own data, and keeps the fastest.
+// autotuner times, per group and level, the candidate lane layouts, block
+// sizes and sampling (global or warp-tiled) of the search kernel and the
+// densify kernels on the group's own data, and keeps the fastest.
 #include <new>
 #include <vector>
 
@@ -182,6 +182,7 @@ bdis_status bdis_plan_info(const bdis_plan *pl, int group, int level, bdis_plan_
   const auto &t = pl->groups[group].tune.level[level];
   out->search_columns_per_lane = t.search_cpl;
   out->search_block_threads = t.search_threads;
+  out->search_tiling = t.search_tiled ? t.search_tiled - 1 : bdis::search_tiled();
   out->densify_tile_height = t.densify_tile_y;
   out->workspace_bytes = pl->groups[group].ws_bytes;
   out->coarsest_scale = pl->groups[group].params.coarsest_scale;

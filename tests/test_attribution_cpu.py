@@ -159,3 +159,24 @@ def test_covered_by_matches_brute_force(orc):
                 if mask[j, i]:
                     want[y0:y0 + ps, x0:x0 + ps] = True
         assert np.array_equal(got, want)
+
+
+def test_posterior_slope_matches_the_closed_form(orc):
+    """On the exactly quadratic energies of a linear texture, E_i = C (d_i +
+    e)^2 around a patch whose D* is off by e, the first-order slope of the
+    posterior equals the derivative of its closed form."""
+    op = orc.OracleParams.make()
+    kappa = 2 * op.sigma_r ** 2 * op.window_samples ** 2
+    offs = np.array([-1.0, -0.5, 0.0, 0.5, 1.0])
+
+    def post(C, e):
+        E = C * (offs + e) ** 2
+        z = np.exp(-(E - E.min()) / kappa)
+        return z[2] / z.sum()
+
+    for C, e in [(50.0, 0.2), (400.0, -0.1), (2000.0, 0.05)]:
+        o = {"energies": (C * (offs + e) ** 2)[None, None, :]}
+        got = at.posterior_slope(o, op)[0, 0]
+        h = 1e-6
+        want = abs(post(C, e + h) - post(C, e - h)) / (2 * h)
+        assert abs(got - want) <= 1e-6 + 1e-6 * want, (C, e, got, want)

@@ -57,7 +57,8 @@ def test_plan_matches_per_group_calls_and_oracle(orc, autotune):
         if autotune:
             for lvl in plan.levels:
                 ch = plan.choice(gi, lvl)
-                assert ch["search_columns_per_lane"] in (1, 2)
+                assert ch["search_columns_per_lane"] in (1, 2, 4)
+                assert ch["search_tiling"] in (0, 1)
                 assert ch["search_block_threads"] in (64, 128)
                 assert ch["densify_tile_height"] in (0, 8, 16, 32)  # 0: strip kernel
                 assert ch["coarsest_scale"] == KW["coarsest_scale"]
@@ -102,4 +103,33 @@ def test_plan_scale_to_width():
         got = host(out)
         assert np.array_equal(np.isnan(got), np.isnan(ref))
         assert np.array_equal(got[~np.isnan(got)], ref[~np.isnan(ref)])
+    plan.close()
+
+
+def test_plan_on_the_mixed_size_batch_sizes(orc):
+    """One autotuned plan over one pair of each size of the mixed-size batch
+    (320x240, 640x480, 1280x720, 1920x1080; disparity range a tenth of the
+    width, 5 scales): each group is exactly the step entry points' result
+    with the lane layouts the autotuner chose, and against the oracle every
+    difference is explained (tests/attribution.py)."""
+    kw = dict(patch_size=8, overlap=0.75, iterations=12, coarsest_scale=4, finest_scale=0,
+              gamma=0.75)
+    params = bd.default_params(**kw)
+    op = orc.OracleParams.make(**kw)
+    sizes = [(240, 320), (480, 640), (720, 1280), (1080, 1920)]
+    pairs = [synth.make_cfg2(seed=synth.stereo.pair_seed(3, 400 + i), h=h, w=w)
+             for i, (h, w) in enumerate(sizes)]
+    groups = [(dev(p.left, torch.uint8).unsqueeze(0), dev(p.right, torch.uint8).unsqueeze(0),
+               torch.empty((1, h, w), dtype=torch.float32, device="cuda"))
+              for p, (h, w) in zip(pairs, sizes)]
+    plan = bd.Plan(groups, params, autotune=True)
+    plan.run()
+    torch.cuda.synchronize()
+    for gi, (p, g) in enumerate(zip(pairs, groups)):
+        var = {lvl: plan.choice(gi, lvl)["search_columns_per_lane"] for lvl in plan.levels}
+        got = host(g[2])[0]
+        _, g_out = gpu_stages(p.left, p.right, params, variants=var)
+        assert same_map(got, g_out), gi
+        assert_explained(orc, got, p.left, p.right, params, op, f"{sizes[gi]}", variants=var,
+                         budget=False)
     plan.close()

@@ -63,6 +63,42 @@ def test_served_results_equal_alone_results():
     m.close()
 
 
+def test_results_equal_alone_under_heavy_batching():
+    """At a load where requests pile up (32 streams, arrivals at 200k/s, up to
+    16 per launch), launches carry several requests each (mean batch above 4)
+    and every result is still exactly what its frame gives alone with the
+    same warm start."""
+    params = bd.default_params(**KW)
+    shape = SHAPES[0]
+    frames = {}
+    for sid in range(32):
+        v = synth.VideoStream(seed=synth.stereo.pair_seed(9, sid), h=shape[0], w=shape[1])
+        frames[sid] = [(f.left, f.right) for f in (v.next() for _ in range(3))]
+    server = serve.StereoServer([shape], params, max_batch=16, inflight=2)
+    for sid in frames:
+        assert server.admit(sid, shape)
+    order = [sid for _ in range(3) for sid in frames]
+    arrivals = serve.poisson_arrivals(200000.0, len(order), seed=11)
+    reqs, _ = serve.simulate(server, frames, arrivals, order)
+    server.close()
+    stats = serve.StereoServer.latency_stats(reqs)
+    assert len(reqs) == 96 and stats["mean_batch"] > 4, stats
+    m = bd.Matcher()
+    by_stream = {}
+    for r in reqs:
+        by_stream.setdefault(r.stream_id, []).append(r)
+    for sid, rs in by_stream.items():
+        prev = None
+        for r in sorted(rs, key=lambda r: r.frame):
+            alone = host(m.match_warm(dev(r.left, torch.uint8), dev(r.right, torch.uint8),
+                                      None if prev is None else dev(prev), params))
+            a = r.disparity
+            assert np.array_equal(np.isnan(a), np.isnan(alone))
+            assert np.array_equal(a[~np.isnan(a)], alone[~np.isnan(alone)]), (sid, r.frame)
+            prev = r.disparity
+    m.close()
+
+
 def test_warm_start_gpu_matches_oracle(orc):
     """bdis_match_warm against the oracle's warm start on consecutive frames."""
     params = bd.default_params(**KW)
