@@ -461,13 +461,17 @@ void bdis_plan_destroy(bdis_plan *plan);
  * (bdis_net_weight_count() floats in all), then b[co]. */
 int bdis_net_weight_count(void);
 
-/* Tuning: the kernels of the network's forward convolutions. 1 (default) =
- * 5th-generation tensor cores (tcgen05: a zero-padded slab of input pixels
- * and the weights in shared memory, each tap's operand a shifted window of
- * the slab, accumulator in tensor memory, 128-pixel tiles); 0 = implicit
- * GEMM on mma.sync (warp-level BF16 MMA). Results agree up to FP32
- * accumulation order. Inputs too wide for one slab, and the training
- * kernels, use mma.sync. Process-wide. */
+/* Tuning: the kernels of the network's forward convolutions, all implicit
+ * GEMMs with BF16 operands and FP32 accumulation. 1 (default) = banded
+ * 5th-generation tensor-core kernel for inference (bdis_net_forward,
+ * bdis_match_learned): activations in a zero-padded planar layout, a band of
+ * image rows with its halo staged by one bulk copy per channel plane, each
+ * 3x3 tap's operand a shifted window of it, accumulators in tensor memory,
+ * the next band's copy overlapping the epilogue; 2 = the per-tile tcgen05
+ * kernel (a 128-pixel tile's slab staged by the threads); 0 = mma.sync
+ * (warp-level BF16 MMA). Results agree up to FP32 accumulation order. The
+ * training forward takes the per-tile kernel under 1 and 2; inputs too wide
+ * for a kernel's shared memory take the next one down. Process-wide. */
 void bdis_set_net_variant(int tensor_path);
 int bdis_get_net_variant(void);
 

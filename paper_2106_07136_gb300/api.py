@@ -324,7 +324,8 @@ def get_pyramid_variant() -> int:
 
 
 def set_net_variant(tensor_path: int):
-    """Proposal network forward convolutions: 1 = tcgen05 kernel (default), 0 = mma.sync kernel."""
+    """Proposal network forward convolutions: 1 = banded tcgen05 kernel (default),
+    2 = per-tile tcgen05 kernel, 0 = mma.sync kernel."""
     _lib.load().bdis_set_net_variant(int(tensor_path))
 
 

@@ -412,6 +412,403 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem));
 }
 
+// ------------------------------------------- conv (tcgen05, banded inference)
+
+// The inference forward pass keeps every activation in a padded planar
+// layout in global memory: each image is framed by kPad zero rows and
+// columns (kPad = the largest dilation, so every tap of a real pixel lands
+// inside its own frame), frames are numbered back to back, and each group of
+// 8 channels is its own plane of 16-byte rows, with zero guard rows before
+// and after. A 3x3 tap is then a constant shift of the position numbering, a
+// plane's rows are exactly the 8-row x 16-byte core matrices of the tensor
+// cores' no-swizzle K-major operand layout, and the rows any band of
+// positions reads form one contiguous range per plane: one bulk copy each.
+//
+// The whole forward pass is one cooperative launch, one block per SM: the
+// input is packed, then the six layers run in turn with a grid barrier
+// between steps (a band's halo was written by other blocks). Within a layer
+// the block is warp-specialised, three stages in flight:
+//   - warps 8-11 (one lane each) issue each unit's MMAs (9 taps x CIN / 16
+//     per 128-position tile; M 128, N = COUT, K 16; every 4th tile each)
+//     into one of two tensor-memory accumulators, one COUT-column slice per
+//     tile; warp 8 also stages the units (a band of BH image rows of one
+//     image, all padded columns, with its halo of up to dil rows + dil
+//     columns either side) by bulk copies into two slab buffers;
+//   - warps 0-7 (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, of
+//     every other tile) take each finished accumulator, add the bias, apply
+//     the ReLU, pack to bf16 and write the real pixels, then hand the
+//     accumulator back; two warps per lane quarter hide each other's latency.
+// So unit k's MMAs run while unit k + 1's copy travels and unit k - 1's
+// epilogue drains. The MMAs bound it: measured on GB300, an M 128 x K 16
+// MMA whose A operand (4 KB) is read afresh from no-swizzle shared memory
+// takes about 68 cycles whether N is 32 or 64, so with 32 output channels
+// the tensor pipe runs at about a quarter of its dense rate.
+// Every wait is bounded by the global timer: on a timeout the block records
+// it in the network's fault word, waits (bounded) for its own copies and
+// MMAs in flight, frees its tensor memory and returns.
+constexpr int kPad = 4;                // frame border = the largest dilation
+constexpr int kBandCols = 256;         // tensor-memory columns per accumulator (two)
+constexpr int kBandSmem = 224 * 1024;  // dynamic shared memory per block (one per SM)
+constexpr int kBandEpiWarps = 8;       // two per tensor-memory lane quarter
+constexpr int kBandMmaWarps = 4;       // MMA issue: one lane of each takes every 4th tile
+constexpr int kBandThreads = 32 * (kBandEpiWarps + kBandMmaWarps);
+
+__host__ __device__ __forceinline__ long long pp_guard(int W) {
+  return (long long)kPad * (W + 2 * kPad) + kPad + 128;
+}
+
+// elements (bf16) between two channel planes of a padded planar buffer
+__host__ __device__ __forceinline__ long long pp_plane(int H, int W, int count) {
+  return ((long long)count * (H + 2 * kPad) * (W + 2 * kPad) + 2 * pp_guard(W)) * 8;
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void *band_smem_base() {
+  extern __shared__ __align__(128) uint8_t band_smem[];
+  return band_smem;
+}
+
+// One layer of the fused inference kernel below.
+struct BandLayer {
+  const __nv_bfloat16 *in, *wt;
+  const float *bias;
+  void *out;      // kFwdRelu: padded planar bf16; kFwdLinearF32: dense float map
+  int dil, BH, nsb;  // dilation, band rows, slab rows per channel plane
+};
+struct BandNet {
+  BandLayer layer[6];
+  const float *L, *R;  // the level planes (R with element stride r_stride)
+  int r_stride, H, W, count;
+  int slab_bytes;      // per slab buffer (the largest layer's), two buffers
+  unsigned *sync;      // grid barrier counter, zero at launch
+  int *fault;          // set when a bounded wait ran out
+};
+
+// Shared state of the fused kernel's block.
+struct BandShared {
+  uint32_t s_base, b_base, tmem;
+  uint32_t full_a[2], mma_a[2], free_a[2];
+};
+
+// Grid-wide barrier of the cooperative launch (all blocks are resident): the
+// block's writes are published, one thread counts the block in and waits,
+// bounded, for every block of the grid. `target` = barriers passed so far x
+// gridDim.x. Returns false (on every thread) if the wait ran out.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned target) {
+  __threadfence();
+  __syncthreads();
+  int ok = 1;
+  if (threadIdx.x == 0) {
+    atomicAdd(count, 1u);
+    const uint64_t t0 = global_ns();
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) break;
+      if (global_ns() - t0 > 1000000000ull) {  // 1 s
+        ok = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// One layer: the roles of the module comment over the layer's units. kg counts
+// the block's units over all layers (buffer = kg & 1, barrier phase = (kg >> 1)
+// & 1); on return every unit of the layer is written and its accumulators are
+// handed back. MODE kFwdRelu: out is a padded planar bf16 buffer of COUT
+// channels; kFwdLinearF32: out is the dense float map of channel 0.
+template <int CIN, int COUT, int MODE>
+__device__ bool band_layer(const BandNet &net, const BandLayer &ly, const BandShared &sh,
+                           float *sbias, long long &kg) {
+  static_assert(CIN % 16 == 0 && (COUT == 16 || COUT == 32), "tile");
+  static_assert(MODE == kFwdRelu || MODE == kFwdLinearF32, "forward only");
+  constexpr int KG = 9 * CIN / 8, NG = COUT / 8, CG = CIN / 8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int H = net.H, W = net.W, count = net.count, dil = ly.dil, BH = ly.BH;
+  const int nsb_max = ly.nsb, slab_bytes = net.slab_bytes;
+  const int Wp = W + 2 * kPad, Hp = H + 2 * kPad;
+  const long long F = (long long)Hp * Wp;
+  const long long plane_in = pp_plane(H, W, count), guard = pp_guard(W);
+  const int soff = dil * Wp + dil;
+  const int nb = (H + BH - 1) / BH;
+  const long long units = (long long)count * nb;
+  // the layer's weights and bias (the previous layer's MMAs are all done)
+  uint8_t *Bs = reinterpret_cast<uint8_t *>(band_smem_base()) + 2 * slab_bytes;
+  for (int i = tid; i < COUT * KG; i += kBandThreads) {
+    const int kgr = i / COUT, co = i - kgr * COUT;  // consecutive threads: consecutive rows
+    const uint4 v = *reinterpret_cast<const uint4 *>(ly.wt + (size_t)co * 9 * CIN + kgr * 8);
+    *reinterpret_cast<uint4 *>(Bs + ((kgr * NG + co / 8) * 8 + co % 8) * 16) = v;
+  }
+  if (tid < COUT) sbias[tid] = ly.bias[tid];
+  // weights: generic-proxy writes read by the tensor cores; the input: written
+  // by other blocks before the grid barrier, read by this block's bulk copies
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  auto band = [&](long long u, long long &q_s, int &cnt, int &tiles) {
+    const int b = (int)(u / nb), j = (int)(u - (long long)b * nb);
+    const int rows = min(BH, H - j * BH);
+    q_s = (long long)b * F + (long long)(kPad + j * BH) * Wp;
+    cnt = rows * Wp;
+    tiles = (cnt + 127) >> 7;
+  };
+  const long long nk = units > blockIdx.x ? (units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  bool ok = true;
+  if (warp >= kBandEpiWarps) {
+    // ---- copies (issuer 0) and MMAs (one lane of each issuer warp)
+    const int issuer = warp - kBandEpiWarps;
+    if (lane == 0 && nk > 0) {
+      constexpr uint32_t idesc = (1u << 4)                 // D: f32
+                                 | (1u << 7) | (1u << 10)  // A, B: bf16, both K-major
+                                 | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+      auto issue_load = [&](long long k) {
+        long long q_s;
+        int cnt, tiles;
+        band(blockIdx.x + k * gridDim.x, q_s, cnt, tiles);
+        const int s = (int)((kg + k) & 1), nsb = tiles * 128 + 2 * soff;
+        mbar_expect_tx(sh.full_a[s], (uint32_t)(CG * nsb * 16));
+        for (int cg = 0; cg < CG; ++cg)
+          bulk_load(sh.s_base + (uint32_t)(s * slab_bytes + cg * nsb_max * 16),
+                    ly.in + ((long long)cg * plane_in / 8 + guard + q_s - soff) * 8,
+                    (uint32_t)(nsb * 16), sh.full_a[s]);
+      };
+      // the last unit whose copy / MMAs went to each buffer (-1: none), for the timeout path
+      long long last_load[2] = {-1, -1}, last_mma[2] = {-1, -1};
+      if (issuer == 0) {
+        issue_load(0);
+        last_load[kg & 1] = kg;
+      }
+      for (long long k = 0; k < nk && ok; ++k) {
+        const long long g = kg + k;
+        const int s = (int)(g & 1);
+        const uint32_t ph = (uint32_t)((g >> 1) & 1);
+        ok = mbar_wait(sh.full_a[s], ph);  // unit k's slab has landed
+        if (ok && g >= 2) ok = mbar_wait(sh.free_a[s], ph ^ 1u);  // unit g - 2's epilogue is done
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        long long q_s;
+        int cnt, tiles;
+        band(blockIdx.x + k * gridDim.x, q_s, cnt, tiles);
+        // descriptors advance in 16-byte units of their start-address field
+        // (shared memory is far below the field's 256 KB reach, so no carry)
+        const uint64_t a0 = umma_smem_desc(sh.s_base + (uint32_t)(s * slab_bytes),
+                                           (uint32_t)nsb_max * 16, 128);
+        const uint64_t b0 = umma_smem_desc(sh.b_base, NG * 128, 128);
+        const uint32_t t0 = sh.tmem + (uint32_t)(s * kBandCols);
+#pragma unroll 1
+        for (int i = issuer; i < tiles; i += kBandMmaWarps) {
+          const uint32_t d_tmem = t0 + (uint32_t)(i * COUT);
+          const int rowi = soff + i * 128;
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int row0 = rowi + (tap / 3 - 1) * dil * Wp + (tap % 3 - 1) * dil;
+#pragma unroll
+            for (int kk = 0; kk < CIN / 16; ++kk) {
+              const uint64_t ad = a0 + (uint64_t)(row0 + 2 * kk * nsb_max);
+              const uint64_t bd = b0 + (uint64_t)((tap * CG + 2 * kk) * NG * 8);
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(tap | kk));
+            }
+          }
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                sh.mma_a[s]));
+        last_mma[s] = g;
+        // the next unit's copy goes to the other slab once unit g - 1's MMAs
+        // (queued ahead of unit g's) have read it
+        if (issuer == 0 && k + 1 < nk) {
+          if (k >= 1) ok = mbar_wait(sh.mma_a[s ^ 1], (uint32_t)(((g - 1) >> 1) & 1));
+          if (!ok) break;
+          issue_load(k + 1);
+          last_load[s ^ 1] = g + 1;
+        }
+      }
+      if (!ok) {
+        atomicOr(net.fault, 1);  // reported by bdis_net_status
+        // let the copies and MMAs this block issued land before its memory is released
+        for (int b2 = 0; b2 < 2; ++b2) {
+          if (last_load[b2] >= 0) mbar_wait(sh.full_a[b2], (uint32_t)((last_load[b2] >> 1) & 1));
+          if (last_mma[b2] >= 0) mbar_wait(sh.mma_a[b2], (uint32_t)((last_mma[b2] >> 1) & 1));
+        }
+      }
+    }
+  } else {
+    // ---- epilogue (warps 0 .. kBandEpiWarps - 1)
+    const int quarter = warp & 3, parity = warp >> 2;
+    const float *bs = sbias;
+    for (long long k = 0; k < nk; ++k) {
+      const long long g = kg + k;
+      const int s = (int)(g & 1);
+      long long q_s;
+      int cnt, tiles;
+      band(blockIdx.x + k * gridDim.x, q_s, cnt, tiles);
+      ok = mbar_wait(sh.mma_a[s], (uint32_t)((g >> 1) & 1));
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      const int b = (int)(q_s / F);
+      for (int i = parity; i < tiles; i += kBandEpiWarps / 4) {
+        const uint32_t taddr = sh.tmem + ((uint32_t)(quarter * 32) << 16) +
+                               (uint32_t)(s * kBandCols + i * COUT);
+        float d[COUT];
+        if constexpr (COUT == 32) {
+          uint32_t r[32];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < COUT; ++c) d[c] = __uint_as_float(r[c]);
+        } else {
+          uint32_t r[16];
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+              "%13,%14,%15}, [%16];\n"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < COUT; ++c) d[c] = __uint_as_float(r[c]);
+        }
+        const int m = i * 128 + quarter * 32 + lane;  // position within the band
+        const int xp = m % Wp, x = xp - kPad;
+        if (m < cnt && x >= 0 && x < W) {
+          const long long q = q_s + m;
+          if constexpr (MODE == kFwdRelu) {
+            uint32_t pk[COUT / 2];
+#pragma unroll
+            for (int c = 0; c < COUT; c += 2)
+              pk[c / 2] = pack_bf16(fmaxf(d[c] + bs[c], 0.f), fmaxf(d[c + 1] + bs[c + 1], 0.f));
+            const long long plane_out = pp_plane(H, W, count) / 8;  // in 16-byte rows
+            uint4 *o = reinterpret_cast<uint4 *>(ly.out) + guard + q;
+#pragma unroll
+            for (int v = 0; v < COUT / 8; ++v)
+              o[v * plane_out] =
+                  make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+          } else {
+            const int y = (int)((q - (long long)b * F) / Wp) - kPad;
+            reinterpret_cast<float *>(ly.out)[((long long)b * H + y) * W + x] = d[0] + bs[0];
+          }
+        }
+      }
+      // this accumulator is read: the unit two later may overwrite it
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      mbar_arrive(sh.free_a[s]);
+    }
+  }
+  kg += nk;
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
+// The whole inference forward pass in one cooperative launch (one block per
+// SM): the input planes are packed into x0, then the six layers run in turn,
+// a grid barrier between steps (a layer reads the bands around its own, which
+// other blocks wrote). Weights and bias are restaged per layer; the slabs,
+// barriers and tensor memory carry over.
+__global__ void __launch_bounds__(kBandThreads, 1) net_forward_kernel(const BandNet net) {
+  __shared__ __align__(8) uint64_t mb_full[2], mb_mma[2], mb_free[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ float sbias[32];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  BandShared sh;
+  for (int i = 0; i < 2; ++i) {
+    sh.full_a[i] = (uint32_t)__cvta_generic_to_shared(&mb_full[i]);
+    sh.mma_a[i] = (uint32_t)__cvta_generic_to_shared(&mb_mma[i]);
+    sh.free_a[i] = (uint32_t)__cvta_generic_to_shared(&mb_free[i]);
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(sh.full_a[i], 1);
+      mbar_init(sh.mma_a[i], kBandMmaWarps);
+      mbar_init(sh.free_a[i], 32 * kBandEpiWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    const uint32_t slot = (uint32_t)__cvta_generic_to_shared(&tmem_slot);
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(slot),
+                 "n"(2 * kBandCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  // x0: plane 0 = [(L - 128) / 64, (R - 128) / 64, 0 x 6] at every real pixel
+  // (plane 1 and the borders stay zero)
+  {
+    const int H = net.H, W = net.W, Wp = W + 2 * kPad, Hp = H + 2 * kPad;
+    const long long plane = (long long)H * W, total = plane * net.count;
+    uint4 *x0 = reinterpret_cast<uint4 *>(const_cast<__nv_bfloat16 *>(net.layer[0].in));
+    for (long long p = (long long)blockIdx.x * kBandThreads + tid; p < total;
+         p += (long long)gridDim.x * kBandThreads) {
+      const int b = (int)(p / plane);
+      const int rem = (int)(p - (long long)b * plane);
+      const int y = rem / W, x = rem - (rem / W) * W;
+      const long long q = ((long long)b * Hp + y + kPad) * Wp + x + kPad;
+      const float l = (__ldg(net.L + p) - 128.f) * (1.f / 64.f);
+      const float r = (__ldg(net.R + p * net.r_stride) - 128.f) * (1.f / 64.f);
+      x0[pp_guard(W) + q] = make_uint4(pack_bf16(l, r), 0u, 0u, 0u);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  sh.tmem = tmem_slot;
+  sh.s_base = (uint32_t)__cvta_generic_to_shared(band_smem_base());
+  sh.b_base = sh.s_base + 2u * (uint32_t)net.slab_bytes;
+  long long kg = 0;
+  unsigned passed = 0;
+  bool ok = grid_barrier(net.sync, ++passed * gridDim.x);
+  if (ok) ok = band_layer<16, 32, kFwdRelu>(net, net.layer[0], sh, sbias, kg);
+  for (int l = 1; l < 5 && ok; ++l) {
+    ok = grid_barrier(net.sync, ++passed * gridDim.x);
+    if (ok) ok = band_layer<32, 32, kFwdRelu>(net, net.layer[l], sh, sbias, kg);
+  }
+  if (ok) ok = grid_barrier(net.sync, ++passed * gridDim.x);
+  if (ok) ok = band_layer<32, 16, kFwdLinearF32>(net, net.layer[5], sh, sbias, kg);
+  if (!ok && tid == 0) atomicOr(net.fault, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(sh.tmem),
+                 "n"(2 * kBandCols));
+}
+
 // ------------------------------------------------------- weight gradient
 
 // dW[co][tap][ci] += sum_p G[p][co] * X[p shifted by tap][ci]; db[co] += sum_p G[p][co].
@@ -617,6 +1014,10 @@ struct bdis_net {
   float *z6 = nullptr;
   // device word set when a forward kernel's bounded wait ran out
   int *fault = nullptr;
+  unsigned *sync = nullptr;  // grid barrier counter of the fused inference kernel
+  // inference activations in the padded planar layout, for pp_h x pp_w x pp_count
+  __nv_bfloat16 *x0pp = nullptr, *app[5] = {};
+  int pp_h = 0, pp_w = 0, pp_count = 0;
 };
 
 namespace {
@@ -633,6 +1034,37 @@ void net_free_acts(bdis_net *n) {
   n->g6 = nullptr;
   n->z6 = nullptr;
   n->cap = 0;
+}
+
+void net_free_pp(bdis_net *n) {
+  cudaFree(n->x0pp);
+  for (auto &p : n->app) cudaFree(p);
+  n->x0pp = nullptr;
+  for (auto &p : n->app) p = nullptr;
+  n->pp_h = n->pp_w = n->pp_count = 0;
+}
+
+// Padded planar activations of the inference pass for count h x w images,
+// zeroed (borders and guards stay zero: only real pixels are ever written).
+bdis_status net_reserve_pp(bdis_net *n, int h, int w, int count, cudaStream_t st) {
+  if (n->pp_h == h && n->pp_w == w && n->pp_count == count) return BDIS_OK;
+  net_free_pp(n);
+  const size_t plane = (size_t)pp_plane(h, w, count) * sizeof(__nv_bfloat16);
+  cudaError_t e = bdis::device_alloc((void **)&n->x0pp, 2 * plane);
+  for (auto &p : n->app)
+    if (e == cudaSuccess) e = bdis::device_alloc((void **)&p, 4 * plane);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->x0pp, 0, 2 * plane, st);
+  for (auto &p : n->app)
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, 4 * plane, st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    net_free_pp(n);
+    return e == cudaErrorMemoryAllocation ? BDIS_E_NOMEM : bdis::record_cuda(e);
+  }
+  n->pp_h = h;
+  n->pp_w = w;
+  n->pp_count = count;
+  return BDIS_OK;
 }
 
 bdis_status net_reserve(bdis_net *n, long long pixels) {
@@ -670,7 +1102,10 @@ cudaError_t pack_all(bdis_net *n, cudaStream_t st) {
 }
 
 int g_sms = 0;
-int g_net_tc = 1;  // forward convolutions: 1 = tcgen05 kernel (default), 0 = mma.sync kernel
+// forward convolutions: 1 = banded tcgen05 kernel for inference (default; training
+// forwards and inputs too wide for it take the per-tile one), 2 = per-tile tcgen05
+// kernel, 0 = mma.sync kernel
+int g_net_tc = 1;
 
 // Dynamic shared memory of the tcgen05 kernel is exactly its slab and the
 // weights (19 to 72 KB for 80-pixel-wide level-3 inputs), so up to four
@@ -707,16 +1142,18 @@ bool conv_tc(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias
   return true;
 }
 
+void init_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (g_sms <= 0) g_sms = 152;
+}
+
 template <int CIN, int COUT, int MODE>
 void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, int dil, int H,
           int W, long long total, const __nv_bfloat16 *mask, void *out, int *fault,
           cudaStream_t st) {
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 152;
-  }
+  if (!g_sms) init_sms();
   if constexpr (MODE == kFwdRelu || MODE == kFwdLinearF32) {
     if (g_net_tc && conv_tc<CIN, COUT, MODE>(in, wt, bias, dil, H, W, total, out, fault, st))
       return;
@@ -725,6 +1162,88 @@ void conv(const __nv_bfloat16 *in, const __nv_bfloat16 *wt, const float *bias, i
   const unsigned grid = (unsigned)std::min<long long>(tiles, (long long)g_sms * 3);
   conv_mma_kernel<CIN, COUT, MODE><<<grid, 128, 0, st>>>(in, wt, bias, dil, H, W, total, mask,
                                                          out);
+}
+
+// Band height of one layer of the fused kernel: the tallest band whose two
+// slabs fit the shared memory beside the largest layer's weights and whose
+// tiles fit one accumulator's tensor-memory columns; 0 if none does (images
+// too wide: the per-tile kernels run instead).
+constexpr int kBandWeightsMax = 36 * 4 * 128;  // 32 -> 32 channels, 9 taps
+
+template <int CIN, int COUT>
+int band_rows(int dil, int H, int W, int *nsb_out) {
+  const int Wp = W + 2 * kPad, soff = dil * Wp + dil;
+  for (int bh = H; bh >= 1; --bh) {
+    const int tiles = (bh * Wp + 127) / 128;
+    if (tiles * COUT > kBandCols) continue;
+    const int nsb = tiles * 128 + 2 * soff;
+    if (2 * (CIN / 8) * nsb * 16 + kBandWeightsMax <= kBandSmem) {
+      *nsb_out = nsb;
+      return bh;
+    }
+  }
+  return 0;
+}
+
+// The inference forward pass as one cooperative launch of net_forward_kernel:
+// level planes in, the proposal (channel 0 of the last layer) written straight
+// to `out`. Returns false, having launched nothing, when the images are too
+// wide for it or the device cannot run the grid cooperatively.
+bool forward_pp(bdis_net *n, const float *L3, const float *R3, int r_stride, int H, int W,
+                int count, float *out, cudaStream_t st) {
+  if (g_net_tc != 1) return false;
+  BandNet net{};
+  int nsb[6], bh[6];
+  bh[0] = band_rows<16, 32>(kDil[0], H, W, &nsb[0]);
+  for (int l = 1; l < 5; ++l) bh[l] = band_rows<32, 32>(kDil[l], H, W, &nsb[l]);
+  bh[5] = band_rows<32, 16>(kDil[5], H, W, &nsb[5]);
+  int slab = 0;
+  for (int l = 0; l < 6; ++l) {
+    if (!bh[l]) return false;
+    slab = std::max(slab, (kCinP[l] / 8) * nsb[l] * 16);
+  }
+  const int smem = 2 * slab + kBandWeightsMax;
+  static uint64_t attr_set = 0;  // bit d: the shared-memory limit is set on device d
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !(attr_set >> dev & 1u)) {
+    if (cudaFuncSetAttribute(net_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kBandSmem) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (dev < 64) attr_set |= 1ull << dev;
+  }
+  const __nv_bfloat16 *ins[6] = {n->x0pp, n->app[0], n->app[1], n->app[2], n->app[3], n->app[4]};
+  for (int l = 0; l < 6; ++l) {
+    net.layer[l].in = ins[l];
+    net.layer[l].wt = n->wf[l];
+    net.layer[l].bias = n->bias[l];
+    net.layer[l].out = l < 5 ? (void *)n->app[l] : (void *)out;
+    net.layer[l].dil = kDil[l];
+    net.layer[l].BH = bh[l];
+    net.layer[l].nsb = nsb[l];
+  }
+  net.L = L3;
+  net.R = R3;
+  net.r_stride = r_stride;
+  net.H = H;
+  net.W = W;
+  net.count = count;
+  net.slab_bytes = slab;
+  net.sync = n->sync;
+  net.fault = n->fault;
+  if (cudaMemsetAsync(n->sync, 0, sizeof(unsigned), st) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  void *args[] = {&net};
+  if (cudaLaunchCooperativeKernel((const void *)net_forward_kernel, dim3((unsigned)g_sms),
+                                  dim3(kBandThreads), args, (size_t)smem, st) != cudaSuccess) {
+    cudaGetLastError();  // not sticky: the per-tile kernels run instead
+    return false;
+  }
+  return true;
 }
 
 cudaError_t forward(bdis_net *n, const float *L3, const float *R3, int r_stride, int H, int W,
@@ -780,12 +1299,14 @@ cudaError_t backward(bdis_net *n, int H, int W, long long total, cudaStream_t st
 void net_release(bdis_net *n) {
   if (!n) return;
   net_free_acts(n);
+  net_free_pp(n);
   cudaFree(n->w);
   cudaFree(n->m);
   cudaFree(n->v);
   cudaFree(n->grad);
   cudaFree(n->loss);
   cudaFree(n->fault);
+  cudaFree(n->sync);
   for (int l = 0; l < kLayers; ++l) {
     cudaFree(n->wf[l]);
     cudaFree(n->wb[l]);
@@ -803,6 +1324,16 @@ namespace bdis {
 bdis_status net_forward_on(bdis_net *n, const float *L, const float *R, int r_stride, int w,
                            int h, int count, float *out, cudaStream_t st) {
   const long long total = (long long)w * h * count;
+  if (g_net_tc == 1) {
+    if (!g_sms) init_sms();
+    int nsb = 0;
+    if (band_rows<32, 32>(4, h, w, &nsb) && band_rows<16, 32>(1, h, w, &nsb) &&
+        band_rows<32, 16>(1, h, w, &nsb)) {
+      bdis_status s = net_reserve_pp(n, h, w, count, st);
+      if (s != BDIS_OK) return s;
+      if (forward_pp(n, L, R, r_stride, h, w, count, out, st)) return record_cuda(cudaGetLastError());
+    }
+  }
   bdis_status s = net_reserve(n, total);
   if (s != BDIS_OK) return s;
   cudaError_t e = forward(n, L, R, r_stride, h, w, total, st);
@@ -819,7 +1350,9 @@ extern "C" {
 
 int bdis_net_weight_count(void) { return kMasterCount; }
 
-void bdis_set_net_variant(int tensor_path) { g_net_tc = tensor_path ? 1 : 0; }
+void bdis_set_net_variant(int tensor_path) {
+  g_net_tc = tensor_path < 0 ? 0 : (tensor_path > 2 ? 1 : tensor_path);
+}
 
 int bdis_get_net_variant(void) { return g_net_tc; }
 
@@ -841,6 +1374,7 @@ bdis_status bdis_net_create(int device, const float *weights, bdis_net **out) {
   alloc((void **)&n->grad, wb);
   alloc((void **)&n->loss, sizeof(float));
   alloc((void **)&n->fault, sizeof(int));
+  alloc((void **)&n->sync, sizeof(unsigned));
   for (int l = 0; l < kLayers; ++l) {
     alloc((void **)&n->wf[l], 2 * kCoutP[l] * 9 * kCinP[l]);
     if (l > 0) alloc((void **)&n->wb[l], 2 * kCoutP[l] * 9 * kCinP[l]);
@@ -868,16 +1402,8 @@ bdis_status bdis_net_forward(bdis_net *n, const float *L3, const float *R3, int 
   if (!n || !L3 || !R3 || !disparity || width < 1 || height < 1 || count < 1 ||
       (r_stride != 1 && r_stride != 2))
     return BDIS_E_INVALID_ARG;
-  const long long total = (long long)width * height * count;
-  bdis_status s = net_reserve(n, total);
-  if (s != BDIS_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = forward(n, L3, R3, r_stride, height, width, total, st);
-  if (e == cudaSuccess) {
-    take_channel0_kernel<<<nblocks(total, 256), 256, 0, st>>>(n->z6, total, disparity);
-    e = cudaGetLastError();
-  }
-  return bdis::record_cuda(e);
+  return bdis::net_forward_on(n, L3, R3, r_stride, width, height, count, disparity,
+                              static_cast<cudaStream_t>(stream));
 }
 
 bdis_status bdis_net_gradient(bdis_net *n, const float *L3, const float *R3, int r_stride,
