@@ -4,7 +4,7 @@
 A step is one pass of the whole method (pyramid + gradients, inverse search
 with the Bayesian posterior at every scale, densification) over a batch of
 640x480 uint8 pairs resident in device memory, through the library's C ABI.
-Default: 128 pairs per step, patch 8, overlap 0.75, 12 iterations, scales
+Default: 512 pairs per step, patch 8, overlap 0.75, 12 iterations, scales
 4..0, gamma 0.75 (the paper's settings, Sec. 3).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--batch", type=int, default=128, help="pairs per step and rank")
+    ap.add_argument("--batch", type=int, default=512, help="pairs per step and rank")
     ap.add_argument("--unique", type=int, default=16, help="distinct seeded pairs per rank")
     ap.add_argument("--patch", type=int, default=8)
     ap.add_argument("--variant", type=int, default=0,
