@@ -5,9 +5,13 @@
 
 Each step draws a batch of seeded surgical-like 640x480 pairs on the device
 (synth.stereo_torch), builds their pyramid with the library's kernels, and
-takes one Adam step of the network on level 3 against the ground-truth
-disparity at level 3 (every 8th pixel, divided by 8). The forward pass,
-backward pass and optimiser all run in libbdis.so.
+takes one Adam step of the network on level 3. The labels come from the
+generator and the plain method: the ground-truth disparity at level 3 (every
+8th pixel, divided by 8) where it exists, and where it does not (pixels
+occluded in the right view) the plain method's own level-3 map, searched
+from level 4 down with the paper's settings by the same kernels
+(`--labels gt` keeps the ground truth alone). The forward pass, backward
+pass and optimiser all run in libbdis.so.
 """
 from __future__ import annotations
 
@@ -38,11 +42,31 @@ def level3(L, R):
     return Lp, Rp
 
 
+def plain_level3(L, R, params):
+    """The plain method's dense map at level 3 (coarse to fine from the
+    coarsest level), with every pixel estimated or carried (not the finest
+    level), by the library's step kernels."""
+    Lp, Rp, Gp = bd.prepare_level0(L, R)
+    planes = {0: (Lp, Rp, Gp)}
+    for lvl in range(1, params.coarsest_scale + 1):
+        Lp, Rp, Gp = bd.pyramid_level(Lp, Rp)
+        planes[lvl] = (Lp, Rp, Gp)
+    coarse = None
+    for lvl in range(params.coarsest_scale, 2, -1):
+        Lp, Rp, Gp = planes[lvl]
+        s = bd.search_level(Lp, Rp, Gp, coarse, params, debug=False)
+        coarse = bd.densify_level(tuple(Lp.shape[1:]), params, s["d_star"], s["weight"], coarse,
+                                  False, Lp, Rp)
+    return coarse
+
+
 def train(pairs=50000, batch=64, lr=2e-3, lr_end=1e-4, seed=0, log_every=100, device="cuda",
-          epochs=1):
-    """`epochs` passes over the same `pairs` seeded pairs, one cosine schedule."""
+          epochs=1, labels="gt+plain"):
+    """`epochs` passes over the same `pairs` seeded pairs, one cosine schedule.
+    labels: "gt+plain" (ground truth, the plain method where it has none) or "gt"."""
     gen = TorchCfg2Generator(device=device)
     net = bd.ProposalNet(bd.net_init_weights(seed=seed))
+    params = bd.default_params()
     per_epoch = max(1, pairs // batch)
     steps = per_epoch * max(1, epochs)
     hist = []
@@ -51,6 +75,8 @@ def train(pairs=50000, batch=64, lr=2e-3, lr_end=1e-4, seed=0, log_every=100, de
         L, R, gt = gen.batch(TRAIN_SEED + s % per_epoch, batch)
         L3, R3 = level3(L, R)
         label = (gt[:, ::8, ::8] / 8.0).contiguous()
+        if labels == "gt+plain":
+            label = torch.where(torch.isfinite(label), label, plain_level3(L, R, params))
         f = s / max(steps - 1, 1)
         rate = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * f))
         loss = net.train_step(L3, R3, label, rate)
@@ -70,13 +96,15 @@ def main():
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--out", default=DEFAULT_OUT)
+    ap.add_argument("--labels", choices=["gt+plain", "gt"], default="gt+plain")
     a = ap.parse_args()
-    w, hist, secs = train(a.pairs, a.batch, a.lr, epochs=a.epochs)
+    w, hist, secs = train(a.pairs, a.batch, a.lr, epochs=a.epochs, labels=a.labels)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    what = ("level-3 ground truth, the plain method's level-3 map where the ground truth has "
+            "none" if a.labels == "gt+plain" else "level-3 ground truth")
     note = (f"trained on {a.pairs} seeded 640x480 surgical-like pairs (seeds from {TRAIN_SEED}), "
             f"{a.epochs} epoch(s), batch {a.batch}, Adam lr {a.lr} cosine to 1e-4, Huber loss on "
-            f"level-3 ground truth; "
-            f"final loss {hist[-1]:.4f}, {secs:.1f}s")
+            f"{what}; final loss {hist[-1]:.4f}, {secs:.1f}s")
     bd.save_net_weights(a.out, w, note)
     print(note)
 
