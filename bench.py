@@ -53,6 +53,16 @@ def alu_peak(device, sm_max_mhz):
     return tflops, src
 
 
+def tensor_peak():
+    """Measured dense bf16 tensor throughput (MEASURED_PEAKS.json, burst: the
+    network is timed alone), else the earlier measurement."""
+    try:
+        v = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        return v, "of measured (MEASURED_PEAKS.json bf16_tflops, cuBLAS burst)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 1900.0, "of fallback (1.9 PFLOP/s bf16, an earlier GB300 measurement)"
+
+
 def hbm_peak():
     """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json), else
     the earlier measurement."""
@@ -83,6 +93,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the ps12 variant, latency and e2e measurements")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="only the plain vs learned-start comparison (a profiling aid)")
     return ap.parse_args()
 
 
@@ -377,6 +389,11 @@ def main():
     stream = torch.cuda.current_stream(device)
     m = bd.Matcher(device, stream)
     m.reserve(W, H, B, params)
+    if args.learned_only:
+        print(json.dumps({"learned_vs_plain": measure_learned(args, bd, m, left, right, Lh, Rh,
+                                                              Dgt, device, stream)}), flush=True)
+        m.close()
+        return 0
 
     clocks = ClockSampler(local)  # running through the warm-up, kept for the timed region
     for _ in range(args.warmup):
@@ -508,6 +525,15 @@ def main():
         "accuracy": acc,
     }
     line.update(extras)
+    net_info = extras.get("learned_vs_plain", {}).get("proposal_net")
+    if net_info:
+        by_kernel["proposal_net"] = {"bound": "tensor", "achieved": net_info["achieved_tflops"],
+                                     "peak": net_info["peak_tflops"], "unit": "TFLOP/s",
+                                     "frac": net_info["frac"],
+                                     "ms_per_step": net_info["ms_per_step"],
+                                     "algorithmic_flops_per_step":
+                                         net_info["algorithmic_flops_per_step"]}
+        by_kernel["peak_sources"]["tensor"] = net_info["peak_source"]
     if cpu is not None:
         line["cpu_baseline"] = cpu
     m.close()
@@ -692,6 +718,21 @@ def measure_learned(args, bd, m, left, right, Lh, Rh, Dgt, device, stream,
         torch.cuda.synchronize()
         return B * k / (ev0.elapsed_time(ev1) / 1e3)
 
+    # the network alone on the batch's level-3 planes (the learned start's main cost)
+    L3, R3, _ = bd.prepare_level0(left, right)
+    for _ in range(3):
+        L3, R3, _ = bd.pyramid_level(L3, R3)
+    prop = torch.empty((B,) + tuple(L3.shape[1:]), dtype=torch.float32, device=device)
+    net_ms = B / rate(lambda: prop.copy_(net.forward(L3, R3))) * 1e3
+    net.status()
+    px = B * L3.shape[1] * L3.shape[2]
+    flop = px * 2 * 9 * sum(ci * co for ci, co in bd.api.NET_CHANNELS)
+    bf16_peak, bf16_src = tensor_peak()
+    net_info = {"ms_per_step": net_ms, "pixels_per_step": px, "algorithmic_flops_per_step": flop,
+                "achieved_tflops": flop / (net_ms / 1e3) / 1e12, "peak_tflops": bf16_peak,
+                "frac": flop / (net_ms / 1e3) / 1e12 / bf16_peak, "peak_source": bf16_src,
+                "kernel": "net_forward_kernel (banded tcgen05, one cooperative launch)"}
+    del L3, R3, prop
     rows = []
     for it in iterations:
         p = bd.default_params(**dict(params_kw(args.patch), iterations=it))
@@ -727,7 +768,7 @@ def measure_learned(args, bd, m, left, right, Lh, Rh, Dgt, device, stream,
                                           "bad1": best[kind]["bad1"],
                                           "mean_abs": best[kind]["mean_abs"]}
     fp, fl = fastest("plain"), fastest("learned")
-    return {"weights": note, "rows": rows,
+    return {"weights": note, "rows": rows, "proposal_net": net_info,
             "matched_error": {
                 "bound": "bad-1 <= plain at 12 iterations + 0.1 point",
                 "plain_reference_12it": {"pairs_per_s": ref["pairs_per_s"], "bad1": ref["bad1"]},
