@@ -718,21 +718,24 @@ def measure_learned(args, bd, m, left, right, Lh, Rh, Dgt, device, stream,
         torch.cuda.synchronize()
         return B * k / (ev0.elapsed_time(ev1) / 1e3)
 
-    # the network alone on the batch's level-3 planes (the learned start's main cost)
-    L3, R3, _ = bd.prepare_level0(left, right)
-    for _ in range(3):
-        L3, R3, _ = bd.pyramid_level(L3, R3)
-    prop = torch.empty((B,) + tuple(L3.shape[1:]), dtype=torch.float32, device=device)
-    net_ms = B / rate(lambda: prop.copy_(net.forward(L3, R3))) * 1e3
+    # the network alone on the batch's planes of the proposal level (the
+    # learned start's main cost)
+    level = bd.proposal_level(params_kw(args.patch)["coarsest_scale"])
+    Lq, Rq, _ = bd.prepare_level0(left, right)
+    for _ in range(level):
+        Lq, Rq, _ = bd.pyramid_level(Lq, Rq)
+    prop = torch.empty((B,) + tuple(Lq.shape[1:]), dtype=torch.float32, device=device)
+    net_ms = B / rate(lambda: prop.copy_(net.forward(Lq, Rq))) * 1e3
     net.status()
-    px = B * L3.shape[1] * L3.shape[2]
+    px = B * Lq.shape[1] * Lq.shape[2]
     flop = px * 2 * 9 * sum(ci * co for ci, co in bd.api.NET_CHANNELS)
     bf16_peak, bf16_src = tensor_peak()
     net_info = {"ms_per_step": net_ms, "pixels_per_step": px, "algorithmic_flops_per_step": flop,
                 "achieved_tflops": flop / (net_ms / 1e3) / 1e12, "peak_tflops": bf16_peak,
                 "frac": flop / (net_ms / 1e3) / 1e12 / bf16_peak, "peak_source": bf16_src,
-                "kernel": "net_forward_kernel (banded tcgen05, one cooperative launch)"}
-    del L3, R3, prop
+                "kernel": "net_forward_kernel (banded tcgen05, one cooperative launch)",
+                "level": level, "input": f"{B} x {Lq.shape[2]}x{Lq.shape[1]}"}
+    del Lq, Rq, prop
     rows = []
     for it in iterations:
         p = bd.default_params(**dict(params_kw(args.patch), iterations=it))

@@ -217,12 +217,19 @@ bdis_status bdis_match_seeded(bdis_handle *h, const bdis_image *left, const bdis
                               const bdis_params *p, const float *seed, int seed_level,
                               int fallback, float *disparity_out);
 
-/* Learned start: the proposal network runs on pyramid level min(3,
- * coarsest) of these pairs (inside the same launch sequence) and its output
- * seeds the coarsest level as at bdis_match_seeded. */
+/* Learned start: the proposal network runs on pyramid level
+ * bdis_proposal_level(coarsest) of these pairs (inside the same launch
+ * sequence) and its output seeds the coarsest level as at bdis_match_seeded. */
 bdis_status bdis_match_learned(bdis_handle *h, bdis_net *net, const bdis_image *left,
                                const bdis_image *right, const bdis_params *p, int fallback,
                                float *disparity_out);
+
+/* The pyramid level the learned start runs its network on for a given
+ * coarsest scale: min(4, coarsest_scale) (-1 for a negative scale). Its map
+ * is reduced to level coarsest + 1 by block means (as at bdis_match_seeded),
+ * so a level near the coarsest loses no information the seed keeps; the
+ * network is trained on this level. */
+int bdis_proposal_level(int coarsest_scale);
 
 /* Same, with HOST buffers: left/right are `count` dense width x height uint8
  * images in host memory, disparity_out a dense host float array. The call

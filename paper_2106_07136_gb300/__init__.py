@@ -23,6 +23,7 @@ from .api import (  # noqa: F401
     pack_right,
     patch_count,
     probe_fp32_tflops,
+    proposal_level,
     set_search_variant,
     get_search_variant,
     set_search_tiling,

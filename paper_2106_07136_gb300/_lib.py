@@ -30,6 +30,7 @@ EXPORTED = [
     "bdis_net_train_step", "bdis_net_get_weights", "bdis_net_destroy", "bdis_match_seeded",
     "bdis_match_learned", "bdis_select_start", "bdis_host_wait_timeout",
     "bdis_inject_alloc_failures", "bdis_net_status", "bdis_net_inject_timeout",
+    "bdis_proposal_level",
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
@@ -135,6 +136,8 @@ def load():
                                        c_void_p, c_void_p, c_void_p]
     fp = P(c_float)
     lib.bdis_net_weight_count.restype = c_int
+    lib.bdis_proposal_level.argtypes = [c_int]
+    lib.bdis_proposal_level.restype = c_int
     lib.bdis_net_create.argtypes = [c_int, c_void_p, P(c_void_p)]
     lib.bdis_net_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, c_int,
                                      c_void_p, c_void_p]

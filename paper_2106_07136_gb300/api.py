@@ -186,7 +186,8 @@ class Matcher:
 
     def match_learned(self, net, left, right, params: BdisParams = None, fallback: bool = True,
                       out=None):
-        """Coarsest level seeded by the proposal network (ProposalNet) run on level 3."""
+        """Coarsest level seeded by the proposal network (ProposalNet) run on
+        pyramid level proposal_level(params.coarsest_scale)."""
         params = params if params is not None else default_params()
         squeeze = left.dim() == 2
         lb, rb = _as_batch(left), _as_batch(right)
@@ -413,6 +414,11 @@ NET_CHANNELS = ((2, 32), (32, 32), (32, 32), (32, 32), (32, 32), (32, 1))
 
 def net_weight_count() -> int:
     return int(_lib.load().bdis_net_weight_count())
+
+
+def proposal_level(coarsest_scale: int) -> int:
+    """The pyramid level the learned start runs the proposal network on."""
+    return int(_lib.load().bdis_proposal_level(int(coarsest_scale)))
 
 
 def net_init_weights(seed: int = 0) -> np.ndarray:

@@ -98,7 +98,7 @@ Layout plan_layout(int w, int h, int count, const bdis_params &p, bool host_stag
     lay.post2 = take(np_top * sizeof(float));
     lay.flags1 = take(np_top);
     lay.flags2 = take(np_top);
-    lay.prop_level = top < 3 ? top : 3;
+    lay.prop_level = proposal_level(top);
     lay.prop = take((size_t)lay.lw[lay.prop_level] * lay.lh[lay.prop_level] * count *
                     sizeof(float));
   }
@@ -802,9 +802,13 @@ bdis_status bdis_match_learned(bdis_handle *h, bdis_net *net, const bdis_image *
   if (!net || !p) return BDIS_E_INVALID_ARG;
   Seed seed;
   seed.net = net;
-  seed.level = p->coarsest_scale < 3 ? p->coarsest_scale : 3;
+  seed.level = proposal_level(p->coarsest_scale);
   seed.fallback = fallback ? 1 : 0;
   return match_with_seed(h, left, right, p, seed, disparity_out);
+}
+
+int bdis_proposal_level(int coarsest_scale) {
+  return coarsest_scale < 0 ? -1 : proposal_level(coarsest_scale);
 }
 
 bdis_status bdis_warm_map(const float *prev, int width, int height, int level, int count,

@@ -28,6 +28,13 @@ constexpr float kConvergeTol = 0.02f;
 constexpr float kStepTol = 1e-4f;
 // R16: seeded and plain results of one patch this close (px) are one solution
 constexpr float kSameSolution = 0.1f;
+// Pyramid level the proposal network of the learned start runs on (at most
+// the coarsest level). Its map seeds the coarsest searched level L through
+// block means at level L + 1 (R16), so a level near L loses nothing.
+constexpr int kProposalLevel = 4;
+__host__ __device__ inline int proposal_level(int coarsest) {
+  return coarsest < kProposalLevel ? coarsest : kProposalLevel;
+}
 // Largest window the search kernel keeps track of.
 constexpr int kMaxWindow = 15;
 // Largest patch side (one patch per group of at most 32 lanes).
@@ -92,7 +99,7 @@ struct Layout {
   // second search of the coarsest level (R16) and the posteriors / flags of both
   size_t d_star2 = 0, weight2 = 0, post1 = 0, post2 = 0, flags1 = 0, flags2 = 0;
   size_t prop = 0;  // network proposal at the proposal level
-  int prop_level = 3;
+  int prop_level = kProposalLevel;
   size_t in_left = 0, in_right = 0, out = 0;  // host-path staging
   size_t bytes = 0;
 };

@@ -1,15 +1,17 @@
 // net.cu -- the learned coarse proposal: a 6-layer 3x3 convolutional network
-// on the level-3 pyramid pair, BF16 weights and activations, FP32
-// accumulation, forward and training kernels on the tensor cores.
+// on one pyramid level of the pair (level 4 of the paper's 5 scales, the
+// level the learned start runs it on), BF16 weights and activations, FP32
+// accumulation, forward and training kernels on the tensor cores. The
+// network is fully convolutional: any level size works.
 //
 // Not part of the paper: the paper's method starts its coarsest level from 0
 // (Sec. 2.1); this network proposes a start instead, and BDIS refines it.
 //
 // Architecture (all 3x3, zero padding, dilations 1, 2, 4, 4, 2, 1 so the
-// receptive field spans +-14 level-3 pixels):
+// receptive field spans +-14 pixels of its level):
 //   x0 = [(L - 128) / 64, (R - 128) / 64]           2 channels (padded to 16)
 //   a1..a5 = relu(conv(a_{i-1}) + b_i)              32 channels
-//   d = conv(a5) + b6                               1 channel (padded to 16), level-3 px
+//   d = conv(a5) + b6                               1 channel (padded to 16), one per pixel
 // Activations are NHWC bf16 (channels innermost).
 //
 // Every convolution is an implicit GEMM (bf16 in, f32 accumulate): rows =
@@ -443,9 +445,12 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(
 // MMA whose A operand (4 KB) is read afresh from no-swizzle shared memory
 // takes about 68 cycles whether N is 32 or 64, so with 32 output channels
 // the tensor pipe runs at about a quarter of its dense rate.
-// Every wait is bounded by the global timer: on a timeout the block records
-// it in the network's fault word, waits (bounded) for its own copies and
-// MMAs in flight, frees its tensor memory and returns.
+// Every wait is bounded by the global timer (200 ms on an mbarrier, 1 s at a
+// grid barrier): on a timeout the block records it in the network's fault
+// word, waits (bounded) for its own copies and MMAs in flight, writes NaN
+// over its bands of the map, frees its tensor memory and returns; the other
+// blocks then time out at the next grid barrier, if there is one, and do
+// the same.
 constexpr int kPad = 4;                // frame border = the largest dilation
 constexpr int kBandCols = 256;         // tensor-memory columns per accumulator (two)
 constexpr int kBandSmem = 224 * 1024;  // dynamic shared memory per block (one per SM)
@@ -800,7 +805,20 @@ __global__ void __launch_bounds__(kBandThreads, 1) net_forward_kernel(const Band
   }
   if (ok) ok = grid_barrier(net.sync, ++passed * gridDim.x);
   if (ok) ok = band_layer<32, 16, kFwdLinearF32>(net, net.layer[5], sh, sbias, kg);
-  if (!ok && tid == 0) atomicOr(net.fault, 1);
+  if (!ok) {
+    // a wait ran out (ok is uniform over the block): record it, and mark this
+    // block's bands of the map as missing (NaN), whatever was written there
+    if (tid == 0) atomicOr(net.fault, 1);
+    const BandLayer &ly = net.layer[5];
+    const int H = net.H, W = net.W, nb = (H + ly.BH - 1) / ly.BH;
+    const long long units = (long long)net.count * nb;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+      const int b = (int)(u / nb), j = (int)(u - (long long)b * nb);
+      const int n = min(ly.BH, H - j * ly.BH) * W;
+      float *o = reinterpret_cast<float *>(ly.out) + ((long long)b * H + j * ly.BH) * W;
+      for (int i = tid; i < n; i += kBandThreads) o[i] = __int_as_float(0x7fc00000);
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -1108,7 +1126,7 @@ int g_sms = 0;
 int g_net_tc = 1;
 
 // Dynamic shared memory of the tcgen05 kernel is exactly its slab and the
-// weights (19 to 72 KB for 80-pixel-wide level-3 inputs), so up to four
+// weights (19 to 72 KB for 80-pixel-wide inputs), so up to four
 // blocks share an SM: some stage their slab while others multiply. (Double-
 // buffering the slab within a block measured slower: it halves the blocks per
 // SM.) Images too wide for one slab (over ~200 KB) take the mma.sync kernel.

@@ -5,13 +5,15 @@
 
 Each step draws a batch of seeded surgical-like 640x480 pairs on the device
 (synth.stereo_torch), builds their pyramid with the library's kernels, and
-takes one Adam step of the network on level 3. The labels come from the
-generator and the plain method: the ground-truth disparity at level 3 (every
-8th pixel, divided by 8) where it exists, and where it does not (pixels
-occluded in the right view) the plain method's own level-3 map, searched
-from level 4 down with the paper's settings by the same kernels
-(`--labels gt` keeps the ground truth alone). The forward pass, backward
-pass and optimiser all run in libbdis.so.
+takes one Adam step of the network on the proposal level (the level the
+learned start runs it on, `proposal_level(coarsest_scale)`: level 4 at the
+paper's 5 scales). The labels come from the generator and the plain method:
+the ground-truth disparity at that level (every 2^l-th pixel, divided by
+2^l) where it exists, and where it does not (pixels occluded in the right
+view) the plain method's own map of that level, searched from the coarsest
+level down with the paper's settings by the same kernels (`--labels gt`
+keeps the ground truth alone). The forward pass, backward pass and optimiser
+all run in libbdis.so.
 """
 from __future__ import annotations
 
@@ -35,15 +37,15 @@ DEFAULT_OUT = os.path.join(HERE, "weights", "proposal.bdisnet")
 TRAIN_SEED = 7_000_000  # disjoint from the evaluation seeds (2106_07136 + ...)
 
 
-def level3(L, R):
+def level_planes(L, R, level):
     Lp, Rp, _ = bd.prepare_level0(L, R)
-    for _ in range(3):
+    for _ in range(level):
         Lp, Rp, _ = bd.pyramid_level(Lp, Rp)
     return Lp, Rp
 
 
-def plain_level3(L, R, params):
-    """The plain method's dense map at level 3 (coarse to fine from the
+def plain_level(L, R, params, level):
+    """The plain method's dense map at `level` (coarse to fine from the
     coarsest level), with every pixel estimated or carried (not the finest
     level), by the library's step kernels."""
     Lp, Rp, Gp = bd.prepare_level0(L, R)
@@ -52,7 +54,7 @@ def plain_level3(L, R, params):
         Lp, Rp, Gp = bd.pyramid_level(Lp, Rp)
         planes[lvl] = (Lp, Rp, Gp)
     coarse = None
-    for lvl in range(params.coarsest_scale, 2, -1):
+    for lvl in range(params.coarsest_scale, level - 1, -1):
         Lp, Rp, Gp = planes[lvl]
         s = bd.search_level(Lp, Rp, Gp, coarse, params, debug=False)
         coarse = bd.densify_level(tuple(Lp.shape[1:]), params, s["d_star"], s["weight"], coarse,
@@ -67,19 +69,21 @@ def train(pairs=50000, batch=64, lr=2e-3, lr_end=1e-4, seed=0, log_every=100, de
     gen = TorchCfg2Generator(device=device)
     net = bd.ProposalNet(bd.net_init_weights(seed=seed))
     params = bd.default_params()
+    level = bd.proposal_level(params.coarsest_scale)
+    f = 1 << level
     per_epoch = max(1, pairs // batch)
     steps = per_epoch * max(1, epochs)
     hist = []
     t0 = time.perf_counter()
     for s in range(steps):
         L, R, gt = gen.batch(TRAIN_SEED + s % per_epoch, batch)
-        L3, R3 = level3(L, R)
-        label = (gt[:, ::8, ::8] / 8.0).contiguous()
+        Ll, Rl = level_planes(L, R, level)
+        label = (gt[:, ::f, ::f] / float(f)).contiguous()
         if labels == "gt+plain":
-            label = torch.where(torch.isfinite(label), label, plain_level3(L, R, params))
-        f = s / max(steps - 1, 1)
-        rate = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * f))
-        loss = net.train_step(L3, R3, label, rate)
+            label = torch.where(torch.isfinite(label), label, plain_level(L, R, params, level))
+        frac = s / max(steps - 1, 1)
+        rate = lr_end + 0.5 * (lr - lr_end) * (1 + math.cos(math.pi * frac))
+        loss = net.train_step(Ll, Rl, label, rate)
         hist.append(loss)
         if log_every and (s % log_every == 0 or s == steps - 1):
             print(f"step {s:5d}/{steps} loss {loss:.4f} lr {rate:.2e} "
@@ -100,8 +104,9 @@ def main():
     a = ap.parse_args()
     w, hist, secs = train(a.pairs, a.batch, a.lr, epochs=a.epochs, labels=a.labels)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-    what = ("level-3 ground truth, the plain method's level-3 map where the ground truth has "
-            "none" if a.labels == "gt+plain" else "level-3 ground truth")
+    lv = bd.proposal_level(bd.default_params().coarsest_scale)
+    what = (f"level-{lv} ground truth, the plain method's level-{lv} map where the ground truth "
+            "has none" if a.labels == "gt+plain" else f"level-{lv} ground truth")
     note = (f"trained on {a.pairs} seeded 640x480 surgical-like pairs (seeds from {TRAIN_SEED}), "
             f"{a.epochs} epoch(s), batch {a.batch}, Adam lr {a.lr} cosine to 1e-4, Huber loss on "
             f"{what}; final loss {hist[-1]:.4f}, {secs:.1f}s")

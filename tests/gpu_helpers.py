@@ -109,7 +109,8 @@ def gpu_stages(left, right, gp, prev=None, seed=None, seed_level=0, fallback=Fal
     plane), G; the coarse map the level started from; the map its uncovered
     pixels carry; the search outputs with the debug ones; the dense map. A
     start from prev (R15), a seed map (R16, with or without the fallback
-    search) or the proposal network `net` (on level 3) seeds the coarsest
+    search) or the proposal network `net` (on level bd.proposal_level(top))
+    seeds the coarsest
     level. variants: {level: columns per lane} (the search lane layout of each
     level; None = the process-wide choice). Returns (levels, final map)."""
     import paper_2106_07136_gb300 as bd
@@ -127,10 +128,10 @@ def gpu_stages(left, right, gp, prev=None, seed=None, seed_level=0, fallback=Fal
         coarse = bd.warm_map(dev(seed), top + 1 - seed_level)
     levels = {}
     if net is not None:
-        seed_level = min(3, top)
+        seed_level = bd.proposal_level(top)
         Ln, Rn, _ = planes[seed_level]
         prop = net.forward(Ln, Rn)
-        levels["proposal"] = host(prop)[0]  # the network's level-3 map (not a level)
+        levels["proposal"] = host(prop)[0]  # the network's map (not a level of the method)
         coarse = bd.warm_map(prop, top + 1 - seed_level)
     seeded = seed is not None or net is not None
     old = bd.get_search_variant()
@@ -193,7 +194,8 @@ def assert_explained(orc, out, left, right, gp, op, label="", budget=True, prev=
     assert same_map(np.asarray(out), g_out), (label, "entry point and step entry points differ")
     o_seed = seed
     if net is not None:
-        o_seed, seed_level = levels["proposal"], min(3, gp.coarsest_scale)
+        import paper_2106_07136_gb300 as bd
+        o_seed, seed_level = levels["proposal"], bd.proposal_level(gp.coarsest_scale)
     o_st = orc.match_stages(left, right, op, prev=prev, seed=o_seed, seed_level=seed_level,
                             fallback=fallback)
     rep = at.explain_e2e(orc, op, o_st, levels, g_out, label)

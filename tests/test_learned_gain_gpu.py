@@ -31,6 +31,8 @@ def test_weights_file_is_valid():
     w, note = bd.load_net_weights(WEIGHTS)
     assert w.size == bd.net_weight_count() and np.all(np.isfinite(w))
     assert "50000" in note
+    level = bd.proposal_level(bd.default_params().coarsest_scale)
+    assert f"level-{level} ground truth" in note  # trained on the level it runs on
 
 
 def test_learned_start_gains_over_plain(held_out):

@@ -59,12 +59,13 @@ def test_learned_start_equals_seeding_with_the_net_output(orc, pair, matcher):
     gp, op = bd.default_params(**CFG2), orc.OracleParams.make(**CFG2)
     net = bd.ProposalNet(bd.net_init_weights(seed=11))
     L, R = dev(pair.left, torch.uint8), dev(pair.right, torch.uint8)
+    level = bd.proposal_level(gp.coarsest_scale)
     Lp, Rp, _ = bd.prepare_level0(L, R)
-    for _ in range(3):
+    for _ in range(level):
         Lp, Rp, _ = bd.pyramid_level(Lp, Rp)
     prop = net.forward(Lp, Rp)
     a = host(matcher.match_learned(net, L, R, gp, fallback=True))
-    b = host(matcher.match_seeded(L, R, prop, 3, gp, fallback=True))
+    b = host(matcher.match_seeded(L, R, prop, level, gp, fallback=True))
     assert np.array_equal(np.isnan(a), np.isnan(b)) and np.array_equal(a[np.isfinite(a)],
                                                                        b[np.isfinite(b)])
     assert_explained(orc, a, pair.left, pair.right, gp, op,
