@@ -75,7 +75,7 @@ def loss_and_grad(L, R, label, w):
     e = torch.where(valid, out - torch.nan_to_num(lab), torch.zeros_like(out))
     loss = torch.where(valid, huber(e), torch.zeros_like(e)).sum() / out.numel()
     loss.backward()
-    return float(loss), wt.grad.numpy().copy()
+    return float(loss.detach()), wt.grad.numpy().copy()
 
 
 def unpack_tensor(wt):
