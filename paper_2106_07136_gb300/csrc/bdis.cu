@@ -18,6 +18,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bdis_internal.cuh"
 
 struct bdis_handle {
@@ -222,11 +224,44 @@ cudaEvent_t take_event(bdis_handle *h) {
 }
 
 // Bracket one launch with events when timing is on.
+// NVTX range over one host scope (a launch, a whole-method call): names are
+// string literals or the per-class, per-level table below.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
+
+// "bdis <class> L<level>" per kernel class and pyramid level, "bdis <class>"
+// without a level; built once (a function-local static).
+const char *range_name(int cls, int level) {
+  struct Table {
+    char s[8][17][40];
+    Table() {
+      static const char *kClass[8] = {"prepare_level0", "pyramid", "search", "densify",
+                                      "upsample", "seed_map", "proposal_net", "select_start"};
+      for (int c = 0; c < 8; ++c)
+        for (int l = 0; l < 17; ++l) {
+          if (l < 16)
+            snprintf(s[c][l], sizeof s[c][l], "bdis %s L%d", kClass[c], l);
+          else
+            snprintf(s[c][l], sizeof s[c][l], "bdis %s", kClass[c]);
+        }
+    }
+  };
+  static const Table t;
+  if (cls < 0 || cls >= 8) return "bdis";
+  return t.s[cls][level >= 0 && level < 16 ? level : 16];
+}
+
 struct Timed {
   bdis_handle *h;
   cudaEvent_t a = nullptr, b = nullptr;
   int cls;
-  Timed(bdis_handle *h_, int cls_) : h(h_), cls(cls_) {
+  Range range;
+  Timed(bdis_handle *h_, int cls_, int level = -1)
+      : h(h_), cls(cls_), range(range_name(cls_, level)) {
     if (h->timing) {
       a = take_event(h);
       b = take_event(h);
@@ -299,6 +334,9 @@ DensifyArgs level_densify_args(char *base, const Layout &lay, const bdis_params 
 bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &right,
                       const bdis_params &p, float *out, const Layout &lay,
                       const Tuning *tune = nullptr, const Seed *seed = nullptr) {
+  Range whole(seed && seed->net ? "bdis match (learned start)"
+               : seed && seed->map ? "bdis match (seeded start)"
+                                   : "bdis match");
   char *base = static_cast<char *>(h->ws);
   auto F = [&](size_t off) { return reinterpret_cast<float *>(base + off); };
   auto F2 = [&](size_t off) { return reinterpret_cast<float2 *>(base + off); };
@@ -318,7 +356,7 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
   // level 0 and (pyramid variant 2) the first pyramid step in the same launch
   const bool fuse0 = pyramid_fused() == 2 && p.coarsest_scale >= 1;
   {
-    Timed tm(h, 0);
+    Timed tm(h, 0, 0);
     e = fuse0 ? launch_prepare_pyramid0(left, right, F(lay.L[0]), F2(lay.R[0]), F(lay.G[0]),
                                         F(lay.L[1]), F2(lay.R[1]), F(lay.G[1]), st)
               : launch_prepare_level0(left, right, F(lay.L[0]), F2(lay.R[0]), F(lay.G[0]), st);
@@ -326,7 +364,7 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
   if (e != cudaSuccess) return record_cuda(e);
   for (int l = fuse0 ? 1 : 0; l < p.coarsest_scale; ++l) {
     {
-      Timed tm(h, 1);
+      Timed tm(h, 1, l + 1);
       e = launch_pyramid_level(F(lay.L[l]), F2(lay.R[l]), lay.lw[l], lay.lh[l], count,
                                F(lay.L[l + 1]), F2(lay.R[l + 1]), F(lay.G[l + 1]), st);
     }
@@ -336,7 +374,7 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
     // the proposal network on the level planes just built, then its seed map
     const int nl = seed->level;
     {
-      Timed tm(h, 6);
+      Timed tm(h, 6, nl);
       bdis_status s = net_forward_on(seed->net, F(lay.L[nl]), F(lay.R[nl]), 2, lay.lw[nl],
                                      lay.lh[nl], count, F(lay.prop), st);
       if (s != BDIS_OK) return s;
@@ -355,7 +393,7 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
       sa.flags = reinterpret_cast<uint8_t *>(base + lay.flags1);
     }
     {
-      Timed tm(h, 2);
+      Timed tm(h, 2, l);
       e = launch_search(sa, st);
     }
     if (e != cudaSuccess) return record_cuda(e);
@@ -368,11 +406,11 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
       sb.posterior = F(lay.post2);
       sb.flags = reinterpret_cast<uint8_t *>(base + lay.flags2);
       {
-        Timed tm(h, 2);
+        Timed tm(h, 2, l);
         e = launch_search(sb, st);
       }
       if (e != cudaSuccess) return record_cuda(e);
-      Timed tm(h, 7);
+      Timed tm(h, 7, l);
       e = launch_select_start(sa.d_star, sa.weight, sa.posterior, sa.flags, sb.d_star, sb.weight,
                               sb.posterior, sb.flags, sa.total, st);
       if (e != cudaSuccess) return record_cuda(e);
@@ -381,7 +419,7 @@ bdis_status run_match(bdis_handle *h, const bdis_image &left, const bdis_image &
     DensifyArgs da = level_densify_args(base, lay, p, count, l, out, seeded && !two);
     if (tune) apply_tuning(da, tune->level[l]);
     {
-      Timed tm(h, 3);
+      Timed tm(h, 3, l);
       e = launch_densify(da, st);
     }
     if (e != cudaSuccess) return record_cuda(e);
