@@ -1215,9 +1215,20 @@ bool forward_pp(bdis_net *n, const float *L3, const float *R3, int r_stride, int
   bh[0] = band_rows<16, 32>(kDil[0], H, W, &nsb[0]);
   for (int l = 1; l < 5; ++l) bh[l] = band_rows<32, 32>(kDil[l], H, W, &nsb[l]);
   bh[5] = band_rows<32, 16>(kDil[5], H, W, &nsb[5]);
+  // Small batches: bands of fewer rows, so that a layer's bands spread over
+  // the SMs (a single 40x30 image would otherwise be two bands on two SMs,
+  // the rest waiting at the grid barriers). A proposal does not depend on
+  // the band height: each position's MMAs and epilogue are the same.
+  const int per_image = (g_sms + count - 1) / count;  // bands wanted per image
+  const int want = std::max(1, (H + per_image - 1) / per_image);
   int slab = 0;
   for (int l = 0; l < 6; ++l) {
     if (!bh[l]) return false;
+    if (want < bh[l]) {
+      const int Wp = W + 2 * kPad, soff = kDil[l] * Wp + kDil[l];
+      bh[l] = want;
+      nsb[l] = (want * Wp + 127) / 128 * 128 + 2 * soff;
+    }
     slab = std::max(slab, (kCinP[l] / 8) * nsb[l] * 16);
   }
   const int smem = 2 * slab + kBandWeightsMax;

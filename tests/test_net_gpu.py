@@ -81,6 +81,11 @@ def test_forward_on_tcgen05_matches_mma_and_oracle(data, reps):
         assert rel(out, outs[0]) < 1e-2, (v, rel(out, outs[0]))
     for k in range(1, reps):  # banded: a repeated image gives the same proposal wherever it sits
         assert np.array_equal(outs[1][3 * k:3 * k + 3], outs[1][:3]), k
+    # small batches run in bands of fewer rows (spread over the SMs): the
+    # proposal is the same bit for bit
+    for n in (1, 3):
+        assert np.array_equal(host(net.forward(Lp[:n].contiguous(), Rp[:n].contiguous())),
+                              outs[1][:n]), n
     net.status()
     net.close()
 
