@@ -1215,19 +1215,24 @@ bool forward_pp(bdis_net *n, const float *L3, const float *R3, int r_stride, int
   bh[0] = band_rows<16, 32>(kDil[0], H, W, &nsb[0]);
   for (int l = 1; l < 5; ++l) bh[l] = band_rows<32, 32>(kDil[l], H, W, &nsb[l]);
   bh[5] = band_rows<32, 16>(kDil[5], H, W, &nsb[5]);
-  // Small batches: bands of fewer rows, so that a layer's bands spread over
-  // the SMs (a single 40x30 image would otherwise be two bands on two SMs,
-  // the rest waiting at the grid barriers). A proposal does not depend on
-  // the band height: each position's MMAs and epilogue are the same.
+  // Band heights. Small batches: bands of fewer rows, so that a layer's
+  // bands spread over the SMs (a single 40x30 image would otherwise be two
+  // bands on two SMs, the rest waiting at the grid barriers). Then the bands
+  // of an image are made equal (30 rows: 15 + 15, not 21 + 9): blocks take
+  // bands round robin, and unequal bands would give every other block all
+  // the tall ones. A proposal does not depend on the band height: each
+  // position's MMAs and epilogue are the same.
   const int per_image = (g_sms + count - 1) / count;  // bands wanted per image
   const int want = std::max(1, (H + per_image - 1) / per_image);
   int slab = 0;
   for (int l = 0; l < 6; ++l) {
     if (!bh[l]) return false;
-    if (want < bh[l]) {
+    const int nb = (H + std::min(want, bh[l]) - 1) / std::min(want, bh[l]);
+    const int even = (H + nb - 1) / nb;  // <= bh[l]: the limits still hold
+    if (even < bh[l]) {
       const int Wp = W + 2 * kPad, soff = kDil[l] * Wp + kDil[l];
-      bh[l] = want;
-      nsb[l] = (want * Wp + 127) / 128 * 128 + 2 * soff;
+      bh[l] = even;
+      nsb[l] = (even * Wp + 127) / 128 * 128 + 2 * soff;
     }
     slab = std::max(slab, (kCinP[l] / 8) * nsb[l] * 16);
   }

@@ -85,6 +85,13 @@ def test_status_strings_and_version():
     assert lib.bdis_version() >> 16 == 1
 
 
+def test_proposal_level():
+    """The learned start's network runs on the coarsest level, at most level
+    4 (the level its weights are trained on); a host-only call."""
+    assert [bd.proposal_level(c) for c in (0, 1, 2, 3, 4, 5, 6)] == [0, 1, 2, 3, 4, 4, 4]
+    assert bd.proposal_level(-1) == -1
+
+
 @pytest.mark.skipif(torch.cuda.is_available(), reason="checks the no-GPU error path")
 def test_create_without_gpu_reports_cuda_error():
     lib = _lib.load()
