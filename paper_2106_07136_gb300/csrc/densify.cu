@@ -165,14 +165,21 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
   const int jr0 = max(0, g0 - M + 1), jr1 = min(gend, a.ny - 2);
   const int NC = max(0, ic1 - ic0 + 1), NR = max(0, jr1 - jr0 + 1);
   {
-    for (int q = threadIdx.x; q < (NR + 1) * (NC + 1); q += blockDim.x) {
-      const int rr = q / (NC + 1), cc = q - rr * (NC + 1);
-      const int j = rr < NR ? jr0 + rr : a.ny - 1, i = cc < NC ? ic0 + cc : a.nx - 1;
-      const long long o = (long long)j * a.nx + i;
-      const unsigned dw = (unsigned)__cvta_generic_to_shared(&sw[rr][cc]);
-      const unsigned dd = (unsigned)__cvta_generic_to_shared(&sd[rr][cc]);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dw), "l"(wp + o));
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dd), "l"(dp + o));
+    // thread cc copies column cc of every tile row (NC + 1 <= NCMAX < 128
+    // columns): no per-element division, one column index per thread
+    static_assert(NCMAX <= 128, "one tile column per thread");
+    const int cc = threadIdx.x;
+    if (cc <= NC) {
+      const int i = cc < NC ? ic0 + cc : a.nx - 1;
+      const unsigned dw0 = (unsigned)__cvta_generic_to_shared(&sw[0][cc]);
+      const unsigned dd0 = (unsigned)__cvta_generic_to_shared(&sd[0][cc]);
+      for (int rr = 0; rr <= NR; ++rr) {
+        const int j = rr < NR ? jr0 + rr : a.ny - 1;
+        const long long o = (long long)j * a.nx + i;
+        const unsigned step = (unsigned)(rr * NCMAX * sizeof(float));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dw0 + step), "l"(wp + o));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dd0 + step), "l"(dp + o));
+      }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
