@@ -458,6 +458,25 @@ void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_param
   a.fusion = p.fusion;
 }
 
+// SMs of the current device (looked up once per device).
+static int densify_sms() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
   if (a.fusion == BDIS_FUSION_DIS) {
@@ -467,19 +486,34 @@ cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
   }
   const int count = (int)(a.total / a.plane);
   if (a.tile_y == 0 && a.nx > 0 && a.ny > 0) {  // default: strips where the geometry allows
-    constexpr int K = 32;
-    const dim3 sg((unsigned)((a.w + 127) / 128), (unsigned)((a.h + K - 1) / K), (unsigned)count);
+    // A thread walks its column down a strip of K rows, one dependent step
+    // per group of S rows, so a launch takes at least one strip's walk. Where
+    // strips of 32 rows would not give every SM two blocks (small levels,
+    // small batches), strips of 8 (9) rows spread the same rows over four
+    // times the blocks. The map is the same either way: each row's
+    // x-weighted sums depend only on the row and the column.
+    const unsigned bx = (unsigned)((a.w + 127) / 128);
+    const bool short_strips = (long long)bx * ((a.h + 31) / 32) * count < 2LL * densify_sms();
+    auto rows = [&](int K) { return dim3(bx, (unsigned)((a.h + K - 1) / K), (unsigned)count); };
     if (a.ps == 8 && a.stride == 2) {
-      densify_strip_kernel<8, 2, K><<<sg, 128, 0, st>>>(a);
+      if (short_strips)
+        densify_strip_kernel<8, 2, 8><<<rows(8), 128, 0, st>>>(a);
+      else
+        densify_strip_kernel<8, 2, 32><<<rows(32), 128, 0, st>>>(a);
       return cudaGetLastError();
     }
     if (a.ps == 12 && a.stride == 3) {
-      densify_strip_kernel<12, 3, K - 2><<<dim3(sg.x, (unsigned)((a.h + K - 3) / (K - 2)), sg.z),
-                                            128, 0, st>>>(a);
+      if (short_strips)
+        densify_strip_kernel<12, 3, 9><<<rows(9), 128, 0, st>>>(a);
+      else
+        densify_strip_kernel<12, 3, 30><<<rows(30), 128, 0, st>>>(a);
       return cudaGetLastError();
     }
     if (a.ps == 16 && a.stride == 4) {
-      densify_strip_kernel<16, 4, K><<<sg, 128, 0, st>>>(a);
+      if (short_strips)
+        densify_strip_kernel<16, 4, 8><<<rows(8), 128, 0, st>>>(a);
+      else
+        densify_strip_kernel<16, 4, 32><<<rows(32), 128, 0, st>>>(a);
       return cudaGetLastError();
     }
   }
