@@ -631,6 +631,23 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
                      "d2h": 4 * B * W * H / ev[2].elapsed_time(ev[3]) / 1e6})
     res["e2e"]["link_gbs"] = link[0]
     res["e2e"]["link_gbs_by_set"] = link
+    # the same copies on a side stream while a match runs on the handle's
+    # stream (as in the streamed form): where the streamed rate falls below
+    # the device-resident one, this shows whether the copies slowed down
+    side = torch.cuda.Stream(device)
+    m.match(left, right, params)  # a 512-pair match takes ~13 ms: the copies fit beside it
+    with torch.cuda.stream(side):
+        ev[0].record(side)
+        dev_in[0].copy_(sets[0][0], non_blocking=True)
+        dev_in[1].copy_(sets[0][1], non_blocking=True)
+        ev[1].record(side)
+        ev[2].record(side)
+        sets[0][2].copy_(dev_out, non_blocking=True)
+        ev[3].record(side)
+    torch.cuda.synchronize(device)
+    res["e2e"]["link_gbs_beside_match"] = {
+        "h2d": 2 * B * W * H / ev[0].elapsed_time(ev[1]) / 1e6,
+        "d2h": 4 * B * W * H / ev[2].elapsed_time(ev[3]) / 1e6}
     del dev_in, dev_out
     # single-pair latency (device-resident inputs, host wall clock incl. sync)
     l1, r1 = left[0], right[0]

@@ -55,6 +55,21 @@ def test_rejected_proposal_gives_the_plain_result(pair, matcher):
     assert np.array_equal(out[np.isfinite(out)], plain[np.isfinite(plain)])
 
 
+def test_missing_proposal_gives_the_plain_result(pair, matcher):
+    """A proposal that is NaN everywhere (what the network's timeout path
+    leaves in its bands) is missing, not wrong: the seed map is 0 there, the
+    coarsest level starts as the plain method does, and the result is
+    exactly the plain one, with or without the fallback search."""
+    gp = bd.default_params(**CFG2)
+    L, R = dev(pair.left, torch.uint8), dev(pair.right, torch.uint8)
+    plain = host(matcher.match(L, R, gp))
+    seed = torch.full((1, 60, 80), float("nan"), device="cuda")
+    for fallback in (False, True):
+        out = host(matcher.match_seeded(L, R, seed, 3, gp, fallback=fallback))
+        assert np.array_equal(np.isnan(out), np.isnan(plain)), fallback
+        assert np.array_equal(out[np.isfinite(out)], plain[np.isfinite(plain)]), fallback
+
+
 def test_learned_start_equals_seeding_with_the_net_output(orc, pair, matcher):
     gp, op = bd.default_params(**CFG2), orc.OracleParams.make(**CFG2)
     net = bd.ProposalNet(bd.net_init_weights(seed=11))
