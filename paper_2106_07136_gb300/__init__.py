@@ -34,6 +34,8 @@ from .api import (  # noqa: F401
     get_pyramid_variant,
     set_net_variant,
     get_net_variant,
+    set_launch_overlap,
+    get_launch_overlap,
     prepare_level0,
     pyramid_level,
     search_level,

@@ -30,7 +30,7 @@ EXPORTED = [
     "bdis_net_train_step", "bdis_net_get_weights", "bdis_net_destroy", "bdis_match_seeded",
     "bdis_match_learned", "bdis_select_start", "bdis_host_wait_timeout",
     "bdis_inject_alloc_failures", "bdis_net_status", "bdis_net_inject_timeout",
-    "bdis_proposal_level",
+    "bdis_proposal_level", "bdis_set_launch_overlap", "bdis_get_launch_overlap",
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
@@ -171,6 +171,9 @@ def load():
     lib.bdis_set_pyramid_variant.argtypes = [c_int]
     lib.bdis_set_pyramid_variant.restype = None
     lib.bdis_get_pyramid_variant.restype = c_int
+    lib.bdis_set_launch_overlap.argtypes = [c_int]
+    lib.bdis_set_launch_overlap.restype = None
+    lib.bdis_get_launch_overlap.restype = c_int
     lib.bdis_set_net_variant.argtypes = [c_int]
     lib.bdis_set_net_variant.restype = None
     lib.bdis_get_net_variant.restype = c_int

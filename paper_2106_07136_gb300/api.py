@@ -324,6 +324,16 @@ def get_pyramid_variant() -> int:
     return int(_lib.load().bdis_get_pyramid_variant())
 
 
+def set_launch_overlap(on: bool):
+    """Launch the default pyramid, search and densify kernels as programmatic
+    dependents of the kernel before them (default on); results are identical."""
+    _lib.load().bdis_set_launch_overlap(int(bool(on)))
+
+
+def get_launch_overlap() -> bool:
+    return bool(_lib.load().bdis_get_launch_overlap())
+
+
 def set_net_variant(tensor_path: int):
     """Proposal network forward convolutions: 1 = banded tcgen05 kernel (default),
     2 = per-tile tcgen05 kernel, 0 = mma.sync kernel."""

@@ -739,6 +739,10 @@ void bdis_set_pyramid_variant(int variant) { set_pyramid_fused(variant); }
 
 int bdis_get_pyramid_variant(void) { return pyramid_fused(); }
 
+void bdis_set_launch_overlap(int on) { set_launch_overlap(on); }
+
+int bdis_get_launch_overlap(void) { return launch_overlap(); }
+
 bdis_status bdis_enable_timing(bdis_handle *h, int on) {
   if (!h) return BDIS_E_INVALID_ARG;
   h->timing = on != 0;

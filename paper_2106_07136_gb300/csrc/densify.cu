@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
   static_assert((126 + PS) / S + 1 + 1 <= NCMAX && K / S + M - 1 + 1 <= NRMAX, "tile bounds");
   __shared__ float sw[NRMAX][NCMAX], sd[NRMAX][NCMAX];
   __shared__ float smask[PS];
+  pdl_enter();
   const int X0 = blockIdx.x * 128, x = X0 + (int)threadIdx.x;
   const int Y0 = blockIdx.y * K, b = blockIdx.z;
   const bool active = x < a.w;
@@ -458,25 +459,6 @@ void fill_densify_args(DensifyArgs &a, int w, int h, int count, const bdis_param
   a.fusion = p.fusion;
 }
 
-// SMs of the current device (looked up once per device).
-static int densify_sms() {
-  static int cache[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    cudaGetLastError();
-    return 152;
-  }
-  if (!cache[dev]) {
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      n = 152;
-    }
-    cache[dev] = n;
-  }
-  return cache[dev];
-}
-
 cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
   if (a.total == 0) return cudaSuccess;
   if (a.fusion == BDIS_FUSION_DIS) {
@@ -493,29 +475,23 @@ cudaError_t launch_densify(const DensifyArgs &a, cudaStream_t st) {
     // times the blocks. The map is the same either way: each row's
     // x-weighted sums depend only on the row and the column.
     const unsigned bx = (unsigned)((a.w + 127) / 128);
-    const bool short_strips = (long long)bx * ((a.h + 31) / 32) * count < 2LL * densify_sms();
+    const bool short_strips = (long long)bx * ((a.h + 31) / 32) * count < 2LL * device_sms();
     auto rows = [&](int K) { return dim3(bx, (unsigned)((a.h + K - 1) / K), (unsigned)count); };
-    if (a.ps == 8 && a.stride == 2) {
-      if (short_strips)
-        densify_strip_kernel<8, 2, 8><<<rows(8), 128, 0, st>>>(a);
-      else
-        densify_strip_kernel<8, 2, 32><<<rows(32), 128, 0, st>>>(a);
-      return cudaGetLastError();
-    }
-    if (a.ps == 12 && a.stride == 3) {
-      if (short_strips)
-        densify_strip_kernel<12, 3, 9><<<rows(9), 128, 0, st>>>(a);
-      else
-        densify_strip_kernel<12, 3, 30><<<rows(30), 128, 0, st>>>(a);
-      return cudaGetLastError();
-    }
-    if (a.ps == 16 && a.stride == 4) {
-      if (short_strips)
-        densify_strip_kernel<16, 4, 8><<<rows(8), 128, 0, st>>>(a);
-      else
-        densify_strip_kernel<16, 4, 32><<<rows(32), 128, 0, st>>>(a);
-      return cudaGetLastError();
-    }
+    if (a.ps == 8 && a.stride == 2)
+      return short_strips ? launch_maybe_overlapped(densify_strip_kernel<8, 2, 8>, rows(8),
+                                                    dim3(128), 0, st, a)
+                          : launch_maybe_overlapped(densify_strip_kernel<8, 2, 32>, rows(32),
+                                                    dim3(128), 0, st, a);
+    if (a.ps == 12 && a.stride == 3)
+      return short_strips ? launch_maybe_overlapped(densify_strip_kernel<12, 3, 9>, rows(9),
+                                                    dim3(128), 0, st, a)
+                          : launch_maybe_overlapped(densify_strip_kernel<12, 3, 30>, rows(30),
+                                                    dim3(128), 0, st, a);
+    if (a.ps == 16 && a.stride == 4)
+      return short_strips ? launch_maybe_overlapped(densify_strip_kernel<16, 4, 8>, rows(8),
+                                                    dim3(128), 0, st, a)
+                          : launch_maybe_overlapped(densify_strip_kernel<16, 4, 32>, rows(32),
+                                                    dim3(128), 0, st, a);
   }
   const int tile_y = a.tile_y > 0 ? a.tile_y : kTileY;
   const dim3 grid((unsigned)((a.w + kTileX - 1) / kTileX), (unsigned)((a.h + tile_y - 1) / tile_y),

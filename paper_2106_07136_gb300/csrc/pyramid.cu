@@ -257,6 +257,7 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
   __shared__ float2 inLR[kStY][kStP];
   __shared__ float2 hLR[kStY][kCx];
   __shared__ float2 sLR[kPyrY + 2][kCx];
+  pdl_enter();
   const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const float *Lb = L + (long long)b * w * h;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(256) prepare_pyramid0_kernel(
   __shared__ float2 inLR[kStY][kStP];
   __shared__ float2 hLR[kStY][kCx];
   __shared__ float2 sLR[kPyrY + 2][kCx];
+  pdl_enter();
   const int b = blockIdx.z, X0 = blockIdx.x * kPyrX, Y0 = blockIdx.y * kPyrY;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const char *lb = reinterpret_cast<const char *>(left) + (size_t)b * stride;
@@ -404,6 +406,28 @@ int g_pyramid_fused = 2;
 }  // namespace
 
 int pyramid_fused() { return g_pyramid_fused; }
+
+int g_launch_overlap = 1;
+int launch_overlap() { return g_launch_overlap; }
+void set_launch_overlap(int on) { g_launch_overlap = on ? 1 : 0; }
+
+int device_sms() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 152;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
 void set_pyramid_fused(int variant) { g_pyramid_fused = variant < 0 ? 0 : (variant > 2 ? 2 : variant); }
 
 cudaError_t launch_prepare_pyramid0(const bdis_image &left, const bdis_image &right, float *L0,
@@ -420,14 +444,12 @@ cudaError_t launch_prepare_pyramid0(const bdis_image &left, const bdis_image &ri
                     (reinterpret_cast<uintptr_t>(left.data) & 3) == 0 &&
                     (reinterpret_cast<uintptr_t>(right.data) & 3) == 0;
   if (left.format == BDIS_U8)
-    prepare_pyramid0_kernel<uint8_t><<<grid, 256, 0, st>>>(left.data, right.data,
-                                                           left.pitch_bytes, stride, w, h, dw,
-                                                           dh, words, L0, R0, G0, L1, R1, G1);
-  else
-    prepare_pyramid0_kernel<float><<<grid, 256, 0, st>>>(left.data, right.data, left.pitch_bytes,
-                                                         stride, w, h, dw, dh, 0, L0, R0, G0, L1,
-                                                         R1, G1);
-  return cudaGetLastError();
+    return launch_maybe_overlapped(prepare_pyramid0_kernel<uint8_t>, grid, dim3(256), 0, st,
+                                   left.data, right.data, left.pitch_bytes, stride, w, h, dw, dh,
+                                   words, L0, R0, G0, L1, R1, G1);
+  return launch_maybe_overlapped(prepare_pyramid0_kernel<float>, grid, dim3(256), 0, st,
+                                 left.data, right.data, left.pitch_bytes, stride, w, h, dw, dh, 0,
+                                 L0, R0, G0, L1, R1, G1);
 }
 
 cudaError_t launch_prepare_level0(const bdis_image &left, const bdis_image &right, float *L0,
@@ -470,8 +492,8 @@ cudaError_t launch_pyramid_level(const float *L, const float2 *R, int w, int h, 
   if (g_pyramid_fused) {
     const dim3 grid((unsigned)((dw + kPyrX - 1) / kPyrX), (unsigned)((dh + kPyrY - 1) / kPyrY),
                     (unsigned)count);
-    pyramid_fused_kernel<<<grid, 256, 0, st>>>(L, R, w, h, dw, dh, L1, R1, G1);
-    return cudaGetLastError();
+    return launch_maybe_overlapped(pyramid_fused_kernel, grid, dim3(256), 0, st, L, R, w, h, dw,
+                                   dh, L1, R1, G1);
   }
   const int threads = 256;
   down_kernel<<<blocks_for(total, threads), threads, 0, st>>>(L, R, w, h, dw, dh, total, L1, R1);

@@ -699,6 +699,7 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
 // SH: the centred-gradient cache in shared memory (GcStore).
 template <int PS, int CPL, int MINB, bool SH>
 __global__ void __launch_bounds__(kSearchThreads, MINB) search_fixed_kernel(const SearchArgs a) {
+  pdl_enter();
   constexpr int LANES = (PS + CPL - 1) / CPL;
   constexpr int G = pow2_at_least(LANES);
   static_assert(G <= 32, "group size");
@@ -955,8 +956,8 @@ cudaError_t launch_fixed(const SearchArgs &a, cudaStream_t st) {
   const int threads = a.block_threads == 64 ? 64 : 128, per_block = threads / G;
   const int count = (int)(a.total / a.np);
   const dim3 grid((unsigned)((a.np + per_block - 1) / per_block), (unsigned)count);
-  search_fixed_kernel<PS, CPL, MINB, SH><<<grid, threads, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_maybe_overlapped(search_fixed_kernel<PS, CPL, MINB, SH>, grid, dim3(threads), 0, st,
+                                 a);
 }
 
 template <int PS, int CPL, int MINB>

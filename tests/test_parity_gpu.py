@@ -99,6 +99,37 @@ def test_fused_pyramid_matches_two_pass(shape):
             assert np.array_equal(x, y)
 
 
+def test_launch_overlap_gives_the_same_maps(matcher):
+    """Launching the pyramid, search and densify kernels as programmatic
+    dependents of the kernel before them (the default) gives exactly the maps
+    of plain stream order: one pair, a batch, the learned start (its
+    cooperative network kernel between overlapped launches) and a plan (the
+    same launches captured in a CUDA graph)."""
+    gp = bd.default_params()
+    L, R, _ = synth.make_batch(2, 3)
+    Lb, Rb = dev(L, torch.uint8), dev(R, torch.uint8)
+    net = bd.ProposalNet(bd.net_init_weights(seed=4))
+    outp = torch.empty(Lb.shape, dtype=torch.float32, device="cuda")
+    plan = bd.Plan([(Lb, Rb, outp)], gp, autotune=False)
+    old = bd.get_launch_overlap()
+    res = {}
+    try:
+        for on in (True, False):
+            bd.set_launch_overlap(on)
+            plan.run()
+            torch.cuda.synchronize()
+            res[on] = [host(matcher.match(Lb[:1], Rb[:1], gp)), host(matcher.match(Lb, Rb, gp)),
+                       host(matcher.match_learned(net, Lb, Rb, gp, fallback=True)), host(outp)]
+    finally:
+        bd.set_launch_overlap(old)
+        plan.close()
+        net.close()
+    assert bd.get_launch_overlap()
+    for a, b in zip(res[True], res[False]):
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
+
+
 @pytest.mark.parametrize("shape", [(61, 97), (35, 47), (120, 160)])
 def test_level0_with_first_step_matches_separate_kernels(matcher, shape):
     """Pyramid variant 2 (level 0 and the first step from one staging of the
