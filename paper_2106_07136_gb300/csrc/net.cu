@@ -1271,8 +1271,15 @@ bool forward_pp(bdis_net *n, const float *L3, const float *R3, int r_stride, int
     cudaGetLastError();
     return false;
   }
+  // one block per SM, or one per band where a layer has fewer bands (a
+  // single image): fewer blocks meet at each grid barrier and restage the
+  // weights
+  long long units = 1;
+  for (int l = 0; l < 6; ++l)
+    units = std::max(units, (long long)count * ((H + bh[l] - 1) / bh[l]));
+  const unsigned grid = (unsigned)std::min<long long>(g_sms, units);
   void *args[] = {&net};
-  if (cudaLaunchCooperativeKernel((const void *)net_forward_kernel, dim3((unsigned)g_sms),
+  if (cudaLaunchCooperativeKernel((const void *)net_forward_kernel, dim3(grid),
                                   dim3(kBandThreads), args, (size_t)smem, st) != cudaSuccess) {
     cudaGetLastError();  // not sticky: the per-tile kernels run instead
     return false;
