@@ -419,6 +419,20 @@ int bdis_get_pyramid_variant(void);
 void bdis_set_launch_overlap(int on);
 int bdis_get_launch_overlap(void);
 
+/* Bounds-checked build (libbdis_checked.so: the same sources compiled with
+ * -DBDIS_CHECKED; the substitute for a memory sanitizer). There, the
+ * kernels' data-dependent global accesses check their element index against
+ * the buffer's extent, skip an access out of bounds (a read gives 0) and
+ * record the access site. bdis_check_status waits for the device, then
+ * writes the sites caught since the last call as bits and clears them:
+ * bit 0 inverse-search samples of the right plane, 1 its template and
+ * gradient rows, 2 its per-patch outputs, 3 the densify patch tile, 4 the
+ * densify output, 5 the level-0 input views, 6 a pyramid step's input level,
+ * 7 the pyramid's output planes. In the normal build it writes 0.
+ * bdis_checked_build returns 1 in the checked build, else 0. */
+bdis_status bdis_check_status(uint32_t *sites);
+int bdis_checked_build(void);
+
 /* Measurement utility, not part of the method: FP32 FMA throughput of the
  * current device in TFLOP/s (the roofline denominator of the inverse search).
  * Runs two launches of an FMA-chain kernel of `iterations` steps per chain on

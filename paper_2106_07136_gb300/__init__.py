@@ -36,6 +36,8 @@ from .api import (  # noqa: F401
     get_net_variant,
     set_launch_overlap,
     get_launch_overlap,
+    check_status,
+    checked_build,
     prepare_level0,
     pyramid_level,
     search_level,

@@ -31,6 +31,7 @@ EXPORTED = [
     "bdis_match_learned", "bdis_select_start", "bdis_host_wait_timeout",
     "bdis_inject_alloc_failures", "bdis_net_status", "bdis_net_inject_timeout",
     "bdis_proposal_level", "bdis_set_launch_overlap", "bdis_get_launch_overlap",
+    "bdis_check_status", "bdis_checked_build",
 ]
 
 BDIS_PLAN_AUTOTUNE = 1
@@ -93,7 +94,7 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    return os.environ.get("BDIS_LIBRARY") or _build.LIB
 
 
 def load():
@@ -103,7 +104,9 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build()
+    # BDIS_LIBRARY: a prebuilt library to load instead (the bounds-checked
+    # build of the same sources, for tests)
+    path = os.environ.get("BDIS_LIBRARY") or _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"libbdis.so is missing at {path}")
     lib = ctypes.CDLL(path)
@@ -174,6 +177,8 @@ def load():
     lib.bdis_set_launch_overlap.argtypes = [c_int]
     lib.bdis_set_launch_overlap.restype = None
     lib.bdis_get_launch_overlap.restype = c_int
+    lib.bdis_check_status.argtypes = [P(ctypes.c_uint32)]
+    lib.bdis_checked_build.restype = c_int
     lib.bdis_set_net_variant.argtypes = [c_int]
     lib.bdis_set_net_variant.restype = None
     lib.bdis_get_net_variant.restype = c_int

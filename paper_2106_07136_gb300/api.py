@@ -324,6 +324,19 @@ def get_pyramid_variant() -> int:
     return int(_lib.load().bdis_get_pyramid_variant())
 
 
+def checked_build() -> bool:
+    """Whether the loaded library is the bounds-checked build."""
+    return bool(_lib.load().bdis_checked_build())
+
+
+def check_status() -> int:
+    """Bit mask of the access sites the bounds-checked build caught out of
+    bounds since the last call (0 in the normal build); waits for the device."""
+    v = ctypes.c_uint32(0)
+    check(_lib.load().bdis_check_status(ctypes.byref(v)), "bdis_check_status")
+    return int(v.value)
+
+
 def set_launch_overlap(on: bool):
     """Launch the default pyramid, search and densify kernels as programmatic
     dependents of the kernel before them (default on); results are identical."""

@@ -3,6 +3,12 @@
 Each .cu file compiles in parallel with nvcc, then one link step makes the
 shared library with the CUDA runtime linked statically, so the library loads
 (and its symbols can be listed) on machines without a GPU.
+
+build(checked=True) makes libbdis_checked.so instead: the same sources with
+-DBDIS_CHECKED, where the kernels check the index of their data-dependent
+global accesses against the buffer's extent (the substitute for a memory
+sanitizer; bdis_check_status reports what was caught). Load it by pointing
+BDIS_LIBRARY at it before the package loads.
 """
 from __future__ import annotations
 
@@ -18,6 +24,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libbdis.so")
+LIB_CHECKED = os.path.join(HERE, "libbdis_checked.so")
 BUILD_DIR = os.path.join(HERE, "_build")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -46,14 +53,18 @@ def _stale(out: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and not _stale(LIB):
-        return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    obj_dir = os.path.join(BUILD_DIR, "checked") if checked else BUILD_DIR
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
+    if checked:
+        extra_flags = (*extra_flags, "-DBDIS_CHECKED")
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(obj_dir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -71,8 +82,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if r.returncode != 0:
         os.unlink(tmp)
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

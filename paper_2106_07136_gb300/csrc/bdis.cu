@@ -739,6 +739,26 @@ void bdis_set_pyramid_variant(int variant) { set_pyramid_fused(variant); }
 
 int bdis_get_pyramid_variant(void) { return pyramid_fused(); }
 
+bdis_status bdis_check_status(uint32_t *sites) {
+  if (!sites) return BDIS_E_INVALID_ARG;
+  unsigned s = 0u, d = 0u, p = 0u;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = take_check_search(&s);
+  if (e == cudaSuccess) e = take_check_densify(&d);
+  if (e == cudaSuccess) e = take_check_pyramid(&p);
+  if (e != cudaSuccess) return record_cuda(e);
+  *sites = s | d | p;
+  return BDIS_OK;
+}
+
+int bdis_checked_build(void) {
+#ifdef BDIS_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 void bdis_set_launch_overlap(int on) { set_launch_overlap(on); }
 
 int bdis_get_launch_overlap(void) { return launch_overlap(); }

@@ -120,6 +120,7 @@ struct SearchArgs {
   // floor(k / nx) = umulhi(k, nx_mul) for every patch index k < np (0: divide)
   unsigned nx_mul;
   long long total;  // count * np
+  long long pixels; // count * plane (the extent of L, G and the packed R)
   int iters, s;
   float step, kappa;
   int nmin_valid, normalize;
@@ -196,6 +197,62 @@ int densify_tile();
 void set_densify_tile(int tile_height);
 int pyramid_fused();
 void set_pyramid_fused(int variant);
+
+// ---- Bounds-checked build (-DBDIS_CHECKED; the memory-sanitizer substitute,
+// libbdis_checked.so). There, the kernels' data-dependent global accesses
+// check their element index against the buffer's extent; an access out of
+// bounds is skipped (a read gives 0) and sets bit `site` of this translation
+// unit's check word, which bdis_check_status reads. In the normal build the
+// checks compile away. Sites:
+enum CheckSite {
+  kCheckSearchSample = 0,   // inverse search: right-plane samples (window and steps)
+  kCheckSearchRows = 1,     // inverse search: template and gradient rows
+  kCheckSearchOut = 2,      // inverse search: per-patch outputs
+  kCheckDensifyTile = 3,    // densify: staged patch tile
+  kCheckDensifyOut = 4,     // densify: dense map
+  kCheckPyramidInput = 5,   // level-0 preparation: the input views
+  kCheckPyramidStage = 6,   // pyramid step: the staged level
+  kCheckPyramidOut = 7,     // level planes written by the pyramid kernels
+};
+#ifdef BDIS_CHECKED
+static __device__ unsigned g_check_word;
+#endif
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int site) {
+#ifdef BDIS_CHECKED
+  if (i < 0 || i >= n) {
+    atomicOr(&g_check_word, 1u << site);
+    return false;
+  }
+#else
+  (void)i;
+  (void)n;
+  (void)site;
+#endif
+  return true;
+}
+// A read-only float load that the checked build bounds-checks against
+// [base, base + n).
+__device__ __forceinline__ float ld_checked(const float *p, const float *base, long long n,
+                                            int site) {
+  if (!in_bounds(p - base, n, site)) return 0.f;
+  return __ldg(p);
+}
+// Read and clear this translation unit's check word (always 0 in the normal
+// build).
+static inline cudaError_t take_check_word(unsigned *v) {
+#ifdef BDIS_CHECKED
+  cudaError_t e = cudaMemcpyFromSymbol(v, g_check_word, sizeof(unsigned));
+  const unsigned z = 0u;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_check_word, &z, sizeof(unsigned));
+  return e;
+#else
+  *v = 0u;
+  return cudaSuccess;
+#endif
+}
+cudaError_t take_check_search(unsigned *v);
+cudaError_t take_check_densify(unsigned *v);
+cudaError_t take_check_pyramid(unsigned *v);
 
 // Programmatic dependent launch of the method's default kernels (pyramid,
 // search, densify): a kernel may be scheduled while the previous kernel on

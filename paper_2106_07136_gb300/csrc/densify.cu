@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
         const int j = rr < NR ? jr0 + rr : a.ny - 1;
         const long long o = (long long)j * a.nx + i;
         const unsigned step = (unsigned)(rr * NCMAX * sizeof(float));
+        if (!in_bounds(o, a.np, kCheckDensifyTile)) continue;
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dw0 + step), "l"(wp + o));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dd0 + step), "l"(dp + o));
       }
@@ -310,7 +311,8 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
                                      y * 0.5f);
       else
         out = 0.f;
-      a.out[obase + (long long)y * a.w] = out;
+      const long long oi = obase + (long long)y * a.w;
+      if (in_bounds(oi, a.total, kCheckDensifyOut)) a.out[oi] = out;
     }
   }
 }
@@ -509,5 +511,7 @@ cudaError_t launch_upsample(const float *map, int mw, int mh, int level, int w, 
       map, mw, mh, (float)(1 << level), w, h, total, out);
   return cudaGetLastError();
 }
+
+cudaError_t take_check_densify(unsigned *v) { return take_check_word(v); }
 
 }  // namespace bdis

@@ -131,7 +131,7 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
   }
   if (nvalid < a.nmin_valid) flags |= kFlagGamma;
   const bool drop = (flags & kDropFlags) != 0;
-  if (write) {
+  if (write && in_bounds(k, a.total, kCheckSearchOut)) {
     if (a.fusion == BDIS_FUSION_DIS) {
       // DIS fuses every patch (Eq. 2); a runaway patch falls back to its start
       a.d_star[k] = (flags & kFlagDiverged) ? u0 : D;
@@ -159,7 +159,7 @@ __device__ __forceinline__ void finish_patch_dis(const SearchArgs &a, long long 
   if (!isfinite(D) || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
   if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
   if (nvalid < a.nmin_valid) flags |= kFlagGamma;
-  if (write) {
+  if (write && in_bounds(k, a.total, kCheckSearchOut)) {
     a.d_star[k] = (flags & kFlagDiverged) ? u0 : D;
     a.weight[k] = 1.f;
     if (a.u_init) a.u_init[k] = u0;
@@ -186,16 +186,35 @@ constexpr int pow2_at_least(int n) { return n <= 1 ? 1 : 2 * pow2_at_least((n + 
 struct GlobalRows {
   const float2 *row0;  // row y0 of the packed right plane
   int w;
+#ifdef BDIS_CHECKED
+  const float2 *base;  // the whole packed plane (count * plane pairs)
+  long long n;
+#endif
   __device__ __forceinline__ const float2 *col(int x) const { return row0 + x; }
   // a column that is always safe to read (for lanes whose sample is unused)
   __device__ __forceinline__ const float2 *col_clamped(int x) const {
     return row0 + min(max(x, 0), w - 1);
   }
   __device__ __forceinline__ float2 ld(const float2 *p, int r) const {
-    return __ldg(p + (size_t)r * w);
+    const float2 *q = p + (size_t)r * w;
+#ifdef BDIS_CHECKED
+    if (!in_bounds(q - base, n, kCheckSearchSample)) return make_float2(0.f, 0.f);
+#endif
+    return __ldg(q);
   }
   __device__ __forceinline__ void ready() const {}
 };
+
+__device__ __forceinline__ GlobalRows global_rows(const SearchArgs &a, const float2 *row0) {
+  GlobalRows g;
+  g.row0 = row0;
+  g.w = a.w;
+#ifdef BDIS_CHECKED
+  g.base = a.R2;
+  g.n = a.pixels;
+#endif
+  return g;
+}
 
 template <int TW>
 struct TileRows {
@@ -273,7 +292,9 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
         float ge[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e)
-          ge[e] = act[2 * jp + e] ? __ldg(Gc + (size_t)r * w + 2 * jp + e) : 0.f;
+          ge[e] = act[2 * jp + e] ? ld_checked(Gc + (size_t)r * w + 2 * jp + e, a.G, a.pixels,
+                                               kCheckSearchRows)
+                                  : 0.f;
         g2[jp][r] = make_float2(ge[0], ge[1]);
         s2 = __ffma2_rn(g2[jp][r], m2[jp], s2);  // adds g where valid, exactly
       }
@@ -294,7 +315,9 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
         float te[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e)
-          te[e] = act[2 * jp + e] ? __ldg(Lc + (size_t)r * w + 2 * jp + e) : 0.f;
+          te[e] = act[2 * jp + e] ? ld_checked(Lc + (size_t)r * w + 2 * jp + e, a.L, a.pixels,
+                                               kCheckSearchRows)
+                                  : 0.f;
         h2 = __ffma2_rn(q, q, h2);
         c2 = __ffma2_rn(q, make_float2(te[0], te[1]), c2);
       }
@@ -308,7 +331,8 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
     for (int j = 0; j < CPL; ++j)
 #pragma unroll
       for (int r = 0; r < PS; ++r) {
-        g[j][r] = v[j] ? __ldg(Gc + (size_t)r * w + j) : 0.f;
+        g[j][r] =
+            v[j] ? ld_checked(Gc + (size_t)r * w + j, a.G, a.pixels, kCheckSearchRows) : 0.f;
         sg += g[j][r];
       }
     sg = group_sum<G>(sg);
@@ -323,7 +347,10 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
         const float q = v[j] ? g[j][r] - mg : 0.f;
         if (need) st.gc.at(j, r) = q;
         hh = fmaf(q, q, hh);
-        ct = fmaf(q, act[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f, ct);
+        ct = fmaf(q,
+                  act[j] ? ld_checked(Lc + (size_t)r * w + j, a.L, a.pixels, kCheckSearchRows)
+                         : 0.f,
+                  ct);
       }
   }
   hh = group_sum<G>(hh);
@@ -447,8 +474,9 @@ __device__ __forceinline__ bool search_next_step(const SearchArgs &a, const Rows
 // outside the image or the staged tile); without it every pair is in both.
 // An invalid column's sums are finite and are multiplied by 0 in the merge.
 template <int PS, int CPL, bool GUARD, class Rows>
-__device__ __forceinline__ void window_rows_pairs(const Rows &rows, int ib, float t, float th,
-                                                  bool hi, const float *Lc, int w,
+__device__ __forceinline__ void window_rows_pairs(const SearchArgs &a, const Rows &rows, int ib,
+                                                  float t, float th, bool hi, const float *Lc,
+                                                  int w,
                                                   const bool (&act)[CPL],
                                                   const bool (&need)[CPL + 2],
                                                   const float (&cs)[CPL],
@@ -472,7 +500,10 @@ __device__ __forceinline__ void window_rows_pairs(const Rows &rows, int ib, floa
       float tn[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e)
-        tn[e] = -(act[j + e] ? __ldg(Lc + (size_t)r * w + j + e) : 0.f) - cs[j + e];
+        tn[e] = -(act[j + e] ? ld_checked(Lc + (size_t)r * w + j + e, a.L, a.pixels,
+                                          kCheckSearchRows)
+                             : 0.f) -
+                cs[j + e];
       const float2 Tn = make_float2(tn[0], tn[1]);
       // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1
       const float2 d[S] = {
@@ -574,7 +605,9 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
   float cs[CPL];
 #pragma unroll
   for (int j = 0; j < CPL; ++j)
-    cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) - __ldg(Lc + j) : 0.f;
+    cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) -
+                        ld_checked(Lc + j, a.L, a.pixels, kCheckSearchRows)
+                  : 0.f;
   // Merge per sample: s1 = sum of the residuals, md their mean, and
   // E = sum (d - md)^2 = S2 - 2 (md - cs) S1 + n (md - cs)^2 per column.
   const float inv_nc = nc > 0 ? __fdividef(1.f, (float)nc) : 0.f;
@@ -591,9 +624,9 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     // A warp whose patches are all in range (so their pairs lie in a staged
     // tile, if any) with all pairs in the image reads them unconditionally.
     if (__all_sync(kFull, inr && ib >= 1 && ib + CPL <= w - 1))
-      window_rows_pairs<PS, CPL, false>(rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
+      window_rows_pairs<PS, CPL, false>(a, rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
     else
-      window_rows_pairs<PS, CPL, true>(rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
+      window_rows_pairs<PS, CPL, true>(a, rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
     // the merge below, per column pair; an invalid column's term is x * 0
     // (every term is finite)
     const float2 kPS = make_float2((float)PS, (float)PS), kM2 = make_float2(-2.f, -2.f);
@@ -642,7 +675,9 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
       }
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
-        const float Tj = (vc[j] ? __ldg(Lc + (size_t)r * w + j) : 0.f) + cs[j];  // template + shift
+        const float Tj =  // template + shift
+            (vc[j] ? ld_checked(Lc + (size_t)r * w + j, a.L, a.pixels, kCheckSearchRows) : 0.f) +
+            cs[j];
         // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1.
         // An invalid column's sums (finite: its pairs read as 0) are not merged below.
         const float d[S] = {Lt[j + 2] - Tj, (hi ? Lh[j + 2] : Lh[j + 1]) - Tj, Lt[j + 1] - Tj,
@@ -722,7 +757,7 @@ __global__ void __launch_bounds__(kSearchThreads, MINB) search_fixed_kernel(cons
                                 cy * 0.5f);
   }
   __shared__ float sgc[SH ? CPL * PS * kSearchThreads : 1];
-  fixed_patch<PS, CPL, SH>(a, GlobalRows{a.R2 + (long long)b * a.plane + (long long)y0 * w, w},
+  fixed_patch<PS, CPL, SH>(a, global_rows(a, a.R2 + (long long)b * a.plane + (long long)y0 * w),
                            k, live, c, gbits, b, x0, y0, u0, sgc);
 }
 
@@ -799,7 +834,7 @@ __global__ void __launch_bounds__(kSearchThreads, MINB) search_tiled_kernel(cons
     }
     fixed_patch<PS, CPL>(a, TileRows<TW>{tile, lo, width}, k, live, c, gbits, b, x0, y0, u0);
   } else {
-    fixed_patch<PS, CPL>(a, GlobalRows{row0, w}, k, live, c, gbits, b, x0, y0, u0);
+    fixed_patch<PS, CPL>(a, global_rows(a, row0), k, live, c, gbits, b, x0, y0, u0);
   }
 }
 
@@ -824,7 +859,8 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
 
   float T[G];
 #pragma unroll
-  for (int r = 0; r < G; ++r) T[r] = (act && r < ps) ? __ldg(Lc + (size_t)r * w) : 0.f;
+  for (int r = 0; r < G; ++r)
+    T[r] = (act && r < ps) ? ld_checked(Lc + (size_t)r * w, a.L, a.pixels, kCheckSearchRows) : 0.f;
 
   const float u0 = pp.u0;
   float D = u0, last_step = 0.f;
@@ -848,14 +884,17 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
     if (__any_sync(kFull, need)) {
       float sg = 0.f;
 #pragma unroll
-      for (int r = 0; r < G; ++r) sg += (v && r < ps) ? __ldg(Gc + (size_t)r * w) : 0.f;
+      for (int r = 0; r < G; ++r)
+        sg += (v && r < ps) ? ld_checked(Gc + (size_t)r * w, a.G, a.pixels, kCheckSearchRows) : 0.f;
       sg = group_sum<G>(sg);
       const int nn = ps * __popc(m);
       const float mg = (a.normalize && nn > 0) ? sg / (float)nn : 0.f;
       float hh = 0.f, ct = 0.f;
 #pragma unroll
       for (int r = 0; r < G; ++r) {
-        const float q = (v && r < ps) ? __ldg(Gc + (size_t)r * w) - mg : 0.f;
+        const float q =
+            (v && r < ps) ? ld_checked(Gc + (size_t)r * w, a.G, a.pixels, kCheckSearchRows) - mg
+                          : 0.f;
         if (need) gc[r] = q;
         hh = fmaf(q, q, hh);
         ct = fmaf(q, T[r], ct);
@@ -1044,6 +1083,7 @@ void fill_search_args(SearchArgs &a, int w, int h, int count, const bdis_params 
     if ((unsigned long long)(a.np - 1) * e < (1ull << 32)) a.nx_mul = (unsigned)m;
   }
   a.total = (long long)a.np * count;
+  a.pixels = a.plane * count;
   a.iters = p.iterations;
   a.s = p.window_samples;
   a.step = p.window_step;
@@ -1077,5 +1117,7 @@ cudaError_t launch_search(const SearchArgs &args, cudaStream_t st) {
   if (a.ps <= 16) return launch_groups(search_generic_kernel<16>, 16, a, st);
   return launch_groups(search_generic_kernel<32>, 32, a, st);
 }
+
+cudaError_t take_check_search(unsigned *v) { return take_check_word(v); }
 
 }  // namespace bdis
