@@ -409,13 +409,13 @@ int bdis_get_densify_variant(void);
 void bdis_set_pyramid_variant(int variant);
 int bdis_get_pyramid_variant(void);
 
-/* Tuning: launch overlap. 1 (default): the method's default pyramid, search
- * and densify kernels, where a launch has at most 16 blocks per SM (small
- * batches, coarse levels), are launched as programmatic dependents of the
- * kernel before them on the stream, so a launch's start-up overlaps the
- * previous kernel's last blocks; each kernel still waits for the previous
- * one to finish before it touches memory. 0: plain stream order. Results
- * are identical. Process-wide. */
+/* Tuning: launch overlap. 1 (default): launches of the default pyramid,
+ * search and densify kernels and of the seed-map and seeded-start choice
+ * kernels that have at most 16 blocks per SM (small batches, coarse levels)
+ * are programmatic dependents of the kernel before them on the stream, so a
+ * launch's start-up overlaps the previous kernel's last blocks; each kernel
+ * still waits for the previous one to finish before it touches memory.
+ * 0: plain stream order. Results are identical. Process-wide. */
 void bdis_set_launch_overlap(int on);
 int bdis_get_launch_overlap(void);
 

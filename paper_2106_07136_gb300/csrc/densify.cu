@@ -402,6 +402,7 @@ __global__ void upsample_kernel(const float *__restrict__ M, int mw, int mh, flo
 // point, divided by 2^level; 0 where none is finite.
 __global__ void warm_map_kernel(const float *__restrict__ P, int w, int h, int level, int mw,
                                 int mh, long long total, float *__restrict__ out) {
+  pdl_enter();
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const long long mplane = (long long)mw * mh;
@@ -434,9 +435,8 @@ cudaError_t launch_warm_map(const float *prev, int w, int h, int level, int coun
   const long long total = (long long)mw * mh * count;
   if (total == 0) return cudaSuccess;
   const int threads = 128;
-  warm_map_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
-      prev, w, h, level, mw, mh, total, out);
-  return cudaGetLastError();
+  return launch_maybe_overlapped(warm_map_kernel, dim3((unsigned)((total + threads - 1) / threads)),
+                                 dim3(threads), 0, st, prev, w, h, level, mw, mh, total, out);
 }
 
 namespace {

@@ -1032,6 +1032,7 @@ __global__ void select_start_kernel(float *__restrict__ d_a, float *__restrict__
                                     const float *__restrict__ d_b, const float *__restrict__ w_b,
                                     const float *__restrict__ p_b, const uint8_t *__restrict__ f_b,
                                     long long total) {
+  pdl_enter();
   const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= total) return;
   const bool kept_a = !(f_a[k] & kDropFlags), kept_b = !(f_b[k] & kDropFlags);
@@ -1050,9 +1051,8 @@ cudaError_t launch_select_start(float *d_a, float *w_a, const float *p_a, const 
                                 const float *d_b, const float *w_b, const float *p_b,
                                 const uint8_t *f_b, long long total, cudaStream_t st) {
   if (total == 0) return cudaSuccess;
-  select_start_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(d_a, w_a, p_a, f_a, d_b,
-                                                                      w_b, p_b, f_b, total);
-  return cudaGetLastError();
+  return launch_maybe_overlapped(select_start_kernel, dim3((unsigned)((total + 255) / 256)),
+                                 dim3(256), 0, st, d_a, w_a, p_a, f_a, d_b, w_b, p_b, f_b, total);
 }
 
 namespace {
