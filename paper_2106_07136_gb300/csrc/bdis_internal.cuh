@@ -237,6 +237,17 @@ __device__ __forceinline__ float ld_checked(const float *p, const float *base, l
   if (!in_bounds(p - base, n, site)) return 0.f;
   return __ldg(p);
 }
+// Site wrappers: in the normal build they expand to the plain expression
+// (so its code is exactly what it was without checks), in the checked build
+// to the checked form. BDIS_CHECKED_ONLY(...) keeps its argument only in the
+// checked build (extra parameters and arguments).
+#ifdef BDIS_CHECKED
+#define BDIS_CHECKED_ONLY(...) __VA_ARGS__
+#define BDIS_LDG(p, base, n, site) ::bdis::ld_checked((p), (base), (n), (site))
+#else
+#define BDIS_CHECKED_ONLY(...)
+#define BDIS_LDG(p, base, n, site) __ldg(p)
+#endif
 // Read and clear this translation unit's check word (always 0 in the normal
 // build).
 static inline cudaError_t take_check_word(unsigned *v) {

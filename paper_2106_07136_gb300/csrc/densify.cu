@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
         const int j = rr < NR ? jr0 + rr : a.ny - 1;
         const long long o = (long long)j * a.nx + i;
         const unsigned step = (unsigned)(rr * NCMAX * sizeof(float));
-        if (!in_bounds(o, a.np, kCheckDensifyTile)) continue;
+        BDIS_CHECKED_ONLY(if (!in_bounds(o, a.np, kCheckDensifyTile)) continue;)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dw0 + step), "l"(wp + o));
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dd0 + step), "l"(dp + o));
       }
@@ -311,8 +311,9 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
                                      y * 0.5f);
       else
         out = 0.f;
-      const long long oi = obase + (long long)y * a.w;
-      if (in_bounds(oi, a.total, kCheckDensifyOut)) a.out[oi] = out;
+      BDIS_CHECKED_ONLY(if (!in_bounds(obase + (long long)y * a.w, a.total, kCheckDensifyOut))
+                            continue;)
+      a.out[obase + (long long)y * a.w] = out;
     }
   }
 }

@@ -244,7 +244,8 @@ __device__ __forceinline__ void pyramid_passes(const float2 (*inLR)[kStP], float
     const float d0 = sLR[cy][cx + 1].x - sLR[cy][cx - 1].x;
     const float dp = sLR[cy + 1][cx + 1].x - sLR[cy + 1][cx - 1].x;
     const size_t o = (size_t)b * dw * dh + (size_t)Y * dw + X;
-    if (!in_bounds((long long)o, (long long)gridDim.z * dw * dh, kCheckPyramidOut)) continue;
+    BDIS_CHECKED_ONLY(
+        if (!in_bounds((long long)o, (long long)gridDim.z * dw * dh, kCheckPyramidOut)) continue;)
     const float2 v = sLR[cy][cx];
     L1[o] = v.x;
     G1[o] = (dm + 2.f * d0 + dp) * 0.125f;
@@ -277,7 +278,9 @@ __global__ void __launch_bounds__(256) pyramid_fused_kernel(
 #pragma unroll
     for (int u = 0; u < 3; ++u) {
       if (!xok[u]) continue;
-      if (!in_bounds((long long)rowoff + xsrc[u], (long long)w * h, kCheckPyramidStage)) continue;
+      BDIS_CHECKED_ONLY(
+          if (!in_bounds((long long)rowoff + xsrc[u], (long long)w * h, kCheckPyramidStage))
+              continue;)
       const int c = lane + 32 * u;
       const unsigned dl = (unsigned)__cvta_generic_to_shared(&inLR[r][c].x);
       const unsigned dr = (unsigned)__cvta_generic_to_shared(&inLR[r][c].y);
@@ -330,12 +333,17 @@ __global__ void __launch_bounds__(256) prepare_pyramid0_kernel(
       const int r = warp + 8 * q, yi = 2 * Y0 - 4 + r;
       const bool rok = lane < kWords && r < kStY && yi <= h + 1;
       const size_t off = (size_t)(rok ? reflect101(yi, h) : 0) * pitch + (size_t)(2 * X0 - 4);
+#ifdef BDIS_CHECKED
       // the word's last byte lies inside the view (h - 1 full rows and w bytes)
       const bool inb =
           !rok || in_bounds((long long)(off + 4 * lane + 3), (long long)(h - 1) * pitch + w,
                             kCheckPyramidInput);
       wl[q] = rok && inb ? __ldg(reinterpret_cast<const uint32_t *>(lb + off) + lane) : 0u;
       wr[q] = rok && inb ? __ldg(reinterpret_cast<const uint32_t *>(rb + off) + lane) : 0u;
+#else
+      wl[q] = rok ? __ldg(reinterpret_cast<const uint32_t *>(lb + off) + lane) : 0u;
+      wr[q] = rok ? __ldg(reinterpret_cast<const uint32_t *>(rb + off) + lane) : 0u;
+#endif
     }
 #pragma unroll
     for (int q = 0; q < kRowsPerWarp; ++q) {
@@ -358,9 +366,10 @@ __global__ void __launch_bounds__(256) prepare_pyramid0_kernel(
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
         if (!xok[u]) continue;
-        if (!in_bounds((long long)row * pitch + (long long)xsrc[u] * sizeof(T),
-                       (long long)(h - 1) * pitch + (long long)w * sizeof(T), kCheckPyramidInput))
-          continue;
+        BDIS_CHECKED_ONLY(
+            if (!in_bounds((long long)row * pitch + (long long)xsrc[u] * sizeof(T),
+                           (long long)(h - 1) * pitch + (long long)w * sizeof(T),
+                           kCheckPyramidInput)) continue;)
         inLR[r][lane + 32 * u] = make_float2(load_px<T>(lb, pitch, xsrc[u], row),
                                              load_px<T>(rb, pitch, xsrc[u], row));
       }
@@ -385,7 +394,8 @@ __global__ void __launch_bounds__(256) prepare_pyramid0_kernel(
       const float d0 = inLR[r][c + 1].x - inLR[r][c - 1].x;
       const float dp = inLR[r + 1][c + 1].x - inLR[r + 1][c - 1].x;
       const size_t o = (size_t)b * w * h + (size_t)y * w + x;
-      if (!in_bounds((long long)o, (long long)gridDim.z * w * h, kCheckPyramidOut)) continue;
+      BDIS_CHECKED_ONLY(
+          if (!in_bounds((long long)o, (long long)gridDim.z * w * h, kCheckPyramidOut)) continue;)
       L0[o] = v.x;
       G0[o] = (dm + 2.f * d0 + dp) * 0.125f;
       R0[o] = make_float2(v.y, x + 1 < w ? inLR[r][c + 1].y - v.y : 0.f);

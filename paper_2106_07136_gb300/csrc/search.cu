@@ -131,7 +131,7 @@ __device__ __forceinline__ void finish_patch(const SearchArgs &a, long long k, b
   }
   if (nvalid < a.nmin_valid) flags |= kFlagGamma;
   const bool drop = (flags & kDropFlags) != 0;
-  if (write && in_bounds(k, a.total, kCheckSearchOut)) {
+  if (write BDIS_CHECKED_ONLY(&&in_bounds(k, a.total, kCheckSearchOut))) {
     if (a.fusion == BDIS_FUSION_DIS) {
       // DIS fuses every patch (Eq. 2); a runaway patch falls back to its start
       a.d_star[k] = (flags & kFlagDiverged) ? u0 : D;
@@ -159,7 +159,7 @@ __device__ __forceinline__ void finish_patch_dis(const SearchArgs &a, long long 
   if (!isfinite(D) || fabsf(D - u0) > (float)ps) flags |= kFlagDiverged;
   if (fabsf(last_step) > kConvergeTol) flags |= kFlagUnconverged;
   if (nvalid < a.nmin_valid) flags |= kFlagGamma;
-  if (write && in_bounds(k, a.total, kCheckSearchOut)) {
+  if (write BDIS_CHECKED_ONLY(&&in_bounds(k, a.total, kCheckSearchOut))) {
     a.d_star[k] = (flags & kFlagDiverged) ? u0 : D;
     a.weight[k] = 1.f;
     if (a.u_init) a.u_init[k] = u0;
@@ -195,26 +195,19 @@ struct GlobalRows {
   __device__ __forceinline__ const float2 *col_clamped(int x) const {
     return row0 + min(max(x, 0), w - 1);
   }
+#ifdef BDIS_CHECKED
   __device__ __forceinline__ float2 ld(const float2 *p, int r) const {
     const float2 *q = p + (size_t)r * w;
-#ifdef BDIS_CHECKED
     if (!in_bounds(q - base, n, kCheckSearchSample)) return make_float2(0.f, 0.f);
-#endif
     return __ldg(q);
   }
+#else
+  __device__ __forceinline__ float2 ld(const float2 *p, int r) const {
+    return __ldg(p + (size_t)r * w);
+  }
+#endif
   __device__ __forceinline__ void ready() const {}
 };
-
-__device__ __forceinline__ GlobalRows global_rows(const SearchArgs &a, const float2 *row0) {
-  GlobalRows g;
-  g.row0 = row0;
-  g.w = a.w;
-#ifdef BDIS_CHECKED
-  g.base = a.R2;
-  g.n = a.pixels;
-#endif
-  return g;
-}
 
 template <int TW>
 struct TileRows {
@@ -292,7 +285,7 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
         float ge[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e)
-          ge[e] = act[2 * jp + e] ? ld_checked(Gc + (size_t)r * w + 2 * jp + e, a.G, a.pixels,
+          ge[e] = act[2 * jp + e] ? BDIS_LDG(Gc + (size_t)r * w + 2 * jp + e, a.G, a.pixels,
                                                kCheckSearchRows)
                                   : 0.f;
         g2[jp][r] = make_float2(ge[0], ge[1]);
@@ -315,7 +308,7 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
         float te[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e)
-          te[e] = act[2 * jp + e] ? ld_checked(Lc + (size_t)r * w + 2 * jp + e, a.L, a.pixels,
+          te[e] = act[2 * jp + e] ? BDIS_LDG(Lc + (size_t)r * w + 2 * jp + e, a.L, a.pixels,
                                                kCheckSearchRows)
                                   : 0.f;
         h2 = __ffma2_rn(q, q, h2);
@@ -332,7 +325,7 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
 #pragma unroll
       for (int r = 0; r < PS; ++r) {
         g[j][r] =
-            v[j] ? ld_checked(Gc + (size_t)r * w + j, a.G, a.pixels, kCheckSearchRows) : 0.f;
+            v[j] ? BDIS_LDG(Gc + (size_t)r * w + j, a.G, a.pixels, kCheckSearchRows) : 0.f;
         sg += g[j][r];
       }
     sg = group_sum<G>(sg);
@@ -348,7 +341,7 @@ __device__ __forceinline__ void patch_sums(const SearchArgs &a, PatchState<PS, C
         if (need) st.gc.at(j, r) = q;
         hh = fmaf(q, q, hh);
         ct = fmaf(q,
-                  act[j] ? ld_checked(Lc + (size_t)r * w + j, a.L, a.pixels, kCheckSearchRows)
+                  act[j] ? BDIS_LDG(Lc + (size_t)r * w + j, a.L, a.pixels, kCheckSearchRows)
                          : 0.f,
                   ct);
       }
@@ -474,9 +467,9 @@ __device__ __forceinline__ bool search_next_step(const SearchArgs &a, const Rows
 // outside the image or the staged tile); without it every pair is in both.
 // An invalid column's sums are finite and are multiplied by 0 in the merge.
 template <int PS, int CPL, bool GUARD, class Rows>
-__device__ __forceinline__ void window_rows_pairs(const SearchArgs &a, const Rows &rows, int ib,
-                                                  float t, float th, bool hi, const float *Lc,
-                                                  int w,
+__device__ __forceinline__ void window_rows_pairs(BDIS_CHECKED_ONLY(const SearchArgs &a, )
+                                                  const Rows &rows, int ib, float t, float th,
+                                                  bool hi, const float *Lc, int w,
                                                   const bool (&act)[CPL],
                                                   const bool (&need)[CPL + 2],
                                                   const float (&cs)[CPL],
@@ -500,7 +493,7 @@ __device__ __forceinline__ void window_rows_pairs(const SearchArgs &a, const Row
       float tn[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e)
-        tn[e] = -(act[j + e] ? ld_checked(Lc + (size_t)r * w + j + e, a.L, a.pixels,
+        tn[e] = -(act[j + e] ? BDIS_LDG(Lc + (size_t)r * w + j + e, a.L, a.pixels,
                                           kCheckSearchRows)
                              : 0.f) -
                 cs[j + e];
@@ -606,7 +599,7 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
 #pragma unroll
   for (int j = 0; j < CPL; ++j)
     cs[j] = vc[j] ? lerp_packed(rows.ld(rows.col(ib + j), 0), t) -
-                        ld_checked(Lc + j, a.L, a.pixels, kCheckSearchRows)
+                        BDIS_LDG(Lc + j, a.L, a.pixels, kCheckSearchRows)
                   : 0.f;
   // Merge per sample: s1 = sum of the residuals, md their mean, and
   // E = sum (d - md)^2 = S2 - 2 (md - cs) S1 + n (md - cs)^2 per column.
@@ -624,9 +617,11 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
     // A warp whose patches are all in range (so their pairs lie in a staged
     // tile, if any) with all pairs in the image reads them unconditionally.
     if (__all_sync(kFull, inr && ib >= 1 && ib + CPL <= w - 1))
-      window_rows_pairs<PS, CPL, false>(a, rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
+      window_rows_pairs<PS, CPL, false>(BDIS_CHECKED_ONLY(a, ) rows, ib, t, th, hi, Lc, w, act,
+                                        need, cs, P1, P2);
     else
-      window_rows_pairs<PS, CPL, true>(a, rows, ib, t, th, hi, Lc, w, act, need, cs, P1, P2);
+      window_rows_pairs<PS, CPL, true>(BDIS_CHECKED_ONLY(a, ) rows, ib, t, th, hi, Lc, w, act,
+                                       need, cs, P1, P2);
     // the merge below, per column pair; an invalid column's term is x * 0
     // (every term is finite)
     const float2 kPS = make_float2((float)PS, (float)PS), kM2 = make_float2(-2.f, -2.f);
@@ -676,7 +671,7 @@ __device__ __forceinline__ void fixed_patch(const SearchArgs &a, const Rows &row
 #pragma unroll
       for (int j = 0; j < CPL; ++j) {
         const float Tj =  // template + shift
-            (vc[j] ? ld_checked(Lc + (size_t)r * w + j, a.L, a.pixels, kCheckSearchRows) : 0.f) +
+            (vc[j] ? BDIS_LDG(Lc + (size_t)r * w + j, a.L, a.pixels, kCheckSearchRows) : 0.f) +
             cs[j];
         // samples i = 0..4 at D* - 1, -0.5, 0, +0.5, +1: columns ib + j + 1 .. ib + j - 1.
         // An invalid column's sums (finite: its pairs read as 0) are not merged below.
@@ -757,7 +752,9 @@ __global__ void __launch_bounds__(kSearchThreads, MINB) search_fixed_kernel(cons
                                 cy * 0.5f);
   }
   __shared__ float sgc[SH ? CPL * PS * kSearchThreads : 1];
-  fixed_patch<PS, CPL, SH>(a, global_rows(a, a.R2 + (long long)b * a.plane + (long long)y0 * w),
+  fixed_patch<PS, CPL, SH>(a,
+                           GlobalRows{a.R2 + (long long)b * a.plane + (long long)y0 * w,
+                                      w BDIS_CHECKED_ONLY(, a.R2, a.pixels)},
                            k, live, c, gbits, b, x0, y0, u0, sgc);
 }
 
@@ -834,7 +831,8 @@ __global__ void __launch_bounds__(kSearchThreads, MINB) search_tiled_kernel(cons
     }
     fixed_patch<PS, CPL>(a, TileRows<TW>{tile, lo, width}, k, live, c, gbits, b, x0, y0, u0);
   } else {
-    fixed_patch<PS, CPL>(a, global_rows(a, row0), k, live, c, gbits, b, x0, y0, u0);
+    fixed_patch<PS, CPL>(a, GlobalRows{row0, w BDIS_CHECKED_ONLY(, a.R2, a.pixels)}, k, live, c,
+                         gbits, b, x0, y0, u0);
   }
 }
 
@@ -860,7 +858,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
   float T[G];
 #pragma unroll
   for (int r = 0; r < G; ++r)
-    T[r] = (act && r < ps) ? ld_checked(Lc + (size_t)r * w, a.L, a.pixels, kCheckSearchRows) : 0.f;
+    T[r] = (act && r < ps) ? BDIS_LDG(Lc + (size_t)r * w, a.L, a.pixels, kCheckSearchRows) : 0.f;
 
   const float u0 = pp.u0;
   float D = u0, last_step = 0.f;
@@ -885,7 +883,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
       float sg = 0.f;
 #pragma unroll
       for (int r = 0; r < G; ++r)
-        sg += (v && r < ps) ? ld_checked(Gc + (size_t)r * w, a.G, a.pixels, kCheckSearchRows) : 0.f;
+        sg += (v && r < ps) ? BDIS_LDG(Gc + (size_t)r * w, a.G, a.pixels, kCheckSearchRows) : 0.f;
       sg = group_sum<G>(sg);
       const int nn = ps * __popc(m);
       const float mg = (a.normalize && nn > 0) ? sg / (float)nn : 0.f;
@@ -893,7 +891,7 @@ __global__ void __launch_bounds__(128) search_generic_kernel(const SearchArgs a)
 #pragma unroll
       for (int r = 0; r < G; ++r) {
         const float q =
-            (v && r < ps) ? ld_checked(Gc + (size_t)r * w, a.G, a.pixels, kCheckSearchRows) - mg
+            (v && r < ps) ? BDIS_LDG(Gc + (size_t)r * w, a.G, a.pixels, kCheckSearchRows) - mg
                           : 0.f;
         if (need) gc[r] = q;
         hh = fmaf(q, q, hh);
