@@ -548,16 +548,18 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     res = {}
     B = left.shape[0]
     # end to end through the C ABI with host buffers (pinned), copies timed.
-    # The two buffer sets of the streamed form are halves of one pinned
-    # allocation each for inputs and outputs, so that they share a placement
-    # in host memory (separately pinned buffers can land on slower memory)
-    hin = torch.empty((2, 2, B, H, W), dtype=torch.uint8, pin_memory=True)
-    hout = torch.empty((2, B, H, W), dtype=torch.float32, pin_memory=True)
+    # The streamed form keeps as many calls in flight as the library has
+    # device slots, each with its own host buffer set; the sets are slices of
+    # one pinned allocation each for inputs and outputs, so that they share a
+    # placement in host memory
+    S = bd.ASYNC_SLOTS
+    hin = torch.empty((S, 2, B, H, W), dtype=torch.uint8, pin_memory=True)
+    hout = torch.empty((S, B, H, W), dtype=torch.float32, pin_memory=True)
     lh, rh = left.cpu(), right.cpu()
-    for s in range(2):
+    for s in range(S):
         hin[s, 0].copy_(lh)
         hin[s, 1].copy_(rh)
-    sets = [(hin[s, 0], hin[s, 1], hout[s]) for s in range(2)]
+    sets = [(hin[s, 0], hin[s, 1], hout[s]) for s in range(S)]
     Lp, Rp, Op = sets[0]
     for _ in range(max(1, args.warmup)):
         m.match_host(Lp, Rp, params, out=Op)
@@ -575,21 +577,22 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
                 "runs": runs, "steps_per_run": k,
                 "path": "bdis_match_host (returns with the result): pinned host uint8 in, "
                         "float32 disparity out, 4 chunks overlapping copies and match"}
-    # the same steps as a stream of batches: step i is enqueued (bdis_match_host_async)
-    # before step i-1's result is waited for, on two pinned buffer sets, so one
-    # step's copies overlap its neighbours' matches; every step's copies are timed
+    # the same steps as a stream of batches (bdis_match_host_async): up to S
+    # steps in flight, step i enqueued once step i - S (whose buffer set it
+    # reuses) has been waited for, so a step's copies overlap other steps'
+    # matches; every step's copies are timed
 
     def stream_of(n):
-        prev = None
+        tickets = []
         for i in range(n):
-            lt, rt, ot = sets[i % 2]
+            if i >= S:
+                m.host_wait(tickets[i - S])
+            lt, rt, ot = sets[i % S]
             t, _ = m.match_host_async(lt, rt, params, out=ot)
-            if prev is not None:
-                m.host_wait(prev)
-            prev = t
-        m.host_wait(prev)
+            tickets.append(t)
+        m.host_wait(tickets[-1])
 
-    stream_of(max(2, args.warmup))
+    stream_of(max(S, args.warmup))
     runs = []
     for _ in range(3):
         t0 = time.perf_counter()
@@ -598,16 +601,17 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     res["e2e"] = {"value": statistics.median(runs), "unit": "pairs/s",
                   "h2d_bytes_per_step": 2 * B * W * H, "d2h_bytes_per_step": 4 * B * W * H,
                   "runs": runs, "steps": k,
-                  "path": "bdis_match_host_async + bdis_host_wait, one call per step, step i "
-                          "enqueued before step i-1 is waited for: pinned host uint8 in, "
+                  "path": "bdis_match_host_async + bdis_host_wait, one call per step, up to "
+                          f"{S} in flight (step i enqueued after step i-{S} is waited for): "
+                          "pinned host uint8 in, "
                           "float32 disparity out, host wall clock over all steps"}
     res["e2e_blocking"] = blocking
-    # both buffer sets hold exactly the device entry's result for these pairs
+    # every buffer set holds exactly the device entry's result for these pairs
     ref_t = m.match(left, right, params)
     torch.cuda.synchronize(device)
     ref = ref_t.cpu().numpy()
     same = True
-    for o in (sets[0][2].numpy(), sets[1][2].numpy()):
+    for o in (st[2].numpy() for st in sets):
         same = same and np.array_equal(np.isnan(o), np.isnan(ref)) and \
             np.array_equal(o[~np.isnan(o)], ref[~np.isnan(ref)])
     res["e2e"]["equals_device_result"] = bool(same)

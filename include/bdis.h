@@ -253,10 +253,12 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
  * serving): the call enqueues the copy-in, the match (Sec. 2, as at
  * bdis_match) and the copy-out of one whole batch and returns at once with
  * a ticket (> 0) in *ticket. Successive calls overlap: a call's copy-in
- * runs beside the previous call's match, its copy-out beside the next one's.
- * The device holds two batches' inputs and outputs (slot = ticket & 1); a
- * slot is refilled only after the match and the copy-out of the call two
- * before have finished.
+ * runs beside earlier calls' matches, its copy-out beside later ones'. The
+ * device holds BDIS_ASYNC_SLOTS (4) batches' inputs and outputs (slot =
+ * ticket % 4); a slot is refilled only after the match and the copy-out of
+ * the call four before have finished, so up to four calls can be in flight
+ * and a copy that runs late holds up the matches only once all four slots
+ * are taken.
  * Ownership: left, right and disparity_out stay the caller's; they must not
  * be written (inputs) or read (output) until bdis_host_wait(h, ticket) has
  * returned. Use pinned host memory: with pageable memory the copies, and so
@@ -267,6 +269,7 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
  * Errors: argument, parameter and geometry errors as at bdis_match_host,
  * returned at once with nothing enqueued; CUDA errors of the enqueue at
  * once; CUDA errors of the work itself from bdis_host_wait. */
+#define BDIS_ASYNC_SLOTS 4
 bdis_status bdis_match_host_async(bdis_handle *h, const uint8_t *left, const uint8_t *right,
                                   int width, int height, int count, const bdis_params *p,
                                   float *disparity_out, uint64_t *ticket);

@@ -45,4 +45,4 @@ from .api import (  # noqa: F401
     upsample,
     warm_map,
 )
-from ._lib import BdisError, BdisParams, library_path, load  # noqa: F401
+from ._lib import ASYNC_SLOTS, BdisError, BdisParams, library_path, load  # noqa: F401

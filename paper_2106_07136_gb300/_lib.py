@@ -38,6 +38,7 @@ BDIS_PLAN_AUTOTUNE = 1
 BDIS_PLAN_SCALE_TO_WIDTH = 2
 
 STATIC_SCRATCH_BYTES = 24 << 20  # BDIS_STATIC_SCRATCH_BYTES
+ASYNC_SLOTS = 4  # BDIS_ASYNC_SLOTS: bdis_match_host_async calls in flight at once
 
 TIMING_CLASSES = ["prepare_level0", "pyramid_level", "search", "densify", "upsample",
                   "warm_map", "proposal_net", "select_start"]

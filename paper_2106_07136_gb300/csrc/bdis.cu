@@ -22,6 +22,10 @@
 
 #include "bdis_internal.cuh"
 
+// Calls of bdis_match_host_async that can be in flight at once: each holds
+// its own device inputs and output, reused by the call kAsyncSlots later.
+constexpr int kAsyncSlots = BDIS_ASYNC_SLOTS;
+
 struct bdis_handle {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -38,12 +42,13 @@ struct bdis_handle {
   // bdis_match_host pipeline: copy-in and copy-out streams beside `stream`,
   // and per buffer slot the events "inputs copied", "matched", "output copied"
   cudaStream_t copy_in = nullptr, copy_out = nullptr;
-  cudaEvent_t ev_in[2] = {}, ev_done[2] = {}, ev_out[2] = {};
+  // (bdis_match_host uses two slots, bdis_match_host_async kAsyncSlots)
+  cudaEvent_t ev_in[kAsyncSlots] = {}, ev_done[kAsyncSlots] = {}, ev_out[kAsyncSlots] = {};
   // bdis_match_host_async: calls enqueued since the streams were last idle,
   // the next ticket, and the workspace layout those calls use (slot buffers)
   int async_pending = 0;
   uint64_t async_next = 1;
-  size_t async_key[7] = {};
+  size_t async_key[1 + 3 * kAsyncSlots] = {};
 };
 
 namespace bdis {
@@ -703,7 +708,7 @@ void bdis_destroy(bdis_handle *h) {
       cudaStreamSynchronize(h->copy_out);
       cudaStreamDestroy(h->copy_in);
       cudaStreamDestroy(h->copy_out);
-      for (int i = 0; i < 2; ++i) {
+      for (int i = 0; i < kAsyncSlots; ++i) {
         cudaEventDestroy(h->ev_in[i]);
         cudaEventDestroy(h->ev_done[i]);
         cudaEventDestroy(h->ev_out[i]);
@@ -888,7 +893,7 @@ bdis_status ensure_pipeline(bdis_handle *h) {
   if (h->copy_in) return BDIS_OK;
   cudaError_t e = cudaStreamCreateWithFlags(&h->copy_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_out, cudaStreamNonBlocking);
-  for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+  for (int i = 0; i < kAsyncSlots && e == cudaSuccess; ++i) {
     e = cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming);
@@ -995,11 +1000,12 @@ bdis_status bdis_match_host_async(bdis_handle *h, const uint8_t *left, const uin
   if (s != BDIS_OK) return s;
   s = ensure_pipeline(h);
   if (s != BDIS_OK) return s;
-  // One whole batch per call, its device inputs and output in slot (ticket & 1):
-  // the copy-in of this call overlaps the match of the previous one, and its
-  // copy-out the match of the next. A slot is refilled only after the match
-  // that read its inputs (ev_done) and the copy-out that read its output
-  // (ev_out) of the call two before have finished.
+  // One whole batch per call, its device inputs and output in slot
+  // (ticket % kAsyncSlots): the copy-in of this call overlaps the matches
+  // before it, and its copy-out the matches after it. A slot is refilled only
+  // after the match that read its inputs (ev_done) and the copy-out that read
+  // its output (ev_out) of the call kAsyncSlots before have finished, so a
+  // copy that runs late holds up the matches only once all slots are taken.
   const size_t wh = (size_t)width * height;
   const Layout lay = plan_layout(width, height, count, *p, true);
   const size_t in_b = wh * count, out_b = wh * count * sizeof(float);
@@ -1009,10 +1015,22 @@ bdis_status bdis_match_host_async(bdis_handle *h, const uint8_t *left, const uin
     off += (n + 255) / 256 * 256;
     return o;
   };
-  const size_t slot_l[2] = {lay.in_left, take(in_b)};
-  const size_t slot_r[2] = {lay.in_right, take(in_b)};
-  const size_t slot_o[2] = {lay.out, take(out_b)};
-  const size_t key[7] = {off, slot_l[0], slot_l[1], slot_r[0], slot_r[1], slot_o[0], slot_o[1]};
+  size_t slot_l[kAsyncSlots], slot_r[kAsyncSlots], slot_o[kAsyncSlots];
+  slot_l[0] = lay.in_left;
+  slot_r[0] = lay.in_right;
+  slot_o[0] = lay.out;
+  for (int i = 1; i < kAsyncSlots; ++i) {
+    slot_l[i] = take(in_b);
+    slot_r[i] = take(in_b);
+    slot_o[i] = take(out_b);
+  }
+  size_t key[1 + 3 * kAsyncSlots] = {off};
+  for (int i = 0; i < kAsyncSlots; ++i) {
+    key[1 + 3 * i] = slot_l[i];
+    key[2 + 3 * i] = slot_r[i];
+    key[3 + 3 * i] = slot_o[i];
+  }
+  static_assert(sizeof key == sizeof(((bdis_handle *)nullptr)->async_key), "key size");
   if (h->async_pending && memcmp(key, h->async_key, sizeof key) != 0) {
     cudaError_t e = drain_async(h);  // calls in flight use another layout
     if (e != cudaSuccess) return record_cuda(e);
@@ -1021,7 +1039,7 @@ bdis_status bdis_match_host_async(bdis_handle *h, const uint8_t *left, const uin
   if (s != BDIS_OK) return s;
   memcpy(h->async_key, key, sizeof key);
   const uint64_t t = h->async_next;
-  const int slot = (int)(t & 1u);
+  const int slot = (int)(t % kAsyncSlots);
   char *base = static_cast<char *>(h->ws);
   cudaError_t e = cudaStreamWaitEvent(h->copy_in, h->ev_done[slot], 0);
   if (e == cudaSuccess)
@@ -1057,7 +1075,7 @@ bdis_status bdis_host_wait(bdis_handle *h, uint64_t ticket) {
   if (!h->async_pending) return BDIS_OK;  // drained since (by a later call or wait)
   // The slot's copy-out event was recorded by this call or by a later one on
   // the same in-order stream: once it has completed, so has this call.
-  cudaError_t e = cudaEventSynchronize(h->ev_out[ticket & 1u]);
+  cudaError_t e = cudaEventSynchronize(h->ev_out[ticket % kAsyncSlots]);
   if (e == cudaSuccess && ticket + 1 == h->async_next) e = drain_async(h);
   return record_cuda(e);
 }
@@ -1073,7 +1091,7 @@ bdis_status bdis_host_wait_timeout(bdis_handle *h, uint64_t ticket, double timeo
                         std::chrono::duration_cast<std::chrono::steady_clock::duration>(
                             std::chrono::duration<double, std::milli>(timeout_ms));
   while (true) {
-    cudaError_t e = cudaEventQuery(h->ev_out[ticket & 1u]);
+    cudaError_t e = cudaEventQuery(h->ev_out[ticket % kAsyncSlots]);
     if (e == cudaSuccess) break;
     if (e != cudaErrorNotReady) return record_cuda(e);
     cudaGetLastError();  // not-ready is not an error

@@ -32,6 +32,7 @@ CONSTANTS = {
     "BDIS_PLAN_AUTOTUNE": _lib.BDIS_PLAN_AUTOTUNE,
     "BDIS_PLAN_SCALE_TO_WIDTH": _lib.BDIS_PLAN_SCALE_TO_WIDTH,
     "BDIS_STATIC_SCRATCH_BYTES": _lib.STATIC_SCRATCH_BYTES,
+    "BDIS_ASYNC_SLOTS": _lib.ASYNC_SLOTS,
     "BDIS_TIMING_CLASSES": len(_lib.BdisTiming._fields_[0][1]()),
 }
 

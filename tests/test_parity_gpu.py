@@ -9,6 +9,7 @@ import pytest
 import torch
 
 import paper_2106_07136_gb300 as bd
+from paper_2106_07136_gb300 import _lib
 import synth
 from gpu_helpers import (DENSE_ATOL, DROP, DSTAR_ATOL, ILL_CONDITIONED_PAIR, POST_ATOL, PYR_ATOL,
                          assert_explained, dev, explained_flag_mismatch, host, oracle_unstable)
@@ -425,28 +426,32 @@ def _same(a, b):
 
 @pytest.mark.parametrize("pinned", [True, False])
 def test_match_host_async_equals_device(matcher, pinned):
-    """Asynchronous host calls: five batches enqueued back to back (more calls
-    in flight than the two device slots), then waited for out of order. Each
-    result is exactly the device entry's. A device call in between waits for
-    the calls in flight first (its workspace layout overlaps their slots);
-    another batch size in flight changes the layout the same way."""
+    """Asynchronous host calls: seven batches enqueued back to back (more calls
+    in flight than the device's BDIS_ASYNC_SLOTS slots, so later calls reuse
+    the slots of earlier ones), then waited for out of order. Each result is
+    exactly the device entry's. A device call in between waits for the calls
+    in flight first (its workspace layout overlaps their slots); another
+    batch size in flight changes the layout the same way."""
     gp = bd.default_params(**CFG1)
-    batches = [synth.make_batch(1, n, first_index=3 * i)[:2] for i, n in enumerate([3, 3, 3, 3, 2])]
+    sizes = [3, 3, 3, 3, 3, 3, 3, 2]
+    batches = [synth.make_batch(1, n, first_index=3 * i)[:2] for i, n in enumerate(sizes)]
     ref = [host(matcher.match(dev(L, torch.uint8), dev(R, torch.uint8), gp)) for L, R in batches]
     pin = (lambda t: t.pin_memory()) if pinned else (lambda t: t)
     hosts = [(pin(torch.from_numpy(L)), pin(torch.from_numpy(R))) for L, R in batches]
-    calls = [matcher.match_host_async(lt, rt, gp) for lt, rt in hosts[:4]]
+    n = len(sizes) - 1
+    assert n > _lib.ASYNC_SLOTS
+    calls = [matcher.match_host_async(lt, rt, gp) for lt, rt in hosts[:n]]
     tickets = [t for t, _ in calls]
-    assert tickets == sorted(tickets) and len(set(tickets)) == 4
+    assert tickets == sorted(tickets) and len(set(tickets)) == n
     matcher.host_wait(tickets[1])
     assert _same(calls[0][1].numpy(), ref[0]) and _same(calls[1][1].numpy(), ref[1])
     mid = host(matcher.match(dev(batches[0][0], torch.uint8), dev(batches[0][1], torch.uint8), gp))
     assert _same(mid, ref[0])
-    t5, out5 = matcher.match_host_async(*hosts[4], gp)  # another batch size
+    t5, out5 = matcher.match_host_async(*hosts[n], gp)  # another batch size
     matcher.host_wait(t5)
-    for (_, out), r in zip(calls[2:], ref[2:4]):
+    for (_, out), r in zip(calls[2:], ref[2:n]):
         assert _same(out.numpy(), r)
-    assert _same(out5.numpy(), ref[4])
+    assert _same(out5.numpy(), ref[n])
     matcher.host_wait(tickets[0])  # long finished: returns at once
     with pytest.raises(bd.BdisError, match="invalid argument"):
         matcher.host_wait(t5 + 1)
