@@ -50,7 +50,7 @@ typedef enum {
     BDIS_E_NOMEM = 2,       /* device or pinned allocation failed; handle still usable */
     BDIS_E_CUDA = 3,        /* a CUDA call failed; see bdis_last_error_string() */
     BDIS_E_TIMEOUT = 4,     /* a bounded wait ran out */
-    BDIS_E_UNSUPPORTED = 5  /* valid for the method but outside this build's limits */
+    BDIS_E_UNSUPPORTED = 5  /* valid for the method but outside this library's limits */
 } bdis_status;
 
 typedef enum { BDIS_U8 = 0, BDIS_F32 = 1 } bdis_format;
