@@ -240,10 +240,11 @@ int bdis_proposal_level(int coarsest_scale);
 /* Same, with HOST buffers: left/right are `count` dense width x height uint8
  * images in host memory, disparity_out a dense host float array. The call
  * copies in, matches, copies out and returns when the result is in
- * disparity_out. A batch of 2 or more pairs runs as 2 (4 from 8 pairs)
- * chunks: one chunk's inputs are copied in while the previous chunk is
- * matched and the one before is copied out (two copy streams owned by the
- * handle, device buffers double-buffered). Pinned host memory makes the
+ * disparity_out. A batch of 2 or more pairs runs as 2 (4 from 8 pairs; from
+ * 32 pairs 5, the first and last a sixteenth of the batch each) chunks: one
+ * chunk's inputs are copied in while the previous chunk is matched and the
+ * one before is copied out (two copy streams owned by the handle, device
+ * buffers double-buffered). Pinned host memory makes the
  * copies asynchronous DMA; pageable memory works but is slower. */
 bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *right,
                             int width, int height, int count, const bdis_params *p,

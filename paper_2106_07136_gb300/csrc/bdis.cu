@@ -12,6 +12,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <new>
@@ -918,9 +919,28 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
   // chunk i-1 is matched (stream) and chunk i-2's result is copied out
   // (copy_out). Inputs and outputs on the device are double-buffered by slot
   // (i & 1); a slot is refilled only after the match that read it (ev_done)
-  // and the copy-out that read its output (ev_out) have finished.
-  const int nchunk = count >= 8 ? 4 : (count >= 2 ? 2 : 1);
-  const int cs = (count + nchunk - 1) / nchunk;
+  // and the copy-out that read its output (ev_out) have finished. From 32
+  // pairs the first and last chunks are a sixteenth of the batch, so that
+  // the copy-in before the first match and the copy-out after the last one
+  // (the only copies nothing hides) are short; three equal chunks between.
+  int chunk_first[5], chunk_n[5], nchunk;
+  if (count >= 32) {
+    const int edge = count / 16, mid = count - 2 * edge;
+    nchunk = 5;
+    chunk_n[0] = chunk_n[4] = edge;
+    chunk_n[1] = chunk_n[2] = mid / 3;
+    chunk_n[3] = mid - 2 * (mid / 3);
+  } else {
+    nchunk = count >= 8 ? 4 : (count >= 2 ? 2 : 1);
+    const int c = (count + nchunk - 1) / nchunk;
+    for (int i = 0; i < nchunk; ++i) chunk_n[i] = std::max(0, std::min(c, count - i * c));
+  }
+  int cs = 0;
+  for (int i = 0, f = 0; i < nchunk; ++i) {
+    chunk_first[i] = f;
+    f += chunk_n[i];
+    cs = std::max(cs, chunk_n[i]);
+  }
   const Layout lay = plan_layout(width, height, cs, *p, true);
   const size_t in_b = wh * cs, out_b = wh * cs * sizeof(float);
   size_t off = lay.bytes;
@@ -943,7 +963,7 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
   cudaStream_t sout = nchunk > 1 ? h->copy_out : h->stream;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < nchunk && e == cudaSuccess; ++i) {
-    const int first = i * cs, n = count - first < cs ? count - first : cs;
+    const int first = chunk_first[i], n = chunk_n[i];
     if (n <= 0) break;
     const int slot = i & 1;
     const size_t ib = wh * n;

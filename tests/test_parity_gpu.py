@@ -401,12 +401,13 @@ def test_batch_equals_single_pairs(orc, matcher):
 
 
 @pytest.mark.parametrize("count,pinned", [(1, True), (2, True), (3, True), (8, True), (13, True),
-                                          (13, False)])
+                                          (13, False), (32, True), (37, True)])
 def test_match_host_equals_device(matcher, count, pinned):
     """The host-buffer entry (chunked: copies of one chunk overlap the match
     of the next, device buffers double-buffered) returns exactly what the
     device entry returns, for every chunking: 1 pair, 2 and 4 chunks, a
-    short last chunk, and pageable host memory."""
+    short last chunk, pageable host memory, and the five graded chunks from
+    32 pairs (short first and last chunks, uneven middle ones)."""
     L, R, _ = synth.make_batch(1, count)
     gp = bd.default_params(**CFG1)
     dv = host(matcher.match(dev(L, torch.uint8), dev(R, torch.uint8), gp))
