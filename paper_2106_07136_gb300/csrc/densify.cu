@@ -135,10 +135,13 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
 // sums A_j, B_j of one new patch row per group and keeps the last M in
 // registers; the y-weighted sums then take them in ascending j, as the tiled
 // kernel does, with the same operations, so the two give identical results.
-// No shared memory and no block barriers: each warp's patch reads (19 patches
-// of a row for 32 columns) are L1 broadcasts.
+// The block's patch values are staged in shared memory once (one barrier);
+// a warp's reads of them (19 patches of a row for 32 columns) are broadcasts.
+// The y weights sit in registers (PS / 2 of them: the mask is symmetric); at
+// PS 8 that takes 72 registers, so 7 blocks of 128 per SM (at 64 registers
+// and 8 blocks they spilled, and the class took 4% longer).
 template <int PS, int S, int K>
-__global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(const DensifyArgs a) {
+__global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(const DensifyArgs a) {
   constexpr int M = PS / S;
   static_assert(M * S == PS && K % S == 0, "strip geometry");
   // patch columns / rows a block (128 columns x K rows) can need, plus one
@@ -258,6 +261,11 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
 
   const long long obase = (long long)b * a.plane + x;
   const int yend = min(Y0 + K, a.h);
+  // the y weights of the group's rows, in registers: the mask is symmetric
+  // (its offsets from the centre are +-m), so PS / 2 values hold it
+  float myr[PS / 2];
+#pragma unroll
+  for (int q = 0; q < PS / 2; ++q) myr[q] = smask[q];
   float nw[M + 1], nd[M + 1];  // row g's loads, issued during group g - 1
   if (g0 <= a.ny - 2) load_row(g0, nw, nd);
   for (int g = g0; g * S < yend; ++g) {
@@ -289,7 +297,8 @@ __global__ void __launch_bounds__(128, PS == 8 ? 8 : 6) densify_strip_kernel(con
 #pragma unroll
       for (int k = 0; k < M; ++k)
         if (kin[k]) {
-          const float my = smask[t + (M - 1 - k) * S];
+          const int q = t + (M - 1 - k) * S;  // known at compile time (unrolled)
+          const float my = myr[q < PS / 2 ? q : PS - 1 - q];
           nd2 = __ffma2_rn(make_float2(my, my), rAB[k], nd2);
         }
       if (y >= ylast) {
