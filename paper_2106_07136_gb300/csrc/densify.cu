@@ -11,8 +11,8 @@
 // Because the mask is separable, a block computes a 32x32 tile in two passes
 // through shared memory: first, for every patch row that touches the tile
 // and every tile column, the x-weighted sums over the covering patches of
-// that row (sum m_x w D and sum m_x w); then, per pixel, the y-weighted sum of
-// those over its covering rows. Work per pixel drops from (ps/stride)^2 to
+// that row (sum m_x (w D) and sum m_x w, w D formed once per patch); then,
+// per pixel, the y-weighted sum of those over its covering rows. Work per pixel drops from (ps/stride)^2 to
 // about 2 ps/stride multiply-adds per quantity.
 //
 // Roofline: DRAM bytes per pixel: 4 written (+4 read for the coarse map where
@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
       for (int ii = ilo; ii <= ihi + ilast; ++ii) {
         const int i = ii > ihi ? a.nx - 1 : ii;
         const float wk = __ldg(wr + i);
-        if (wk > 0.f) {
-          const float q2 = wk * mask[x - grid_origin(i, a.nx, a.w, a.ps, a.stride)];
-          A = fmaf(q2, __ldg(dr + i), A);
-          B += q2;
+        if (wk > 0.f) {  // a dropped patch has weight 0 (its D* may be NaN)
+          const float mx = mask[x - grid_origin(i, a.nx, a.w, a.ps, a.stride)];
+          A = fmaf(mx, wk * __ldg(dr + i), A);
+          B = fmaf(mx, wk, B);
         }
       }
     }
@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
   // at most K / S + M - 1 (rows g0 - M + 1 .. g0 + K / S - 1): with the last
   // column / row slot they fit the tile.
   static_assert((126 + PS) / S + 1 + 1 <= NCMAX && K / S + M - 1 + 1 <= NRMAX, "tile bounds");
-  __shared__ float sw[NRMAX][NCMAX], sd[NRMAX][NCMAX];
+  // staged patch values as (w D*, w) pairs; a dropped patch (w <= 0) as (0, 0)
+  __shared__ float2 swd[NRMAX][NCMAX];
   __shared__ float smask[PS];
   pdl_enter();
   const int X0 = blockIdx.x * 128, x = X0 + (int)threadIdx.x;
@@ -175,18 +176,26 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
     const int cc = threadIdx.x;
     if (cc <= NC) {
       const int i = cc < NC ? ic0 + cc : a.nx - 1;
-      const unsigned dw0 = (unsigned)__cvta_generic_to_shared(&sw[0][cc]);
-      const unsigned dd0 = (unsigned)__cvta_generic_to_shared(&sd[0][cc]);
+      const unsigned dd0 = (unsigned)__cvta_generic_to_shared(&swd[0][cc].x);
       for (int rr = 0; rr <= NR; ++rr) {
         const int j = rr < NR ? jr0 + rr : a.ny - 1;
         const long long o = (long long)j * a.nx + i;
-        const unsigned step = (unsigned)(rr * NCMAX * sizeof(float));
-        BDIS_CHECKED_ONLY(if (!in_bounds(o, a.np, kCheckDensifyTile)) continue;)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dw0 + step), "l"(wp + o));
+        const unsigned step = (unsigned)(rr * NCMAX * sizeof(float2));
+        BDIS_CHECKED_ONLY(if (!in_bounds(o, a.np, kCheckDensifyTile)) {
+          swd[rr][cc] = make_float2(0.f, 0.f);
+          continue;
+        })
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dd0 + step), "l"(dp + o));
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dd0 + step + 4),
+                     "l"(wp + o));
+      }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      // the thread's own copies are complete: form (w D*, w), as the tiled kernel does
+      for (int rr = 0; rr <= NR; ++rr) {
+        const float2 v = swd[rr][cc];  // (D*, w)
+        swd[rr][cc] = v.y > 0.f ? make_float2(v.y * v.x, v.y) : make_float2(0.f, 0.f);
       }
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
   }
   if (threadIdx.x < PS) {  // Gaussian mask (Eq. 5): the tiled kernel's expression and values
     const float m = (float)threadIdx.x - (PS - 1) * 0.5f;
@@ -208,43 +217,39 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
   }
   const float mxl = ilast ? mask_at(x - (a.w - PS)) : 0.f;
   // covering patch k of column x (k = 0..M: the regular ilo + k, then the last)
+  // and its x weight
   bool use[M + 1];
   int pidx[M + 1];
+  float mxk[M + 1];
 #pragma unroll
   for (int k = 0; k <= M; ++k) {
     const int ii = ilo + k;
     const bool reg = ii <= ihi;
     use[k] = reg || (ilast && ii == ihi + 1);
     pidx[k] = reg ? ii : a.nx - 1;
+    mxk[k] = reg ? mxr[k] : mxl;
   }
-  // a patch row's values (staged; read one row ahead of their use) and its
-  // x-weighted sums, in the same order and with the same operations as the
-  // tiled kernel
-  auto load_row = [&](int j, float *wv, float *dv) {
+  // a patch row's (w D*, w) pairs (staged; read one row ahead of their use)
+  // and its x-weighted sums, in the same order and with the same fmas as the
+  // tiled kernel: a patch that is not used, or dropped, is (0, 0) and adds
+  // exactly 0
+  auto load_row = [&](int j, float2 *v) {
     const int rr = j <= a.ny - 2 ? j - jr0 : NR;
 #pragma unroll
     for (int k = 0; k <= M; ++k) {
       const int cc = ilo + k <= ihi ? pidx[k] - ic0 : NC;
-      wv[k] = use[k] ? sw[rr][cc] : 0.f;
-      dv[k] = use[k] ? sd[rr][cc] : 0.f;
+      v[k] = use[k] ? swd[rr][cc] : make_float2(0.f, 0.f);
     }
   };
-  auto sum_row = [&](const float *wv, const float *dv, float &A, float &B) {
-    A = 0.f;
-    B = 0.f;
+  auto sum_row = [&](const float2 *v, float2 &AB) {
+    AB = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k <= M; ++k) {
-      if (use[k] && wv[k] > 0.f) {
-        const float q2 = wv[k] * (ilo + k <= ihi ? mxr[k] : mxl);
-        A = fmaf(q2, dv[k], A);
-        B += q2;
-      }
-    }
+    for (int k = 0; k <= M; ++k) AB = __ffma2_rn(make_float2(mxk[k], mxk[k]), v[k], AB);
   };
-  auto row_sums = [&](int j, float &A, float &B) {
-    float wv[M + 1], dv[M + 1];
-    load_row(j, wv, dv);
-    sum_row(wv, dv, A, B);
+  auto row_sums = [&](int j, float2 &AB) {
+    float2 v[M + 1];
+    load_row(j, v);
+    sum_row(v, AB);
   };
   const int ylast = a.h - PS;  // first pixel row the last patch row covers
   float2 last = make_float2(0.f, 0.f);
@@ -256,7 +261,7 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
   for (int k = 0; k < M - 1; ++k) {
     const int j = g0 - M + 1 + k;
     rAB[k + 1] = make_float2(0.f, 0.f);
-    if (j >= 0 && j <= a.ny - 2) row_sums(j, rAB[k + 1].x, rAB[k + 1].y);
+    if (j >= 0 && j <= a.ny - 2) row_sums(j, rAB[k + 1]);
   }
 
   const long long obase = (long long)b * a.plane + x;
@@ -266,20 +271,17 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
   float myr[PS / 2];
 #pragma unroll
   for (int q = 0; q < PS / 2; ++q) myr[q] = smask[q];
-  float nw[M + 1], nd[M + 1];  // row g's loads, issued during group g - 1
-  if (g0 <= a.ny - 2) load_row(g0, nw, nd);
+  float2 nv[M + 1];  // row g's loads, issued during group g - 1
+  if (g0 <= a.ny - 2) load_row(g0, nv);
   for (int g = g0; g * S < yend; ++g) {
-    float cw[M + 1], cd[M + 1];
+    float2 cv[M + 1];
 #pragma unroll
-    for (int k = 0; k <= M; ++k) {
-      cw[k] = nw[k];
-      cd[k] = nd[k];
-    }
-    if (g + 1 <= a.ny - 2 && (g + 1) * S < yend) load_row(g + 1, nw, nd);
+    for (int k = 0; k <= M; ++k) cv[k] = nv[k];
+    if (g + 1 <= a.ny - 2 && (g + 1) * S < yend) load_row(g + 1, nv);
 #pragma unroll
     for (int k = 0; k < M - 1; ++k) rAB[k] = rAB[k + 1];
     rAB[M - 1] = make_float2(0.f, 0.f);
-    if (g <= a.ny - 2) sum_row(cw, cd, rAB[M - 1].x, rAB[M - 1].y);
+    if (g <= a.ny - 2) sum_row(cv, rAB[M - 1]);
     // the covering regular rows of this group (the same for all its pixel rows)
     bool kin[M];
 #pragma unroll
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
         }
       if (y >= ylast) {
         if (!have_last) {
-          row_sums(a.ny - 1, last.x, last.y);
+          row_sums(a.ny - 1, last);
           have_last = true;
         }
         const float my = mask_at(y - ylast);
