@@ -152,6 +152,10 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
   // at most K / S + M - 1 (rows g0 - M + 1 .. g0 + K / S - 1): with the last
   // column / row slot they fit the tile.
   static_assert((126 + PS) / S + 1 + 1 <= NCMAX && K / S + M - 1 + 1 <= NRMAX, "tile bounds");
+  // column ZC is never a patch column: it holds (0, 0), the value of a patch
+  // that does not cover the pixel
+  constexpr int ZC = NCMAX - 1;
+  static_assert((126 + PS) / S + 1 + 1 <= ZC, "zero column");
   // staged patch values as (w D*, w) pairs; a dropped patch (w <= 0) as (0, 0)
   __shared__ float2 swd[NRMAX][NCMAX];
   __shared__ float smask[PS];
@@ -195,6 +199,8 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
         const float2 v = swd[rr][cc];  // (D*, w)
         swd[rr][cc] = v.y > 0.f ? make_float2(v.y * v.x, v.y) : make_float2(0.f, 0.f);
       }
+    } else if (cc == ZC) {
+      for (int rr = 0; rr <= NR; ++rr) swd[rr][ZC] = make_float2(0.f, 0.f);
     }
   }
   if (threadIdx.x < PS) {  // Gaussian mask (Eq. 5): the tiled kernel's expression and values
@@ -216,17 +222,15 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
     mxr[k] = (q >= 0 && q < PS) ? mask_at(q) : 0.f;
   }
   const float mxl = ilast ? mask_at(x - (a.w - PS)) : 0.f;
-  // covering patch k of column x (k = 0..M: the regular ilo + k, then the last)
-  // and its x weight
-  bool use[M + 1];
-  int pidx[M + 1];
+  // covering patch k of column x (k = 0..M: the regular ilo + k, then the
+  // last): its tile column (ZC where there is none) and its x weight
+  int cck[M + 1];
   float mxk[M + 1];
 #pragma unroll
   for (int k = 0; k <= M; ++k) {
     const int ii = ilo + k;
     const bool reg = ii <= ihi;
-    use[k] = reg || (ilast && ii == ihi + 1);
-    pidx[k] = reg ? ii : a.nx - 1;
+    cck[k] = reg ? ii - ic0 : (ilast && ii == ihi + 1) ? NC : ZC;
     mxk[k] = reg ? mxr[k] : mxl;
   }
   // a patch row's (w D*, w) pairs (staged; read one row ahead of their use)
@@ -234,12 +238,9 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
   // tiled kernel: a patch that is not used, or dropped, is (0, 0) and adds
   // exactly 0
   auto load_row = [&](int j, float2 *v) {
-    const int rr = j <= a.ny - 2 ? j - jr0 : NR;
+    const float2 *row = swd[j <= a.ny - 2 ? j - jr0 : NR];
 #pragma unroll
-    for (int k = 0; k <= M; ++k) {
-      const int cc = ilo + k <= ihi ? pidx[k] - ic0 : NC;
-      v[k] = use[k] ? swd[rr][cc] : make_float2(0.f, 0.f);
-    }
+    for (int k = 0; k <= M; ++k) v[k] = row[cck[k]];
   };
   auto sum_row = [&](const float2 *v, float2 &AB) {
     AB = make_float2(0.f, 0.f);
@@ -282,27 +283,20 @@ __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(con
     for (int k = 0; k < M - 1; ++k) rAB[k] = rAB[k + 1];
     rAB[M - 1] = make_float2(0.f, 0.f);
     if (g <= a.ny - 2) sum_row(cv, rAB[M - 1]);
-    // the covering regular rows of this group (the same for all its pixel rows)
-    bool kin[M];
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-      const int j = g - M + 1 + k;
-      kin[k] = j >= 0 && j <= a.ny - 2;
-    }
 #pragma unroll
     for (int t = 0; t < S; ++t) {
       const int y = g * S + t;
       if (y >= yend) break;
       // (numerator, denominator) as one packed f32x2 FMA per covering row:
-      // per component the same fma as the tiled kernel
+      // per component the same fma as the tiled kernel; a ring slot outside
+      // the regular rows holds (0, 0) and adds exactly 0
       float2 nd2 = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int k = 0; k < M; ++k)
-        if (kin[k]) {
-          const int q = t + (M - 1 - k) * S;  // known at compile time (unrolled)
-          const float my = myr[q < PS / 2 ? q : PS - 1 - q];
-          nd2 = __ffma2_rn(make_float2(my, my), rAB[k], nd2);
-        }
+      for (int k = 0; k < M; ++k) {
+        const int q = t + (M - 1 - k) * S;  // known at compile time (unrolled)
+        const float my = myr[q < PS / 2 ? q : PS - 1 - q];
+        nd2 = __ffma2_rn(make_float2(my, my), rAB[k], nd2);
+      }
       if (y >= ylast) {
         if (!have_last) {
           row_sums(a.ny - 1, last);
