@@ -509,17 +509,18 @@ def test_argument_errors(matcher):
 # ------------------------------------------- full sizes, bench launch shape
 
 def test_bench_launch_configuration(orc, matcher):
-    """The benchmark's launch: 128 pairs of 640x480 in one call (16 distinct
-    pairs tiled). Sampled pairs match the oracle; repeated pairs are
-    bit-identical wherever they sit in the batch."""
+    """The benchmark's launch: 512 pairs of 640x480 in one call (16 distinct
+    pairs tiled 32 times). Sampled pairs, taken from the front and the back of
+    the batch, match the oracle; repeated pairs are bit-identical wherever
+    they sit in the batch."""
     L, R, _ = synth.make_batch(2, 16)
-    Lb, Rb = np.concatenate([L] * 8), np.concatenate([R] * 8)
+    Lb, Rb = np.concatenate([L] * 32), np.concatenate([R] * 32)
     gp, op = params(orc, **CFG2)
     out = host(matcher.match(dev(Lb, torch.uint8), dev(Rb, torch.uint8), gp))
-    for i in (0, 5):
-        assert_explained(orc, out[i], L[i], R[i], gp, op, f"batch pair {i}")
+    for i, at in ((0, 0), (5, 16 * 31 + 5)):
+        assert_explained(orc, out[at], L[i], R[i], gp, op, f"batch pair {at}")
     for i in (0, 5, 11):
-        for rep in (1, 7):
+        for rep in (1, 7, 31):
             a, b = out[i], out[i + 16 * rep]
             assert np.array_equal(np.isnan(a), np.isnan(b))
             assert np.array_equal(a[~np.isnan(a)], b[~np.isnan(b)])
