@@ -137,9 +137,9 @@ __global__ void __launch_bounds__(256) densify_kernel(const DensifyArgs a) {
 // kernel does, with the same operations, so the two give identical results.
 // The block's patch values are staged in shared memory once (one barrier);
 // a warp's reads of them (19 patches of a row for 32 columns) are broadcasts.
-// The y weights sit in registers (PS / 2 of them: the mask is symmetric); at
-// PS 8 that takes 72 registers, so 7 blocks of 128 per SM (at 64 registers
-// and 8 blocks they spilled, and the class took 4% longer).
+// The y weights sit in registers (PS / 2 of them: the mask is symmetric). At
+// PS 8 the kernel runs at up to 72 registers, 7 blocks of 128 per SM, which
+// measured faster than 8 blocks at 64.
 template <int PS, int S, int K>
 __global__ void __launch_bounds__(128, PS == 8 ? 7 : 6) densify_strip_kernel(const DensifyArgs a) {
   constexpr int M = PS / S;
