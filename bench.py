@@ -564,8 +564,9 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
     for _ in range(max(1, args.warmup)):
         m.match_host(Lp, Rp, params, out=Op)
     # host-path rates move with the host (other tenants, its memory): three
-    # runs of k steps each, the median reported and all three listed
-    k = max(3, args.steps // 3)
+    # runs of the bench's K steps each, the median reported and all three
+    # listed; a run starts with an empty pipeline and ends with a drained one
+    k = max(3, args.steps)
     runs = []
     for _ in range(3):
         t0 = time.perf_counter()
@@ -592,7 +593,7 @@ def measure_extras(args, bd, m, params, left, right, Lh, Rh, Dgt, device, stream
             tickets.append(t)
         m.host_wait(tickets[-1])
 
-    stream_of(max(S, args.warmup))
+    stream_of(max(2 * S, args.warmup))
     runs = []
     for _ in range(3):
         t0 = time.perf_counter()
