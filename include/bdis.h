@@ -259,7 +259,9 @@ bdis_status bdis_match_host(bdis_handle *h, const uint8_t *left, const uint8_t *
  * ticket % 4); a slot is refilled only after the match and the copy-out of
  * the call four before have finished, so up to four calls can be in flight
  * and a copy that runs late holds up the matches only once all four slots
- * are taken.
+ * are taken. Device memory: bdis_match's workspace, whose own input and
+ * output buffers are slot 0, plus three more slots of 6 bytes per pixel
+ * (2 in, 4 out): 2.8 GB more for 512 pairs of 640 x 480.
  * Ownership: left, right and disparity_out stay the caller's; they must not
  * be written (inputs) or read (output) until bdis_host_wait(h, ticket) has
  * returned. Use pinned host memory: with pageable memory the copies, and so
